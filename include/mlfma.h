@@ -1,0 +1,183 @@
+/*
+ * mlfma.h -- C ABI of the GB300 (sm_103a) MLFMA matvec library.
+ *
+ * The library evaluates, for points r_1..r_n and complex charges q,
+ *
+ *     phi_i = sum_{j != i, |r_i - r_j| > 0}  q_j e^{ik|r_i - r_j|} / |r_i - r_j|
+ *
+ * (the Helmholtz potential of Sec. 2, Eq. (1); read here with the kernel
+ * e^{+ikR}/R and without the 1/(4 pi) factor -- the paper's e^{-jkR}/(4 pi R) is its
+ * complex conjugate over 4 pi) with the multilevel fast multipole algorithm: an
+ * octree with Morton-Z keys (Sec. 3.1), near-field direct sums at the leaves and
+ * the five far-field stages C2M, M2M, M2L, L2L, L2O (Sec. 2, Sec. 3.2.1-3.2.5),
+ * with global interpolation/anterpolation between levels and diagonal
+ * translation over the far-field (V) lists (Alg. 1, Alg. 2).
+ *
+ * Conventions shared by every entry point:
+ *   - Complex numbers are interleaved (re, im): complex128 for MLFMA_PREC_FP64,
+ *     complex64 for every other precision.
+ *   - Vectors with several right-hand sides are [nrhs][n], contiguous, in the
+ *     caller's point order (the plan permutes internally).
+ *   - Pointers may address device memory or host memory (pageable or pinned);
+ *     the library detects which.  Device pointers: the call only enqueues work
+ *     on the plan stream and returns.  Host pointers: the call stages the data
+ *     through plan-owned device buffers and synchronises the plan stream before
+ *     returning, so the output is ready.
+ *   - The caller owns every buffer it passes; the plan copies the points at
+ *     creation and never keeps a caller pointer.
+ *   - Errors are returned as mlfma_status; nothing aborts or traps.  A
+ *     thread-local message is available from mlfma_last_error().
+ *   - A plan is not thread-safe: calls on one plan must not overlap.
+ */
+#ifndef MLFMA_H
+#define MLFMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mlfma_plan mlfma_plan;   /* opaque; owns all device state of one tree */
+
+typedef enum {
+    MLFMA_OK = 0,
+    MLFMA_ERR_INVALID_ARG = 1,    /* bad size, null pointer, non-finite input, k <= 0 ... */
+    MLFMA_ERR_OUT_OF_MEMORY = 2,  /* a device allocation failed; nothing leaked */
+    MLFMA_ERR_CUDA = 3,           /* a CUDA runtime call failed (message has the CUDA error) */
+    MLFMA_ERR_TIMEOUT = 4,        /* a bounded device wait ran out */
+    MLFMA_ERR_UNSUPPORTED = 5     /* valid request outside what this build implements */
+} mlfma_status;
+
+typedef enum {
+    MLFMA_PREC_FP64 = 0,          /* complex128 data, FP64 arithmetic on every stage */
+    MLFMA_PREC_FP32 = 1           /* complex64 data, FP32 arithmetic; operators built in FP64 */
+} mlfma_precision;
+
+/* Options of mlfma_plan_create.  Initialise with mlfma_options_init(). */
+typedef struct mlfma_options {
+    size_t struct_size;           /* sizeof(mlfma_options), for forward compatibility */
+    mlfma_precision precision;    /* default MLFMA_PREC_FP32 */
+    double leaf_edge;             /* leaf box edge; <= 0 selects the default: a quarter
+                                     wavelength (pi/(2k)) for digits <= 4, half a
+                                     wavelength (pi/k) for digits >= 5 */
+    int max_depth;                /* deepest tree level, root = 1; default 12 */
+    int digit_margin;             /* d0 = digits + digit_margin in the truncation rule; default 1 */
+    void* stream;                 /* cudaStream_t for all work; NULL = the legacy default stream */
+    /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, void* stream, void* ctx);
+    void* alloc_ctx;
+} mlfma_options;
+
+/* Summary of a plan (levels are numbered from the root, level 1). */
+#define MLFMA_MAX_LEVELS 22
+typedef struct mlfma_info {
+    int64_t n;                    /* number of points */
+    int nlev;                     /* deepest level */
+    int top;                      /* highest level with far-field (M2L) work; 0 if none */
+    int precision;
+    double k, leaf_edge, root_edge;
+    double root_corner[3];        /* x0: lower corner of the root cube */
+    int64_t nbox[MLFMA_MAX_LEVELS + 1];     /* boxes per level */
+    int64_t nleaf[MLFMA_MAX_LEVELS + 1];    /* leaves per level */
+    int L[MLFMA_MAX_LEVELS + 1];            /* truncation per far-field level (0 elsewhere) */
+    int64_t K[MLFMA_MAX_LEVELS + 1];        /* samples per box: (L+1)(2L+2) */
+    int64_t nv[MLFMA_MAX_LEVELS + 1];       /* far-field (V) pairs per level */
+    int64_t near_pairs;                      /* point pairs summed directly */
+    int64_t device_bytes;                    /* device memory held by the plan */
+    double setup_ms;                         /* wall time of mlfma_plan_create */
+} mlfma_info;
+
+/* Tree and list arrays that mlfma_plan_export can copy out (for verification). */
+typedef enum {
+    MLFMA_EXPORT_PERM = 0,        /* int32 [n]: sorted position -> caller index */
+    MLFMA_EXPORT_KEYS = 1,        /* uint64 [n]: sorted Morton keys */
+    MLFMA_EXPORT_BOX_KEY = 2,     /* uint64 [nbox(level)] */
+    MLFMA_EXPORT_BOX_BEGIN = 3,   /* int32 [nbox(level)] first sorted point */
+    MLFMA_EXPORT_BOX_END = 4,     /* int32 [nbox(level)] */
+    MLFMA_EXPORT_BOX_PARENT = 5,  /* int32 [nbox(level)] */
+    MLFMA_EXPORT_BOX_LEAF = 6,    /* uint8 [nbox(level)] */
+    MLFMA_EXPORT_V_OFFSETS = 7,   /* int32 [nbox(level)+1] CSR offsets of the V lists */
+    MLFMA_EXPORT_V_SOURCES = 8,   /* int32 [nv(level)] source boxes (same level), ascending */
+    MLFMA_EXPORT_NEAR_OFFSETS = 9,/* int32 [nleaf_total+1] CSR offsets, leaves ordered by (level, key) */
+    MLFMA_EXPORT_NEAR_SOURCES = 10,/* int32 [2*nnear] (source level, source box) pairs */
+    MLFMA_EXPORT_F = 11,          /* complex [nbox(level)][K(level)]: last apply's multipole signatures */
+    MLFMA_EXPORT_G = 12,          /* complex [nbox(level)][K(level)]: last apply's local signatures */
+    MLFMA_EXPORT_NEAR_PHI = 13,   /* complex [n] sorted order: last apply's near-field part (last rhs) */
+    MLFMA_EXPORT_TRANSLATION = 14 /* complex [316][K(level)]: translation operators of a level */
+} mlfma_export_item;
+
+/* Fills *opt with the defaults. */
+void mlfma_options_init(mlfma_options* opt);
+
+/*
+ * Builds the octree, interaction lists, sampling grids, interpolation matrices
+ * and translation operators of one point set.  Sec. 3.1 (tree, level count,
+ * Morton keys), Sec. 2 (near/far rule), Sec. 3.2.3 (precomputed translation
+ * operators).
+ *   points   [n][3] FP64 xyz, device or host; copied.
+ *   n        >= 1.
+ *   k        wavenumber 2 pi / lambda, finite and > 0.
+ *   digits   requested accuracy 1..12; sets the truncation per level.
+ *   leaf_max 0 = level-uniform tree (leaf edge = options.leaf_edge, Sec. 3.1);
+ *            > 0 = adaptive tree: split while a box holds more than leaf_max points,
+ *            far field only on levels whose edge is >= the leaf edge.
+ *   opt      NULL = defaults.
+ *   out      receives the plan (NULL on error).
+ * Errors: INVALID_ARG (n < 1, k, digits, leaf_max < 0, null pointers, non-finite
+ * coordinates), UNSUPPORTED (uniform tree deeper than max_depth, adaptive trees
+ * in this build), OUT_OF_MEMORY, CUDA.  Synchronises the plan stream.
+ */
+mlfma_status mlfma_plan_create(const double* points, int64_t n, double k, int digits, int leaf_max,
+                               const mlfma_options* opt, mlfma_plan** out);
+
+/*
+ * phi = A q: the matvec above for nrhs right-hand sides (Sec. 2, five stages +
+ * near field).  q [nrhs][n] complex, phi [nrhs][n] complex (overwritten).
+ * Errors: INVALID_ARG (null plan/pointers, nrhs < 1), CUDA.
+ */
+mlfma_status mlfma_apply(mlfma_plan* plan, const void* q, void* phi, int nrhs);
+
+/*
+ * g = A^H r.  A is complex symmetric, so A^H r = conj(A conj(r)); the
+ * conjugations are folded into the permutation kernels.  Same layout and
+ * errors as mlfma_apply.
+ */
+mlfma_status mlfma_apply_adjoint(mlfma_plan* plan, const void* r, void* g, int nrhs);
+
+/* Fills *info.  INVALID_ARG on null pointers. */
+mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info);
+
+/*
+ * Copies one tree/list/signature array to dst (device or host), for
+ * verification.  level is ignored for per-point items.  bytes must be at
+ * least the item's size (returned in *needed when dst is NULL).
+ * Errors: INVALID_ARG (unknown item, level outside 1..nlev, too small), CUDA.
+ * Synchronises the plan stream.
+ */
+mlfma_status mlfma_plan_export(const mlfma_plan* plan, int item, int level, void* dst, size_t bytes,
+                               size_t* needed);
+
+/*
+ * Exact FP64 direct sum on the GPU at selected targets (the quantity the MLFMA
+ * approximates, Sec. 2 Eq. (1)), for accuracy measurement.
+ *   points [n][3] FP64 device, q [n] complex128 device, targets [nt] int64 device
+ *   (caller indices), phi [nt] complex128 device.  Enqueued on ``stream``.
+ * Errors: INVALID_ARG, CUDA.
+ */
+mlfma_status mlfma_direct_fp64(const double* points, int64_t n, const void* q, double k,
+                               const int64_t* targets, int64_t nt, void* phi, void* stream);
+
+/* Releases all device memory of the plan after synchronising its stream.  NULL-safe. */
+void mlfma_destroy(mlfma_plan* plan);
+
+/* Message of the last error on this thread ("" if none). */
+const char* mlfma_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLFMA_H */

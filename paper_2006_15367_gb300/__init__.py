@@ -1,0 +1,305 @@
+"""Python binding of the GB300 MLFMA library (argument marshalling only).
+
+Every step of the matvec runs in the CUDA kernels of ``libmlfma.so`` behind the
+C ABI declared in ``include/mlfma.h``; this module only passes pointers, sizes
+and the current CUDA stream, and hands the library PyTorch's caching allocator
+for its device memory.  There is no fallback: if the library is missing the
+import of a plan fails with an error that says how to build it.
+
+The functions keep the C names (``mlfma_plan_create``, ``mlfma_apply``,
+``mlfma_apply_adjoint``, ``mlfma_plan_info``, ``mlfma_plan_export``,
+``mlfma_direct_fp64``, ``mlfma_destroy``, ``mlfma_last_error``); ``Plan`` wraps
+them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+PREC_FP64 = 0
+PREC_FP32 = 1
+_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32}
+MAX_LEVELS = 22
+
+EXPORT = dict(PERM=0, KEYS=1, BOX_KEY=2, BOX_BEGIN=3, BOX_END=4, BOX_PARENT=5, BOX_LEAF=6, V_OFFSETS=7,
+              V_SOURCES=8, NEAR_OFFSETS=9, NEAR_SOURCES=10, F=11, G=12, NEAR_PHI=13, TRANSLATION=14)
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED"}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_size_t), ("precision", ctypes.c_int), ("leaf_edge", ctypes.c_double),
+                ("max_depth", ctypes.c_int), ("digit_margin", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nlev", ctypes.c_int), ("top", ctypes.c_int), ("precision", ctypes.c_int),
+                ("k", ctypes.c_double), ("leaf_edge", ctypes.c_double), ("root_edge", ctypes.c_double),
+                ("root_corner", ctypes.c_double * 3), ("nbox", ctypes.c_int64 * (MAX_LEVELS + 1)),
+                ("nleaf", ctypes.c_int64 * (MAX_LEVELS + 1)), ("L", ctypes.c_int * (MAX_LEVELS + 1)),
+                ("K", ctypes.c_int64 * (MAX_LEVELS + 1)), ("nv", ctypes.c_int64 * (MAX_LEVELS + 1)),
+                ("near_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double)]
+
+
+class MLFMAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libmlfma.so; raises if it is missing (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError("libmlfma.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, i64, ci, cd = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.mlfma_options_init.argtypes = [ctypes.POINTER(Options)]
+    lib.mlfma_options_init.restype = None
+    lib.mlfma_plan_create.argtypes = [vp, i64, cd, ci, ci, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    lib.mlfma_plan_create.restype = ci
+    lib.mlfma_apply.argtypes = [vp, vp, vp, ci]
+    lib.mlfma_apply.restype = ci
+    lib.mlfma_apply_adjoint.argtypes = [vp, vp, vp, ci]
+    lib.mlfma_apply_adjoint.restype = ci
+    lib.mlfma_plan_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.mlfma_plan_info.restype = ci
+    lib.mlfma_plan_export.argtypes = [vp, ci, ci, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    lib.mlfma_plan_export.restype = ci
+    lib.mlfma_direct_fp64.argtypes = [vp, i64, vp, cd, vp, i64, vp, vp]
+    lib.mlfma_direct_fp64.restype = ci
+    lib.mlfma_destroy.argtypes = [vp]
+    lib.mlfma_destroy.restype = None
+    lib.mlfma_last_error.argtypes = []
+    lib.mlfma_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def mlfma_last_error() -> str:
+    return load().mlfma_last_error().decode()
+
+
+def _check(st):
+    if st != 0:
+        raise MLFMAError(st, mlfma_last_error())
+
+
+def _ptr(x):
+    """Address of a torch tensor or numpy array (must be contiguous)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    return int(x)
+
+
+def mlfma_options_init() -> Options:
+    o = Options()
+    load().mlfma_options_init(ctypes.byref(o))
+    return o
+
+
+def mlfma_plan_create(points, n, k, digits, leaf_max, options=None):
+    """C call: returns the opaque plan handle (int)."""
+    h = ctypes.c_void_p()
+    _check(load().mlfma_plan_create(_ptr(points), int(n), float(k), int(digits), int(leaf_max),
+                                    ctypes.byref(options) if options is not None else None, ctypes.byref(h)))
+    return h.value
+
+
+def mlfma_apply(plan, q, phi, nrhs):
+    _check(load().mlfma_apply(plan, _ptr(q), _ptr(phi), int(nrhs)))
+
+
+def mlfma_apply_adjoint(plan, r, g, nrhs):
+    _check(load().mlfma_apply_adjoint(plan, _ptr(r), _ptr(g), int(nrhs)))
+
+
+def mlfma_plan_info(plan) -> Info:
+    info = Info()
+    _check(load().mlfma_plan_info(plan, ctypes.byref(info)))
+    return info
+
+
+def mlfma_plan_export(plan, item, level, dst=None):
+    need = ctypes.c_size_t()
+    if dst is None:
+        _check(load().mlfma_plan_export(plan, int(item), int(level), None, 0, ctypes.byref(need)))
+        return need.value
+    nbytes = dst.numel() * dst.element_size() if hasattr(dst, "numel") else dst.nbytes
+    _check(load().mlfma_plan_export(plan, int(item), int(level), _ptr(dst), nbytes, ctypes.byref(need)))
+    return need.value
+
+
+def mlfma_direct_fp64(points, n, q, k, targets, nt, phi, stream=None):
+    _check(load().mlfma_direct_fp64(_ptr(points), int(n), _ptr(q), float(k), _ptr(targets), int(nt), _ptr(phi),
+                                    stream))
+
+
+def mlfma_destroy(plan):
+    if plan:
+        load().mlfma_destroy(plan)
+
+
+# ---------------------------------------------------------------------------
+# torch-facing wrapper
+# ---------------------------------------------------------------------------
+class _TorchAllocator:
+    """Routes the library's device allocations through PyTorch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(size, stream, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(size), device=self.device,
+                                                              stream=int(stream or 0)))
+            except Exception:
+                return None
+
+        def _free(ptr, stream, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+class Plan:
+    """An MLFMA plan for one point set: ``phi = plan.apply(q)``.
+
+    points    [n, 3] float64 (torch tensor on a CUDA device, or host array)
+    k         wavenumber; digits: requested accuracy; leaf_max: 0 = level-uniform tree
+    precision "fp32" (complex64 data) or "fp64" (complex128 data)
+    """
+
+    def __init__(self, points, k, digits=3, leaf_max=0, precision="fp32", leaf_edge=0.0, max_depth=12,
+                 digit_margin=1, stream=None, use_torch_allocator=True):
+        import torch
+        self.torch = torch
+        load()
+        if hasattr(points, "device") and points.device.type == "cuda":
+            self.device = points.device
+        else:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        if hasattr(points, "dtype") and hasattr(points, "data_ptr"):
+            pts = points.to(torch.float64).contiguous()
+        else:
+            pts = np.ascontiguousarray(points, dtype=np.float64)
+        self.n = int(pts.shape[0])
+        self.k = float(k)
+        self.precision = precision
+        self.cdtype = torch.complex128 if precision == "fp64" else torch.complex64
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            o = mlfma_options_init()
+            o.precision = _PREC[precision]
+            o.leaf_edge = float(leaf_edge)
+            o.max_depth = int(max_depth)
+            o.digit_margin = int(digit_margin)
+            o.stream = self.stream.cuda_stream
+            self._alloc = None
+            if use_torch_allocator:
+                self._alloc = _TorchAllocator(self.device)
+                o.alloc = self._alloc.alloc
+                o.free = self._alloc.free
+            self.handle = mlfma_plan_create(pts, self.n, self.k, digits, leaf_max, o)
+        self._points = pts
+
+    def _vec(self, x, name):
+        t = self.torch
+        if not isinstance(x, t.Tensor):
+            x = t.as_tensor(np.asarray(x))
+        if x.dtype != self.cdtype:
+            raise TypeError(f"{name} must be {self.cdtype} for precision {self.precision}")
+        if x.shape[-1] != self.n or x.dim() > 2:
+            raise ValueError(f"{name} must be [n] or [nrhs, n] with n = {self.n}")
+        return x.contiguous()
+
+    def apply(self, q, out=None, adjoint=False):
+        q = self._vec(q, "q")
+        nrhs = 1 if q.dim() == 1 else q.shape[0]
+        if out is None:
+            out = self.torch.empty_like(q)
+        with self.torch.cuda.device(self.device):
+            (mlfma_apply_adjoint if adjoint else mlfma_apply)(self.handle, q, out, nrhs)
+        return out
+
+    def adjoint(self, r, out=None):
+        return self.apply(r, out, adjoint=True)
+
+    def info(self) -> dict:
+        i = mlfma_plan_info(self.handle)
+        nl = i.nlev
+        return dict(n=i.n, nlev=nl, top=i.top, precision=i.precision, k=i.k, leaf_edge=i.leaf_edge,
+                    root_edge=i.root_edge, root_corner=list(i.root_corner),
+                    nbox=list(i.nbox[:nl + 1]), nleaf=list(i.nleaf[:nl + 1]), L=list(i.L[:nl + 1]),
+                    K=list(i.K[:nl + 1]), nv=list(i.nv[:nl + 1]), near_pairs=i.near_pairs,
+                    device_bytes=i.device_bytes, setup_ms=i.setup_ms)
+
+    def export(self, item, level=0):
+        """Copies a tree/list/signature array to a host numpy array."""
+        it = EXPORT[item] if isinstance(item, str) else int(item)
+        nbytes = mlfma_plan_export(self.handle, it, level)
+        buf = np.empty(nbytes, dtype=np.uint8)
+        mlfma_plan_export(self.handle, it, level, buf)
+        name = item if isinstance(item, str) else [k for k, v in EXPORT.items() if v == it][0]
+        if name in ("KEYS", "BOX_KEY"):
+            return buf.view(np.uint64)
+        if name == "BOX_LEAF":
+            return buf.view(np.uint8)
+        if name in ("F", "G", "NEAR_PHI", "TRANSLATION"):
+            return buf.view(np.complex128 if self.precision == "fp64" else np.complex64)
+        return buf.view(np.int32)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mlfma_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def direct_fp64(points, q, k, targets, stream=None):
+    """Exact FP64 sum on the GPU at ``targets`` (torch CUDA tensors)."""
+    import torch
+    pts = points.to(torch.float64).contiguous()
+    qq = q.to(torch.complex128).contiguous()
+    tg = targets.to(torch.int64).contiguous()
+    out = torch.empty(tg.shape[0], dtype=torch.complex128, device=pts.device)
+    s = stream if stream is not None else torch.cuda.current_stream(pts.device)
+    mlfma_direct_fp64(pts, pts.shape[0], qq, k, tg, tg.shape[0], out, s.cuda_stream)
+    return out

@@ -1,0 +1,181 @@
+// Internal declarations of the MLFMA library (plan layout, helpers, kernels' launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/mlfma.h"
+
+namespace mlfma {
+
+constexpr int kMaxLev = MLFMA_MAX_LEVELS;   // levels 1..22 (21 key bits per axis)
+constexpr int kBits = 21;
+constexpr int kNumOffsets = 316;            // [-3,3]^3 minus [-1,1]^3: far offsets of one level
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+struct Failure {
+    mlfma_status status;
+};
+[[noreturn]] void fail(mlfma_status st, const char* fmt, ...);
+
+#define MLFMA_CUDA(call)                                                                     \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            ::mlfma::fail(e_ == cudaErrorMemoryAllocation ? MLFMA_ERR_OUT_OF_MEMORY          \
+                                                          : MLFMA_ERR_CUDA,                  \
+                          "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,  \
+                          __LINE__);                                                         \
+    } while (0)
+
+#define MLFMA_LAUNCH_CHECK() MLFMA_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- complex helpers
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(decltype(C::x) a, decltype(C::x) b) {
+    C c; c.x = a; c.y = b; return c;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return cmake<C>(a.x, -a.y); }
+// acc += a * b
+template <typename C> __host__ __device__ __forceinline__ void cfma(C& acc, C a, C b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename C> __host__ __device__ __forceinline__ void cfma_conj(C& acc, C a, C b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc += s * b (s real)
+template <typename C, typename R> __host__ __device__ __forceinline__ void crfma(C& acc, R s, C b) {
+    acc.x = fma(s, b.x, acc.x); acc.y = fma(s, b.y, acc.y);
+}
+
+// ---------------------------------------------------------------- device allocation
+struct Allocator {
+    void* (*alloc)(size_t, void*, void*) = nullptr;
+    void (*free)(void*, void*, void*) = nullptr;
+    void* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    std::vector<std::pair<void*, size_t>> live;
+    size_t bytes = 0;
+    void* get(size_t n);
+    template <typename T> T* make(size_t count) { return static_cast<T*>(get(count * sizeof(T))); }
+    void release_all();
+};
+
+// ---------------------------------------------------------------- plan layout
+struct TreeLevel {                 // one octree level (root = 1)
+    int l = 0;
+    double edge = 0;
+    int64_t nbox = 0;
+    uint64_t* key = nullptr;       // [nbox] ascending level keys
+    int* begin = nullptr;          // [nbox] first sorted point
+    int* end = nullptr;            // [nbox]
+    int* parent = nullptr;         // [nbox] box at level l-1 (-1 at root)
+    int* child_begin = nullptr;    // [nbox] first child at level l+1
+    int* child_end = nullptr;      // [nbox]
+    uint8_t* leaf = nullptr;       // [nbox]
+    int* ijk = nullptr;            // [nbox][3]
+    double* center = nullptr;      // [nbox][3]
+    int* coll = nullptr;           // [nbox][27] colleagues (-1 absent), slot = (dx+1)+3(dy+1)+9(dz+1)
+    int* v_off = nullptr;          // [nbox+1]
+    int* v_src = nullptr;          // [nv]
+    int64_t nv = 0;
+    int64_t nleaf = 0;
+};
+
+struct FarLevel {                  // sampling grid, operators and signatures of one far-field level
+    int L = 0, nth = 0, nph = 0;
+    int64_t K = 0;
+    double* x = nullptr;           // [nth] Gauss-Legendre nodes (cos theta), ascending, FP64
+    double* wgl = nullptr;         // [nth] weights, FP64
+    void* dirs = nullptr;          // [K][4] real: khat_p (x, y, z) and quadrature weight w_p
+    void* tw = nullptr;            // [nph] complex: e^{-2 pi i j / nph}
+    void* T = nullptr;             // [316][K] complex translation operators
+    void* F = nullptr;             // [nbox][K] complex multipole signatures
+    void* G = nullptr;             // [nbox][K] complex local signatures
+    // interpolation from level l+1 (child) to this level (parent); set when l+1 is far-field
+    void* At = nullptr;            // [Lc+1][nth_c][nth_p] real: At[m][i][i'] = A_m[i'][i]
+    void* Bt = nullptr;            // [Lc+1][nth_p][nth_c] real: Bt[m][i'][i] = A_m[i'][i] w'_i' / w_i
+    void* Sz = nullptr;            // [2][nth] complex: e^{-ik cos(theta_i') dz}, dz = -+ edge/4
+    void* Sxy = nullptr;           // [4][K] complex: e^{-ik sin(theta)(cos(phi) dx + sin(phi) dy)}
+    void* X = nullptr;             // [nbox(l+1)][2Lc+1][nth_c] complex scratch (spectral, child grid)
+    void* Y = nullptr;             // [nbox(l+1)][2Lc+1][nth_p] complex scratch (spectral, parent rows)
+};
+
+struct Plan {
+    int64_t n = 0;
+    double k = 0;
+    int digits = 0, leaf_max = 0, max_depth = 12, margin = 1;
+    mlfma_precision prec = MLFMA_PREC_FP32;
+    double leaf_edge = 0, a1 = 0, D0 = 0;
+    double x0[3] = {0, 0, 0}, scale = 0;
+    int nlev = 0, top = 0;
+    int* off343 = nullptr;         // [343] (dx+3)+7(dy+3)+49(dz+3) -> far-offset index 0..315, -1 if near
+    cudaStream_t stream = nullptr;
+    Allocator mem;
+    // per point (sorted order)
+    double* pos = nullptr;         // [n][3] sorted positions, FP64
+    uint64_t* keys = nullptr;      // [n] sorted keys
+    int* perm = nullptr;           // [n] sorted -> caller index
+    int* leaf_of_pt = nullptr;     // [n] index into the leaf table
+    // leaf table (all leaves, ordered by (level, key))
+    int64_t nleaf_total = 0;
+    int* leaf_level = nullptr;     // [nleaf_total]
+    int* leaf_box = nullptr;       // [nleaf_total]
+    std::vector<int64_t> leaf_first;  // host: first leaf-table index of each level
+    // near field: per leaf, source boxes (level, box) summed directly
+    int* near_off = nullptr;       // [nleaf_total+1]
+    int* near_lev = nullptr;       // [nnear]
+    int* near_box = nullptr;       // [nnear]
+    int64_t nnear = 0, near_pairs = 0;
+    TreeLevel lev[kMaxLev + 1];
+    FarLevel far[kMaxLev + 1];
+    // apply buffers
+    void* qs = nullptr;            // [nrhs_cap][n] complex, sorted order
+    void* phis = nullptr;          // [nrhs_cap][n] complex, sorted order
+    void* near_dump = nullptr;     // [n] complex near-field part of the last apply
+    int nrhs_cap = 0;
+    void* host_stage = nullptr;    // device staging for host pointers: [2][nrhs_stage][n] complex
+    int nrhs_stage = 0;
+    double setup_ms = 0;
+};
+
+size_t csize(const Plan& p);       // bytes per complex number
+const char* prec_name(mlfma_precision p);
+
+// ---------------------------------------------------------------- steps (host launchers)
+// tree.cu
+void build_tree(Plan& p, const double* pts_dev);
+void build_lists(Plan& p);
+// setup.cu
+int truncation_L(double edge, double k, int digits, int margin);
+void build_far_levels(Plan& p);
+// far.cu / near.cu
+void apply_pipeline(Plan& p, const void* qs_r, void* phis_r);   // one right-hand side, sorted order
+void far_apply(Plan& p, const void* qs, void* phis);
+void permute_in(Plan& p, const void* q, void* qs, int nrhs, bool conj);
+void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj);
+void direct_fp64(const double* pts, int64_t n, const void* q, double k, const int64_t* tg, int64_t nt,
+                 void* phi, cudaStream_t s);
+
+// device-wide exclusive scan of int32 (returns total); tmp must hold scan_tmp_ints(n) ints
+int64_t scan_tmp_ints(int64_t n);
+int scan_exclusive(const int* in, int* out, int64_t n, int* tmp, cudaStream_t s);
+
+}  // namespace mlfma

@@ -1,0 +1,193 @@
+// Near-field direct sums (Sec. 2: near-field calculations happen only at the leaves),
+// permutation to/from Morton order, the FP64 direct sum used for accuracy checks,
+// and the per-right-hand-side apply pipeline.
+//
+// P2P for a target leaf b sums q_j e^{ikR}/R over the points of its near sources
+// (U list; W and X lists of adaptive trees), skipping R = 0 (the point itself and
+// coincident points).  One warp per target leaf; the source points of each source
+// box are staged through shared memory relative to the target leaf centre (FP64
+// difference, then rounded), lanes split (target, source slice) and the slices are
+// combined with warp shuffles.
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace mlfma {
+
+void far_apply(Plan& p, const void* qs, void* phis);
+
+static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+__device__ __forceinline__ void scpi(float x, float& s, float& c) { sincospif(x, &s, &c); }
+__device__ __forceinline__ void scpi(double x, double& s, double& c) { sincospi(x, &s, &c); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+struct LevelRanges {
+    const int* begin[kMaxLev + 1];
+    const int* end[kMaxLev + 1];
+    const double* center[kMaxLev + 1];
+};
+
+template <typename R, typename C>
+__global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restrict__ leaf_level, const int* __restrict__ leaf_box,
+                                             const int* __restrict__ near_off, const int* __restrict__ near_lev,
+                                             const int* __restrict__ near_box, LevelRanges LR, const double* __restrict__ pos,
+                                             const C* __restrict__ qs, R kpi, C* __restrict__ phis) {
+    __shared__ R sx[4][32], sy[4][32], sz[4][32];
+    __shared__ C sq[4][32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t w = (int64_t)blockIdx.x * 4 + wl;
+    if (w >= nleaf) return;
+    const int l = leaf_level[w], b = leaf_box[w];
+    const int t0 = LR.begin[l][b], t1 = LR.end[l][b];
+    const double* ct = LR.center[l] + 3 * b;
+    const double cx = ct[0], cy = ct[1], cz = ct[2];
+    const int s_lo = near_off[w], s_hi = near_off[w + 1];
+    for (int j0 = t0; j0 < t1; j0 += 32) {
+        const int np = min(32, t1 - j0);
+        int P = 1;
+        while (P < np) P <<= 1;
+        const int S = 32 / P;
+        const int tp = lane & (P - 1), sl = lane / P;
+        const int i = j0 + tp;
+        R x = 0, y = 0, z = 0;
+        if (tp < np) {
+            x = (R)(pos[3 * (int64_t)i] - cx);
+            y = (R)(pos[3 * (int64_t)i + 1] - cy);
+            z = (R)(pos[3 * (int64_t)i + 2] - cz);
+        }
+        C acc = cmake<C>(0, 0);
+        for (int e = s_lo; e < s_hi; ++e) {
+            const int ls = near_lev[e], bs = near_box[e];
+            const int u0 = LR.begin[ls][bs], u1 = LR.end[ls][bs];
+            for (int k0 = u0; k0 < u1; k0 += 32) {
+                const int cnt = min(32, u1 - k0);
+                if (lane < cnt) {
+                    int64_t j = k0 + lane;
+                    sx[wl][lane] = (R)(pos[3 * j] - cx);
+                    sy[wl][lane] = (R)(pos[3 * j + 1] - cy);
+                    sz[wl][lane] = (R)(pos[3 * j + 2] - cz);
+                    sq[wl][lane] = qs[j];
+                }
+                __syncwarp();
+                if (tp < np) {
+                    for (int jj = sl; jj < cnt; jj += S) {
+                        R dx = x - sx[wl][jj], dy = y - sy[wl][jj], dz = z - sz[wl][jj];
+                        R r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 > (R)0) {
+                            R inv = rsq(r2);
+                            R r = r2 * inv;
+                            R s, c;
+                            scpi(kpi * r, s, c);
+                            cfma(acc, sq[wl][jj], cmake<C>(c * inv, s * inv));
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int o = 16; o >= P; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (sl == 0 && tp < np) phis[i] = acc;
+    }
+}
+
+template <typename C>
+__global__ void k_permute_in(int64_t n, int nrhs, const int* __restrict__ perm, const C* __restrict__ q, C* __restrict__ qs, int conj) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * nrhs) return;
+    int64_t r = idx / n, i = idx % n;
+    C v = q[r * n + perm[i]];
+    if (conj) v.y = -v.y;
+    qs[idx] = v;
+}
+
+template <typename C>
+__global__ void k_permute_out(int64_t n, int nrhs, const int* __restrict__ perm, const C* __restrict__ phis, C* __restrict__ phi, int conj) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * nrhs) return;
+    int64_t r = idx / n, i = idx % n;
+    C v = phis[idx];
+    if (conj) v.y = -v.y;
+    phi[r * n + perm[i]] = v;
+}
+
+void permute_in(Plan& p, const void* q, void* qs, int nrhs, bool conj) {
+    int64_t tot = p.n * nrhs;
+    if (p.prec == MLFMA_PREC_FP64)
+        k_permute_in<double2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const double2*)q, (double2*)qs, conj);
+    else
+        k_permute_in<float2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const float2*)q, (float2*)qs, conj);
+    MLFMA_LAUNCH_CHECK();
+}
+
+void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj) {
+    int64_t tot = p.n * nrhs;
+    if (p.prec == MLFMA_PREC_FP64)
+        k_permute_out<double2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const double2*)phis, (double2*)phi, conj);
+    else
+        k_permute_out<float2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const float2*)phis, (float2*)phi, conj);
+    MLFMA_LAUNCH_CHECK();
+}
+
+template <typename R>
+static void near_apply(Plan& p, const void* qs, void* phis) {
+    using C = typename Cx<R>::T;
+    LevelRanges LR;
+    for (int l = 0; l <= kMaxLev; ++l) {
+        LR.begin[l] = l <= p.nlev ? p.lev[l].begin : nullptr;
+        LR.end[l] = l <= p.nlev ? p.lev[l].end : nullptr;
+        LR.center[l] = l <= p.nlev ? p.lev[l].center : nullptr;
+    }
+    const int64_t nl = p.nleaf_total;
+    k_p2p<R, C><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos,
+                                                   (const C*)qs, (R)(p.k / M_PI), (C*)phis);
+    MLFMA_LAUNCH_CHECK();
+}
+
+void apply_pipeline(Plan& p, const void* qs, void* phis) {
+    if (p.prec == MLFMA_PREC_FP64) near_apply<double>(p, qs, phis);
+    else near_apply<float>(p, qs, phis);
+    if (p.near_dump) MLFMA_CUDA(cudaMemcpyAsync(p.near_dump, phis, p.n * csize(p), cudaMemcpyDeviceToDevice, p.stream));
+    far_apply(p, qs, phis);
+}
+
+// ============================================================== FP64 direct sum at selected targets
+__global__ void k_direct_fp64(const double* __restrict__ pts, int64_t n, const double2* __restrict__ q, double k,
+                              const int64_t* __restrict__ tg, double2* __restrict__ phi) {
+    __shared__ double sre[256], sim[256];
+    const int64_t i = tg[blockIdx.x];
+    const double xi = pts[3 * i], yi = pts[3 * i + 1], zi = pts[3 * i + 2];
+    double re = 0, im = 0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        if (j == i) continue;
+        double dx = xi - pts[3 * j], dy = yi - pts[3 * j + 1], dz = zi - pts[3 * j + 2];
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r == 0.0) continue;
+        double s, c;
+        sincos(k * r, &s, &c);
+        double2 qj = q[j];
+        re += (qj.x * c - qj.y * s) / r;
+        im += (qj.x * s + qj.y * c) / r;
+    }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st) { sre[threadIdx.x] += sre[threadIdx.x + st]; sim[threadIdx.x] += sim[threadIdx.x + st]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) phi[blockIdx.x] = make_double2(sre[0], sim[0]);
+}
+
+void direct_fp64(const double* pts, int64_t n, const void* q, double k, const int64_t* tg, int64_t nt, void* phi,
+                 cudaStream_t s) {
+    if (nt <= 0) return;
+    k_direct_fp64<<<(unsigned)nt, 256, 0, s>>>(pts, n, (const double2*)q, k, tg, (double2*)phi);
+    MLFMA_LAUNCH_CHECK();
+}
+
+}  // namespace mlfma

@@ -1,0 +1,339 @@
+// Per-level sampling grids, translation operators, interpolation matrices and shift
+// tables, all computed on the device in FP64 and stored in the apply precision.
+//
+// Sec. 3.2.3 (translation operators are precomputed per level and offset), Sec. 3.2.2
+// and 3.2.4 (global interpolation / anterpolation between the grids of two levels).
+// The grid of a level with truncation L is (L+1) Gauss-Legendre nodes in cos(theta)
+// (ascending) times 2L+2 uniform phi nodes, sample p = i (2L+2) + j, weight
+// w_p = w_i 2 pi / (2L+2).  Translation operator for the box offset X = c_t - c_s:
+//   T_X(khat) = sum_{n=0}^{L} i^n (2n+1) h_n(k|X|) P_n(khat . Xhat),
+// the diagonal plane-wave form of the Gegenbauer addition theorem.
+// Interpolation child (Lc) -> parent (Lp), per Fourier mode m (|m| <= Lc):
+//   A_m[i'][i] = sum_{n=|m|}^{Lc} Pbar_n^m(x'_i') Pbar_n^m(x_i) w_i
+// (Pbar orthonormal on [-1, 1]); anterpolation uses the weighted transpose
+//   B_m[i][i'] = A_m[i'][i] w'_i' / w_i.
+#include <cmath>
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace mlfma {
+
+int truncation_L(double edge, double k, int digits, int margin) {
+    double kD = k * std::sqrt(3.0) * edge;
+    double d0 = (double)(digits + margin);
+    return (int)std::ceil(kD + 1.8 * std::pow(d0, 2.0 / 3.0) * std::pow(kD, 1.0 / 3.0));
+}
+
+static void offsets_table(int* off343, int* dxyz /* [316][3] */) {
+    int c = 0;
+    for (int dz = -3; dz <= 3; ++dz)
+        for (int dy = -3; dy <= 3; ++dy)
+            for (int dx = -3; dx <= 3; ++dx) {
+                int idx = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
+                if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) <= 1) {
+                    off343[idx] = -1;
+                } else {
+                    off343[idx] = c;
+                    dxyz[3 * c] = dx; dxyz[3 * c + 1] = dy; dxyz[3 * c + 2] = dz;
+                    ++c;
+                }
+            }
+}
+
+// ---------------------------------------------------------------- Gauss-Legendre (Newton on P_n)
+__global__ void k_gauss_legendre(int npts, double* __restrict__ x, double* __restrict__ w) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npts) return;
+    // ascending nodes: x_i = -cos(pi (i + 3/4) / (n + 1/2)) as the starting guess
+    double z = -cos(M_PI * (i + 0.75) / (npts + 0.5));
+    double p0 = 1, p1 = z;
+    for (int it = 0; it < 100; ++it) {
+        p0 = 1.0; p1 = z;
+        for (int n = 1; n < npts; ++n) {
+            double p2 = ((2 * n + 1) * z * p1 - n * p0) / (n + 1);
+            p0 = p1; p1 = p2;
+        }
+        double dp = npts * (z * p1 - p0) / (z * z - 1.0);
+        double dz = p1 / dp;
+        z -= dz;
+        if (fabs(dz) < 1e-16) break;
+    }
+    p0 = 1.0; p1 = z;
+    for (int n = 1; n < npts; ++n) {
+        double p2 = ((2 * n + 1) * z * p1 - n * p0) / (n + 1);
+        p0 = p1; p1 = p2;
+    }
+    double dp = npts * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+}
+
+// khat_p and w_p in the apply precision
+template <typename R>
+__global__ void k_dirs(const double* __restrict__ x, const double* __restrict__ wgl, int nth, int nph, R* __restrict__ dirs) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= (int64_t)nth * nph) return;
+    int i = (int)(p / nph), j = (int)(p % nph);
+    double sp, cp;
+    sincospi(2.0 * j / nph, &sp, &cp);
+    double st = sqrt(1.0 - x[i] * x[i]);
+    dirs[4 * p + 0] = (R)(st * cp);
+    dirs[4 * p + 1] = (R)(st * sp);
+    dirs[4 * p + 2] = (R)x[i];
+    dirs[4 * p + 3] = (R)(wgl[i] * 2.0 * M_PI / nph);
+}
+
+template <typename C>
+__global__ void k_twiddle(int nph, C* __restrict__ tw) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nph) return;
+    double s, c;
+    sincospi(-2.0 * j / nph, &s, &c);
+    tw[j] = cmake<C>(c, s);
+}
+
+// ---------------------------------------------------------------- spherical Hankel functions per offset
+// h_n(x), n = 0..L, x = k |X_o|: y_n by upward recurrence; j_n upward while n < x
+// (stable there), else by Miller's downward recurrence normalised with
+// sum_n (2n+1) j_n^2 = 1.
+constexpr int kMillerMax = 2048;
+
+__global__ void k_hankel(int L, double k, double edge, const int* __restrict__ dxyz, double2* __restrict__ hn,
+                         double* __restrict__ work) {
+    int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= kNumOffsets) return;
+    double X[3] = {dxyz[3 * o] * edge, dxyz[3 * o + 1] * edge, dxyz[3 * o + 2] * edge};
+    double x = k * sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+    double2* h = hn + (size_t)o * (L + 1);
+    // y_n
+    double sx, cx;
+    sincos(x, &sx, &cx);
+    double ym1 = -cx / x, y0 = -cx / (x * x) - sx / x;
+    h[0].y = ym1;
+    if (L >= 1) h[1].y = y0;
+    for (int n = 1; n < L; ++n) {
+        double y1 = (2 * n + 1) / x * y0 - ym1;
+        h[n + 1].y = y1;
+        ym1 = y0; y0 = y1;
+    }
+    // j_n
+    if (x > L + 1) {
+        double jm1 = sx / x, j0 = sx / (x * x) - cx / x;
+        h[0].x = jm1;
+        if (L >= 1) h[1].x = j0;
+        for (int n = 1; n < L; ++n) {
+            double j1 = (2 * n + 1) / x * j0 - jm1;
+            h[n + 1].x = j1;
+            jm1 = j0; j0 = j1;
+        }
+    } else {
+        double* v = work + (size_t)o * (kMillerMax + 2);
+        int ns = (int)fmax((double)L, x) + 40 + (int)(2.0 * sqrt(fmax((double)L, x)));
+        if (ns > kMillerMax) ns = kMillerMax;
+        v[ns + 1] = 0.0;
+        v[ns] = 1.0;
+        for (int n = ns; n > 0; --n) {
+            v[n - 1] = (2 * n + 1) / x * v[n] - v[n + 1];
+            if (fabs(v[n - 1]) > 1e100)
+                for (int m = n - 1; m <= ns + 1; ++m) v[m] *= 1e-100;
+        }
+        double s = 0;
+        for (int n = 0; n <= ns + 1; ++n) s += (2.0 * n + 1.0) * v[n] * v[n];
+        double inv = 1.0 / sqrt(s);
+        for (int n = 0; n <= L; ++n) h[n].x = v[n] * inv;
+    }
+}
+
+template <typename C>
+__global__ void k_translation(int L, int nth, int nph, double edge, const double* __restrict__ x, const int* __restrict__ dxyz,
+                              const double2* __restrict__ hn, C* __restrict__ T) {
+    int64_t K = (int64_t)nth * nph;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= K * kNumOffsets) return;
+    int o = (int)(idx / K);
+    int64_t p = idx % K;
+    int i = (int)(p / nph), j = (int)(p % nph);
+    double X[3] = {(double)dxyz[3 * o], (double)dxyz[3 * o + 1], (double)dxyz[3 * o + 2]};
+    double r = sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+    double sp, cp;
+    sincospi(2.0 * j / nph, &sp, &cp);
+    double st = sqrt(1.0 - x[i] * x[i]);
+    double t = (st * cp * X[0] + st * sp * X[1] + x[i] * X[2]) / r;
+    const double2* h = hn + (size_t)o * (L + 1);
+    double re = 0, im = 0;
+    double pm1 = 1.0, p0 = t;
+    // n = 0: i^0 (1) h_0 P_0
+    re += h[0].x; im += h[0].y;
+    for (int n = 1; n <= L; ++n) {
+        double Pn = (n == 1) ? t : p0;
+        if (n >= 2) {
+            Pn = ((2 * n - 1) * t * p0 - (n - 1) * pm1) / n;
+            pm1 = p0; p0 = Pn;
+        }
+        double a = (2 * n + 1) * Pn;
+        // i^n h_n
+        double hr = h[n].x, hi = h[n].y, cr, ci;
+        switch (n & 3) {
+            case 0: cr = hr; ci = hi; break;
+            case 1: cr = -hi; ci = hr; break;
+            case 2: cr = -hr; ci = -hi; break;
+            default: cr = hi; ci = -hr; break;
+        }
+        re += a * cr; im += a * ci;
+    }
+    (void)edge;
+    T[idx] = cmake<C>(re, im);
+}
+
+// ---------------------------------------------------------------- interpolation matrices
+// Pbar_m^m = sqrt((2m+1)/2 prod_{k<=m} (2k-1)/(2k)) (1-x^2)^{m/2}, then the column recurrence in n.
+__device__ double pbar_mm(int m, double x) {
+    double c = 0.5 * (2 * m + 1);
+    for (int kk = 1; kk <= m; ++kk) c *= (2.0 * kk - 1.0) / (2.0 * kk);
+    double s2 = fmax(1.0 - x * x, 0.0);
+    return sqrt(c) * pow(s2, 0.5 * m);
+}
+
+template <typename R>
+__global__ void k_interp(int Lc, const double* __restrict__ xc, const double* __restrict__ wc, int nthp,
+                         const double* __restrict__ xp, const double* __restrict__ wp, R* __restrict__ At, R* __restrict__ Bt) {
+    const int nthc = Lc + 1;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t tot = (int64_t)(Lc + 1) * nthc * nthp;
+    if (idx >= tot) return;
+    int ip = (int)(idx % nthp);
+    int i = (int)((idx / nthp) % nthc);
+    int m = (int)(idx / ((int64_t)nthp * nthc));
+    double a = xc[i], b = xp[ip];
+    double pa = pbar_mm(m, a), pb = pbar_mm(m, b);
+    double s = pa * pb;
+    if (m + 1 <= Lc) {
+        double qa = a * sqrt(2.0 * m + 3.0) * pa, qb = b * sqrt(2.0 * m + 3.0) * pb;
+        s += qa * qb;
+        for (int n = m + 2; n <= Lc; ++n) {
+            double an = sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+            double bn = sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+            double ra = an * (a * qa - bn * pa), rb = an * (b * qb - bn * pb);
+            pa = qa; qa = ra; pb = qb; qb = rb;
+            s += ra * rb;
+        }
+    }
+    double A = s * wc[i];                       // A_m[i'][i]
+    At[((int64_t)m * nthc + i) * nthp + ip] = (R)A;
+    Bt[((int64_t)m * nthp + ip) * nthc + i] = (R)(A * wp[ip] / wc[i]);
+}
+
+// shift tables of a parent level: Sz[sz][i'] and Sxy[q][p']
+template <typename C>
+__global__ void k_shifts(int nth, int nph, double k, double edge, const double* __restrict__ x, C* __restrict__ Sz, C* __restrict__ Sxy) {
+    int64_t K = (int64_t)nth * nph;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const double q4 = 0.25 * edge;
+    if (idx < 2 * nth) {
+        int sz = (int)(idx / nth), i = (int)(idx % nth);
+        double dz = (2 * sz - 1) * q4;
+        double s, c;
+        sincos(-k * x[i] * dz, &s, &c);
+        Sz[idx] = cmake<C>(c, s);
+    }
+    if (idx < 4 * K) {
+        int q = (int)(idx / K);
+        int64_t p = idx % K;
+        int i = (int)(p / nph), j = (int)(p % nph);
+        double dx = (2 * (q & 1) - 1) * q4, dy = (2 * ((q >> 1) & 1) - 1) * q4;
+        double sp, cp;
+        sincospi(2.0 * j / nph, &sp, &cp);
+        double st = sqrt(1.0 - x[i] * x[i]);
+        double s, c;
+        sincos(-k * st * (cp * dx + sp * dy), &s, &c);
+        Sxy[idx] = cmake<C>(c, s);
+    }
+}
+
+static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+template <typename R>
+static void build_far_levels_t(Plan& p) {
+    using C = typename Cx<R>::T;
+    cudaStream_t s = p.stream;
+    int off343[343], dxyz[3 * kNumOffsets];
+    offsets_table(off343, dxyz);
+    p.off343 = p.mem.make<int>(343);
+    MLFMA_CUDA(cudaMemcpyAsync(p.off343, off343, sizeof(off343), cudaMemcpyHostToDevice, s));
+    int* d_dxyz = p.mem.make<int>(3 * kNumOffsets);
+    MLFMA_CUDA(cudaMemcpyAsync(d_dxyz, dxyz, sizeof(dxyz), cudaMemcpyHostToDevice, s));
+
+    // top: highest level with a non-empty V list
+    p.top = 0;
+    for (int l = 2; l <= p.nlev; ++l)
+        if (p.lev[l].nv > 0) { p.top = l; break; }
+    if (!p.top) return;
+    int Lmax = 0;
+    for (int l = p.top; l <= p.nlev; ++l) {
+        FarLevel& F = p.far[l];
+        F.L = truncation_L(p.lev[l].edge, p.k, p.digits, p.margin);
+        F.nth = F.L + 1;
+        F.nph = 2 * F.L + 2;
+        F.K = (int64_t)F.nth * F.nph;
+        Lmax = std::max(Lmax, F.L);
+    }
+    double2* hn = p.mem.make<double2>((size_t)kNumOffsets * (Lmax + 1));
+    double* work = p.mem.make<double>((size_t)kNumOffsets * (kMillerMax + 2));
+    for (int l = p.top; l <= p.nlev; ++l) {
+        FarLevel& F = p.far[l];
+        F.x = p.mem.make<double>(F.nth);
+        F.wgl = p.mem.make<double>(F.nth);
+        k_gauss_legendre<<<nblk(F.nth, 64), 64, 0, s>>>(F.nth, F.x, F.wgl);
+        MLFMA_LAUNCH_CHECK();
+        F.dirs = p.mem.make<R>(4 * F.K);
+        k_dirs<R><<<nblk(F.K, 256), 256, 0, s>>>(F.x, F.wgl, F.nth, F.nph, (R*)F.dirs);
+        MLFMA_LAUNCH_CHECK();
+        F.tw = p.mem.make<C>(F.nph);
+        k_twiddle<C><<<nblk(F.nph, 256), 256, 0, s>>>(F.nph, (C*)F.tw);
+        MLFMA_LAUNCH_CHECK();
+        k_hankel<<<nblk(kNumOffsets, 32), 32, 0, s>>>(F.L, p.k, p.lev[l].edge, d_dxyz, hn, work);
+        MLFMA_LAUNCH_CHECK();
+        F.T = p.mem.make<C>((size_t)kNumOffsets * F.K);
+        k_translation<C><<<nblk(F.K * kNumOffsets, 128), 128, 0, s>>>(F.L, F.nth, F.nph, p.lev[l].edge, F.x, d_dxyz, hn,
+                                                                      (C*)F.T);
+        MLFMA_LAUNCH_CHECK();
+        F.F = p.mem.make<C>((size_t)p.lev[l].nbox * F.K);
+        F.G = p.mem.make<C>((size_t)p.lev[l].nbox * F.K);
+    }
+    for (int l = p.top; l < p.nlev; ++l) {
+        FarLevel& P = p.far[l];
+        FarLevel& Ch = p.far[l + 1];
+        int64_t nA = (int64_t)(Ch.L + 1) * Ch.nth * P.nth;
+        P.At = p.mem.make<R>(nA);
+        P.Bt = p.mem.make<R>(nA);
+        k_interp<R><<<nblk(nA, 128), 128, 0, s>>>(Ch.L, Ch.x, Ch.wgl, P.nth, P.x, P.wgl, (R*)P.At, (R*)P.Bt);
+        MLFMA_LAUNCH_CHECK();
+        P.Sz = p.mem.make<C>(2 * P.nth);
+        P.Sxy = p.mem.make<C>(4 * P.K);
+        k_shifts<C><<<nblk(4 * P.K, 256), 256, 0, s>>>(P.nth, P.nph, p.k, p.lev[l].edge, P.x, (C*)P.Sz, (C*)P.Sxy);
+        MLFMA_LAUNCH_CHECK();
+    }
+    // spectral scratch shared by all level pairs: X [nbox_c][2Lc+1][nth_c], Y [nbox_c][2Lc+1][nth_p]
+    size_t xs = 0, ys = 0;
+    for (int l = p.top; l < p.nlev; ++l) {
+        const FarLevel& P = p.far[l];
+        const FarLevel& Ch = p.far[l + 1];
+        size_t nb = (size_t)p.lev[l + 1].nbox;
+        xs = std::max(xs, nb * (2 * Ch.L + 1) * Ch.nth);
+        ys = std::max(ys, nb * (2 * Ch.L + 1) * P.nth);
+    }
+    if (xs) {
+        void* X = p.mem.make<C>(xs);
+        void* Y = p.mem.make<C>(ys);
+        for (int l = p.top; l < p.nlev; ++l) { p.far[l].X = X; p.far[l].Y = Y; }
+    }
+    MLFMA_CUDA(cudaStreamSynchronize(s));
+}
+
+void build_far_levels(Plan& p) {
+    if (p.prec == MLFMA_PREC_FP64) build_far_levels_t<double>(p);
+    else build_far_levels_t<float>(p);
+}
+
+}  // namespace mlfma
