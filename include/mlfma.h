@@ -109,6 +109,25 @@ typedef enum {
     MLFMA_EXPORT_TRANSLATION = 14 /* complex [316][K(level)]: translation operators of a level */
 } mlfma_export_item;
 
+/* Stages timed by mlfma_plan_profile / mlfma_plan_timings. */
+typedef enum {
+    MLFMA_STAGE_PERMUTE = 0,      /* caller order <-> Morton order */
+    MLFMA_STAGE_P2P = 1,          /* near-field direct sums */
+    MLFMA_STAGE_C2M = 2,
+    MLFMA_STAGE_M2M = 3,          /* interpolate, shift, aggregate (all kernels of one level) */
+    MLFMA_STAGE_M2L = 4,
+    MLFMA_STAGE_L2L = 5,          /* shift, anterpolate, add */
+    MLFMA_STAGE_L2O = 6,
+    MLFMA_STAGE_COUNT = 7
+} mlfma_stage;
+
+typedef struct mlfma_timings {
+    double ms[MLFMA_STAGE_COUNT];             /* summed CUDA-event time per stage */
+    int64_t launches[MLFMA_STAGE_COUNT];      /* kernel launches per stage */
+    double m2l_ms[MLFMA_MAX_LEVELS + 1];      /* M2L time per level */
+    int64_t applies;                          /* right-hand sides applied while profiling */
+} mlfma_timings;
+
 /* Fills *opt with the defaults. */
 void mlfma_options_init(mlfma_options* opt);
 
@@ -169,6 +188,19 @@ mlfma_status mlfma_plan_export(const mlfma_plan* plan, int item, int level, void
  */
 mlfma_status mlfma_direct_fp64(const double* points, int64_t n, const void* q, double k,
                                const int64_t* targets, int64_t nt, void* phi, void* stream);
+
+/*
+ * Starts (enable = 1) or stops (0) recording CUDA events around every stage of
+ * the apply on the plan stream.  Recording adds two event records per stage
+ * launch group and nothing else.  INVALID_ARG on a null plan.
+ */
+mlfma_status mlfma_plan_profile(mlfma_plan* plan, int enable);
+
+/*
+ * Synchronises the plan stream and returns the per-stage times recorded since
+ * the last reset; reset = 1 clears them.  INVALID_ARG on null pointers, CUDA.
+ */
+mlfma_status mlfma_plan_timings(mlfma_plan* plan, mlfma_timings* out, int reset);
 
 /* Releases all device memory of the plan after synchronising its stream.  NULL-safe. */
 void mlfma_destroy(mlfma_plan* plan);

@@ -23,8 +23,8 @@ and the Funk-Hecke identity (derivation in the design doc):
 
 Readings (listed in the design doc): kernel e^{+ikR}/R without 1/(4 pi), self term and
 coincident points excluded; sampling grid = (L+1) Gauss-Legendre nodes in
-cos(theta) (ascending) x (2L+2) uniform phi nodes, sample p = i (2L+2) + j,
-weights w_p = w_i^GL 2pi/(2L+2); global interpolation by spherical-harmonic
+cos(theta) (ascending) x nph uniform phi nodes (nph = smallest even 7-smooth number
+>= 2L+2), sample p = i nph + j, weights w_p = w_i^GL 2pi/nph; global interpolation by spherical-harmonic
 projection per Fourier mode (the 'global interpolation' the paper insists on,
 Sec. 2 Related Work); truncation L = ceil(kD + 1.8 d0^(2/3) (kD)^(1/3)) with
 D = sqrt(3) * edge, d0 = digits + DIGIT_MARGIN (excess-bandwidth rule, not
@@ -51,13 +51,31 @@ def truncation_L(edge: float, k: float, digits: int, margin: int = DIGIT_MARGIN)
     return int(math.ceil(kD + 1.8 * d0 ** (2.0 / 3.0) * kD ** (1.0 / 3.0)))
 
 
+def smooth_even(m: int) -> int:
+    """Smallest even number >= m whose prime factors are all in {2, 3, 5, 7}."""
+    while True:
+        t = m
+        for r in (2, 3, 5, 7):
+            while t % r == 0:
+                t //= r
+        if t == 1 and m % 2 == 0:
+            return m
+        m += 1
+
+
 class Grid:
-    """theta-phi sampling grid of one level."""
+    """theta-phi sampling grid of one level.
+
+    (L+1) Gauss-Legendre nodes in cos(theta) and nph uniform phi nodes, with nph the
+    smallest even 7-smooth number >= 2L+2 (>= 2L+2 keeps the phi quadrature exact
+    for the degree-2L products it integrates; the smooth size lets the GPU path use
+    mixed-radix FFTs in phi).
+    """
 
     def __init__(self, L: int):
         self.L = L
         self.nth = L + 1
-        self.nph = 2 * L + 2
+        self.nph = smooth_even(2 * L + 2)
         self.K = self.nth * self.nph
         self.x, self.wgl = special.gauss_legendre(self.nth)
         self.phi = 2.0 * math.pi * np.arange(self.nph) / self.nph

@@ -48,6 +48,14 @@ class Info(ctypes.Structure):
                 ("near_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double)]
 
 
+STAGES = ["PERMUTE", "P2P", "C2M", "M2M", "M2L", "L2L", "L2O"]
+
+
+class Timings(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * len(STAGES)), ("launches", ctypes.c_int64 * len(STAGES)),
+                ("m2l_ms", ctypes.c_double * (MAX_LEVELS + 1)), ("applies", ctypes.c_int64)]
+
+
 class MLFMAError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -87,6 +95,10 @@ def load(build_if_missing: bool = False):
     lib.mlfma_plan_export.restype = ci
     lib.mlfma_direct_fp64.argtypes = [vp, i64, vp, cd, vp, i64, vp, vp]
     lib.mlfma_direct_fp64.restype = ci
+    lib.mlfma_plan_profile.argtypes = [vp, ci]
+    lib.mlfma_plan_profile.restype = ci
+    lib.mlfma_plan_timings.argtypes = [vp, ctypes.POINTER(Timings), ci]
+    lib.mlfma_plan_timings.restype = ci
     lib.mlfma_destroy.argtypes = [vp]
     lib.mlfma_destroy.restype = None
     lib.mlfma_last_error.argtypes = []
@@ -160,6 +172,16 @@ def mlfma_plan_export(plan, item, level, dst=None):
 def mlfma_direct_fp64(points, n, q, k, targets, nt, phi, stream=None):
     _check(load().mlfma_direct_fp64(_ptr(points), int(n), _ptr(q), float(k), _ptr(targets), int(nt), _ptr(phi),
                                     stream))
+
+
+def mlfma_plan_profile(plan, enable):
+    _check(load().mlfma_plan_profile(plan, int(bool(enable))))
+
+
+def mlfma_plan_timings(plan, reset=True) -> Timings:
+    t = Timings()
+    _check(load().mlfma_plan_timings(plan, ctypes.byref(t), int(bool(reset))))
+    return t
 
 
 def mlfma_destroy(plan):
@@ -280,6 +302,16 @@ class Plan:
         if name in ("F", "G", "NEAR_PHI", "TRANSLATION"):
             return buf.view(np.complex128 if self.precision == "fp64" else np.complex64)
         return buf.view(np.int32)
+
+    def profile(self, enable=True):
+        """Start/stop recording CUDA events around every apply stage."""
+        mlfma_plan_profile(self.handle, enable)
+
+    def timings(self, reset=True) -> dict:
+        t = mlfma_plan_timings(self.handle, reset)
+        return dict(ms={s: t.ms[i] for i, s in enumerate(STAGES)},
+                    launches={s: t.launches[i] for i, s in enumerate(STAGES)},
+                    m2l_ms=list(t.m2l_ms), applies=t.applies)
 
     def close(self):
         if getattr(self, "handle", None):

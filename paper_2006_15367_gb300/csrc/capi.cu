@@ -99,10 +99,17 @@ static void apply_impl(Plan& p, const void* q, void* phi, int nrhs, bool adjoint
         }
         if (!dphi) phid = (char*)p.host_stage + bytes;
     }
-    permute_in(p, qd, p.qs, nrhs, adjoint);
+    {
+        StageTimer st(p, MLFMA_STAGE_PERMUTE, 0, 1);
+        permute_in(p, qd, p.qs, nrhs, adjoint);
+    }
     for (int r = 0; r < nrhs; ++r)
         apply_pipeline(p, (const char*)p.qs + (size_t)r * p.n * csize(p), (char*)p.phis + (size_t)r * p.n * csize(p));
-    permute_out(p, p.phis, phid, nrhs, adjoint);
+    {
+        StageTimer st(p, MLFMA_STAGE_PERMUTE, 0, 1);
+        permute_out(p, p.phis, phid, nrhs, adjoint);
+    }
+    if (p.profiling) p.acc.applies += nrhs;
     if (!dphi) {
         MLFMA_CUDA(cudaMemcpyAsync(phi, phid, bytes, cudaMemcpyDeviceToHost, p.stream));
         MLFMA_CUDA(cudaStreamSynchronize(p.stream));
@@ -314,10 +321,73 @@ mlfma_status mlfma_direct_fp64(const double* points, int64_t n, const void* q, d
 void mlfma_destroy(mlfma_plan* plan) {
     if (!plan) return;
     cudaStreamSynchronize(plan->p.stream);
+    for (auto& r : plan->p.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : plan->p.pool) cudaEventDestroy(e);
     plan->p.mem.release_all();
     delete plan;
 }
 
 const char* mlfma_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+namespace mlfma {
+
+static cudaEvent_t take_event(Plan& p) {
+    if (!p.pool.empty()) {
+        cudaEvent_t e = p.pool.back();
+        p.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    MLFMA_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+StageTimer::StageTimer(Plan& plan, int stage, int level, int launches) : p(plan) {
+    if (!p.profiling) return;
+    Plan::EventRec r{stage, level, launches, take_event(p), take_event(p)};
+    MLFMA_CUDA(cudaEventRecord(r.a, p.stream));
+    p.recs.push_back(r);
+    idx = (int)p.recs.size() - 1;
+}
+
+StageTimer::~StageTimer() {
+    if (idx >= 0) cudaEventRecord(p.recs[idx].b, p.stream);
+}
+
+void collect_timings(Plan& p) {
+    MLFMA_CUDA(cudaStreamSynchronize(p.stream));
+    for (auto& r : p.recs) {
+        float ms = 0;
+        MLFMA_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        p.acc.ms[r.stage] += ms;
+        p.acc.launches[r.stage] += r.launches;
+        if (r.stage == MLFMA_STAGE_M2L && r.level >= 0 && r.level <= kMaxLev) p.acc.m2l_ms[r.level] += ms;
+        p.pool.push_back(r.a);
+        p.pool.push_back(r.b);
+    }
+    p.recs.clear();
+}
+
+}  // namespace mlfma
+
+extern "C" {
+
+mlfma_status mlfma_plan_profile(mlfma_plan* plan, int enable) {
+    return guarded([&] {
+        if (!plan) fail(MLFMA_ERR_INVALID_ARG, "null plan");
+        plan->p.profiling = enable != 0;
+    });
+}
+
+mlfma_status mlfma_plan_timings(mlfma_plan* plan, mlfma_timings* out, int reset) {
+    return guarded([&] {
+        if (!plan || !out) fail(MLFMA_ERR_INVALID_ARG, "null plan or out");
+        collect_timings(plan->p);
+        *out = plan->p.acc;
+        if (reset) memset(&plan->p.acc, 0, sizeof(plan->p.acc));
+    });
+}
 
 }  // extern "C"

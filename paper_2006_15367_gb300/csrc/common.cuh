@@ -99,8 +99,17 @@ struct TreeLevel {                 // one octree level (root = 1)
     int64_t nleaf = 0;
 };
 
+struct FftPlan {                   // mixed-radix factorisation of an FFT length (radices 2, 3, 4, 5, 7)
+    int n = 0;
+    int ns = 0;
+    int r[16] = {0};
+};
+FftPlan make_fft_plan(int n);
+int smooth_even(int m);
+
 struct FarLevel {                  // sampling grid, operators and signatures of one far-field level
     int L = 0, nth = 0, nph = 0;
+    FftPlan fft;                   // plan for length nph
     int64_t K = 0;
     double* x = nullptr;           // [nth] Gauss-Legendre nodes (cos theta), ascending, FP64
     double* wgl = nullptr;         // [nth] weights, FP64
@@ -154,7 +163,25 @@ struct Plan {
     void* host_stage = nullptr;    // device staging for host pointers: [2][nrhs_stage][n] complex
     int nrhs_stage = 0;
     double setup_ms = 0;
+    // stage profiling (CUDA events on the plan stream)
+    bool profiling = false;
+    struct EventRec {
+        int stage, level, launches;
+        cudaEvent_t a, b;
+    };
+    std::vector<EventRec> recs;
+    std::vector<cudaEvent_t> pool;
+    mlfma_timings acc{};
 };
+
+// Records CUDA events around a group of launches of one stage while profiling is on.
+struct StageTimer {
+    Plan& p;
+    int idx = -1;
+    StageTimer(Plan& plan, int stage, int level, int launches);
+    ~StageTimer();
+};
+void collect_timings(Plan& p);
 
 size_t csize(const Plan& p);       // bytes per complex number
 const char* prec_name(mlfma_precision p);

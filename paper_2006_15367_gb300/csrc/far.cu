@@ -9,7 +9,7 @@
 //
 // Interpolation I_{c->P} (global, per Fourier mode): forward DFT in phi on the child
 // grid (modes |m| <= Lc), theta map A_|m| per mode, inverse DFT onto the parent phi
-// nodes.  The shift to the parent centre factors into a theta-only part
+// nodes; both phi transforms are mixed-radix FFTs in shared memory.  The shift to the parent centre factors into a theta-only part
 // e^{-ik cos(theta') dz} (applied per mode, before the inverse DFT, which lets the
 // two children stacked in z share one inverse DFT) and a theta-phi part applied on
 // the parent grid.  Anterpolation is the weighted transpose of the same steps.
@@ -193,43 +193,225 @@ __global__ void __launch_bounds__(256) k_m2l(const int* __restrict__ pcb, const 
         if (t < nt) G[(int64_t)(t0 + t) * K + p] = acc[t];
 }
 
-// ============================================================== interpolation building blocks
-// forward DFT in phi of the rows of one box: X[b][mi][i] = scale sum_j F[b][i][j] tw[(sgn m j) mod nph]
+// ============================================================== phi transforms: mixed-radix FFTs in shared memory
+// Stockham autosort FFT of several rows at once (length n = prod of radices 2, 3, 4, 5, 7).
+// tw[k] = e^{-2 pi i k / n}; inv = true uses e^{+2 pi i k / n} (no 1/n scaling).
 template <typename C>
-__global__ void k_dft_rows(int64_t nbox, const C* __restrict__ F, int nth, int nph, int L, int sgn, const C* __restrict__ tw,
-                           typename std::conditional<sizeof(C) == 8, float, double>::type scale, int RT, C* __restrict__ X,
-                           const C* __restrict__ pre, int pre_q) {
-    extern __shared__ unsigned char smem_raw[];
-    C* rows = reinterpret_cast<C*>(smem_raw);
-    const int ld = nph + 1;
-    C* stw = rows + RT * ld;
-    const int64_t b = blockIdx.x;
-    const int i0 = blockIdx.y * RT;
-    const int nr = min(RT, nth - i0);
-    const int64_t K = (int64_t)nth * nph;
-    for (int idx = threadIdx.x; idx < nr * nph; idx += blockDim.x) {
-        int r = idx / nph, j = idx % nph;
-        C v = F[b * K + (int64_t)(i0 + r) * nph + j];
-        if (pre) v = cmul(cconj(pre[(int64_t)pre_q * K + (int64_t)(i0 + r) * nph + j]), v);
-        rows[r * ld + j] = v;
+__device__ __forceinline__ C twid(const C* __restrict__ tw, int idx, bool inv) {
+    C t = tw[idx];
+    if (inv) t.y = -t.y;
+    return t;
+}
+
+template <int R, typename C>
+__device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict__ b, int j, int Ns, int n,
+                                         const C* __restrict__ tw, bool inv) {
+    const int nb = n / R;
+    const int k = j % Ns;
+    const int tstep = n / (Ns * R);
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        C x = a[j + r * nb];
+        if (r > 0) x = cmul(x, twid(tw, k * r * tstep, inv));
+        v[r] = x;
     }
-    for (int j = threadIdx.x; j < nph; j += blockDim.x) stw[j] = tw[j];
-    __syncthreads();
-    const int nm = 2 * L + 1;
-    for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
-        int r = idx % nr, mi = idx / nr;
-        int m = mi - L;
-        int step = ((sgn * m) % nph + nph) % nph;
-        int kk = 0;
-        C acc = cmake<C>(0, 0);
-        const C* row = rows + r * ld;
-        for (int j = 0; j < nph; ++j) {
-            cfma(acc, row[j], stw[kk]);
-            kk += step;
-            if (kk >= nph) kk -= nph;
+    const int idxD = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int kk = 0; kk < R; ++kk) {
+        C s = v[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) cfma(s, v[r], twid(tw, ((r * kk) % R) * nb, inv));
+        b[idxD + kk * Ns] = s;
+    }
+}
+
+// Transforms nrows rows of length fp.n stored contiguously in buf0; returns the buffer
+// holding the result (buf0 or buf1).  All threads of the block take part.
+template <typename C>
+__device__ C* fft_rows(C* buf0, C* buf1, int nrows, const FftPlan& fp, const C* __restrict__ tw, bool inv) {
+    const int n = fp.n;
+    C* in = buf0;
+    C* out = buf1;
+    int Ns = 1;
+    for (int st = 0; st < fp.ns; ++st) {
+        const int R = fp.r[st];
+        const int nb = n / R;
+        for (int idx = threadIdx.x; idx < nrows * nb; idx += blockDim.x) {
+            const int row = idx / nb, j = idx - row * nb;
+            const C* a = in + row * n;
+            C* b = out + row * n;
+            switch (R) {
+                case 2: fft_bfly<2>(a, b, j, Ns, n, tw, inv); break;
+                case 3: fft_bfly<3>(a, b, j, Ns, n, tw, inv); break;
+                case 4: fft_bfly<4>(a, b, j, Ns, n, tw, inv); break;
+                case 5: fft_bfly<5>(a, b, j, Ns, n, tw, inv); break;
+                default: fft_bfly<7>(a, b, j, Ns, n, tw, inv); break;
+            }
         }
-        acc.x *= scale; acc.y *= scale;
-        X[(b * nm + mi) * nth + i0 + r] = acc;
+        __syncthreads();
+        C* t = in; in = out; out = t;
+        Ns *= R;
+    }
+    return in;
+}
+
+__device__ __forceinline__ int wrap(int m, int n) { return m < 0 ? m + n : m; }
+
+// M2M first step: X[c][mi][i] = scale sum_j F[c][i][j] e^{-i m phi_j}, |m| <= Lc, for the rows
+// (c, i) of all children (rows are contiguous in F).
+template <typename C, typename R>
+__global__ void k_fft_fwd_rows(int64_t nrows_tot, const C* __restrict__ F, int nth, int Lc, FftPlan fp,
+                               const C* __restrict__ tw, R scale, int RB, C* __restrict__ X) {
+    extern __shared__ unsigned char smem_raw[];
+    const int n = fp.n, nm = 2 * Lc + 1;
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + RB * n;
+    C* stw = buf1 + RB * n;
+    const int64_t r0 = (int64_t)blockIdx.x * RB;
+    const int nr = (int)((nrows_tot - r0) < RB ? (nrows_tot - r0) : RB);
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = F[r0 * n + idx];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
+    __syncthreads();
+    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
+    for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
+        const int row = idx % nr, mi = idx / nr;
+        const int64_t r = r0 + row;
+        const int64_t c = r / nth;
+        const int i = (int)(r - c * nth);
+        C v = res[row * n + wrap(mi - Lc, n)];
+        v.x *= scale; v.y *= scale;
+        X[(c * nm + mi) * nth + i] = v;
+    }
+}
+
+// M2M last step, per parent P and tile of parent rows i':
+//   W_q[i'][m] = sum_{children c = (q, sz)} Sz[sz][i'] Y[c][mi][i']          (z part of the shift, per mode)
+//   F_P[i'][j'] = sum_q Sxy[q][i'][j'] sum_m W_q[i'][m] e^{+i m phi'_j'}     (inverse FFT, xy part of the shift)
+template <typename C>
+__global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict__ ce, const uint64_t* __restrict__ ckey,
+                              const C* __restrict__ Y, int Lc, int nthp, FftPlan fp, const C* __restrict__ tw,
+                              const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, C* __restrict__ Fp) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_child[4][2];
+    const int n = fp.n, nm = 2 * Lc + 1;
+    const int64_t Kp = (int64_t)nthp * n;
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + RT * n;
+    C* acc = buf1 + RT * n;
+    C* stw = acc + RT * n;
+    const int P = blockIdx.x;
+    const int c0 = cb[P], c1 = ce[P];
+    if (c0 >= c1) return;
+    const int i0 = blockIdx.y * RT;
+    const int nr = min(RT, nthp - i0);
+    if (threadIdx.x < 8) s_child[threadIdx.x >> 1][threadIdx.x & 1] = -1;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) acc[idx] = cmake<C>(0, 0);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int c = c0; c < c1; ++c) {
+            const int oct = (int)(ckey[c] & 7);
+            s_child[oct & 3][oct >> 2] = c;
+        }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        const int ca = s_child[q][0], cz = s_child[q][1];
+        if (ca < 0 && cz < 0) continue;
+        for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
+            const int r = idx % nr, mi = idx / nr;
+            C w = cmake<C>(0, 0);
+            if (ca >= 0) cfma(w, Sz[i0 + r], Y[((int64_t)ca * nm + mi) * nthp + i0 + r]);
+            if (cz >= 0) cfma(w, Sz[nthp + i0 + r], Y[((int64_t)cz * nm + mi) * nthp + i0 + r]);
+            buf0[r * n + wrap(mi - Lc, n)] = w;
+        }
+        __syncthreads();
+        const C* res = fft_rows(buf0, buf1, nr, fp, stw, true);
+        for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
+            const int r = idx / n, j = idx - r * n;
+            cfma(acc[idx], Sxy[(int64_t)q * Kp + (int64_t)(i0 + r) * n + j], res[idx]);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) Fp[(int64_t)P * Kp + (int64_t)i0 * n + idx] = acc[idx];
+}
+
+// L2L first step, per parent P, tile of parent rows i' and xy-quadrant q with children:
+//   V_q[i'][m] = (1/n) sum_j' conj(Sxy[q][i'][j']) G_P[i'][j'] e^{+i m phi'_j'},  |m| <= Lc
+//   Y[c][mi][i'] = conj(Sz[sz][i']) V_q[i'][m] for each child c = (q, sz)
+template <typename C, typename R>
+__global__ void k_l2l_fft_in(const int* __restrict__ cb, const int* __restrict__ ce, const uint64_t* __restrict__ ckey,
+                             const C* __restrict__ Gp, int Lc, int nthp, FftPlan fp, const C* __restrict__ tw,
+                             const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, R inv_n, C* __restrict__ Y) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_child[4][2];
+    const int n = fp.n, nm = 2 * Lc + 1;
+    const int64_t Kp = (int64_t)nthp * n;
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + RT * n;
+    C* stw = buf1 + RT * n;
+    const int P = blockIdx.x;
+    const int c0 = cb[P], c1 = ce[P];
+    if (c0 >= c1) return;
+    const int i0 = blockIdx.y * RT;
+    const int nr = min(RT, nthp - i0);
+    if (threadIdx.x < 8) s_child[threadIdx.x >> 1][threadIdx.x & 1] = -1;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int c = c0; c < c1; ++c) {
+            const int oct = (int)(ckey[c] & 7);
+            s_child[oct & 3][oct >> 2] = c;
+        }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        const int ca = s_child[q][0], cz = s_child[q][1];
+        if (ca < 0 && cz < 0) continue;
+        for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
+            const int64_t g = (int64_t)i0 * n + idx;
+            buf0[idx] = cmul(cconj(Sxy[(int64_t)q * Kp + g]), Gp[(int64_t)P * Kp + g]);
+        }
+        __syncthreads();
+        const C* res = fft_rows(buf0, buf1, nr, fp, stw, true);
+        for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
+            const int r = idx % nr, mi = idx / nr;
+            C v = res[r * n + wrap(mi - Lc, n)];
+            v.x *= inv_n; v.y *= inv_n;
+            if (ca >= 0) Y[((int64_t)ca * nm + mi) * nthp + i0 + r] = cmul(cconj(Sz[i0 + r]), v);
+            if (cz >= 0) Y[((int64_t)cz * nm + mi) * nthp + i0 + r] = cmul(cconj(Sz[nthp + i0 + r]), v);
+        }
+        __syncthreads();
+    }
+}
+
+// L2L last step: G[c][i][j] += sum_m H[c][mi][i] e^{-i m phi_j} for the rows (c, i) of all children.
+template <typename C>
+__global__ void k_l2l_fft_out(int64_t nrows_tot, const C* __restrict__ H, int nth, int Lc, FftPlan fp,
+                              const C* __restrict__ tw, int RB, C* __restrict__ G) {
+    extern __shared__ unsigned char smem_raw[];
+    const int n = fp.n, nm = 2 * Lc + 1;
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + RB * n;
+    C* stw = buf1 + RB * n;
+    const int64_t r0 = (int64_t)blockIdx.x * RB;
+    const int nr = (int)((nrows_tot - r0) < RB ? (nrows_tot - r0) : RB);
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
+        const int row = idx % nr, mi = idx / nr;
+        const int64_t r = r0 + row;
+        const int64_t c = r / nth;
+        const int i = (int)(r - c * nth);
+        buf0[row * n + wrap(mi - Lc, n)] = H[(c * nm + mi) * nth + i];
+    }
+    __syncthreads();
+    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
+        C* g = G + r0 * n + idx;
+        *g = cadd(*g, res[idx]);
     }
 }
 
@@ -261,152 +443,6 @@ __global__ void k_theta_map(int64_t nbox, int Lc, int nin, int nout, const R* __
     }
 }
 
-// M2M final step: F[P][i'][j'] = sum_q Sxy[q][i'][j'] sum_mi e^{i m phi'_j'} W_q[i'][mi],
-// W_q[i'][mi] = sum_{children c = (q, sz)} Sz[sz][i'] Y[c][mi][i'].  Non-leaf parents only.
-template <typename C>
-__global__ void k_m2m_out(const int* __restrict__ cb, const int* __restrict__ ce, const uint64_t* __restrict__ ckey,
-                          const C* __restrict__ Y, int Lc, int nthp, int nphp, const C* __restrict__ tw, const C* __restrict__ Sz,
-                          const C* __restrict__ Sxy, int RT, C* __restrict__ Fp) {
-    extern __shared__ unsigned char smem_raw[];
-    const int nm = 2 * Lc + 1;
-    C* W = reinterpret_cast<C*>(smem_raw);           // [4][RT][nm]
-    C* stw = W + 4 * RT * nm;                         // [nphp]
-    __shared__ int s_has[4];
-    const int P = blockIdx.x;
-    const int c0 = cb[P], c1 = ce[P];
-    if (c0 >= c1) return;
-    const int i0 = blockIdx.y * RT;
-    const int nr = min(RT, nthp - i0);
-    if (threadIdx.x < 4) s_has[threadIdx.x] = 0;
-    for (int idx = threadIdx.x; idx < 4 * RT * nm; idx += blockDim.x) W[idx] = cmake<C>(0, 0);
-    for (int j = threadIdx.x; j < nphp; j += blockDim.x) stw[j] = tw[j];
-    __syncthreads();
-    for (int c = c0; c < c1; ++c) {
-        const int oct = (int)(ckey[c] & 7);
-        const int q = oct & 3, sz = oct >> 2;
-        if (threadIdx.x == 0) s_has[q] = 1;
-        for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
-            int r = idx % nr, mi = idx / nr;
-            C y = Y[((int64_t)c * nm + mi) * nthp + i0 + r];
-            cfma(W[(q * RT + r) * nm + mi], Sz[sz * nthp + i0 + r], y);
-        }
-        __syncthreads();
-    }
-    const int64_t Kp = (int64_t)nthp * nphp;
-    for (int idx = threadIdx.x; idx < nr * nphp; idx += blockDim.x) {
-        int r = idx / nphp, j = idx % nphp;
-        C acc = cmake<C>(0, 0);
-        for (int q = 0; q < 4; ++q) {
-            if (!s_has[q]) continue;
-            const C* w = W + (q * RT + r) * nm;
-            // e^{+i m phi_j} = tw[(-m j) mod n]; start at m = -Lc
-            int step = j;                       // index increment per unit m for e^{+i m phi_j}: tw[-j]
-            int kk = (int)(((int64_t)Lc * j) % nphp);   // (-(-Lc) j) ... tw index of e^{+i(-Lc) phi_j} = tw[Lc j]
-            C s = cmake<C>(0, 0);
-            for (int mi = 0; mi < nm; ++mi) {
-                cfma(s, w[mi], stw[kk]);
-                kk -= step;
-                if (kk < 0) kk += nphp;
-            }
-            cfma(acc, Sxy[(int64_t)q * Kp + (int64_t)(i0 + r) * nphp + j], s);
-        }
-        Fp[(int64_t)P * Kp + (int64_t)(i0 + r) * nphp + j] = acc;
-    }
-}
-
-// L2L first step (per parent, per xy-quadrant q present):
-//   V_q[i'][mi] = (1/nph_p) sum_j' conj(Sxy[q][i'][j']) G_P[i'][j'] e^{+i m phi'_j'}
-//   Yc[c][mi][i'] = conj(Sz[sz][i']) V_q[i'][mi] for each child c = (q, sz)
-template <typename C>
-__global__ void k_l2l_in(const int* __restrict__ cb, const int* __restrict__ ce, const uint64_t* __restrict__ ckey,
-                         const C* __restrict__ Gp, int Lc, int nthp, int nphp, const C* __restrict__ tw, const C* __restrict__ Sz,
-                         const C* __restrict__ Sxy, int RT, C* __restrict__ Y) {
-    extern __shared__ unsigned char smem_raw[];
-    const int nm = 2 * Lc + 1;
-    const int ld = nphp + 1;
-    C* rows = reinterpret_cast<C*>(smem_raw);        // [RT][ld]
-    C* stw = rows + RT * ld;
-    __shared__ int s_child[4][2];
-    const int P = blockIdx.x;
-    const int c0 = cb[P], c1 = ce[P];
-    if (c0 >= c1) return;
-    const int i0 = blockIdx.y * RT;
-    const int nr = min(RT, nthp - i0);
-    const int64_t Kp = (int64_t)nthp * nphp;
-    if (threadIdx.x < 8) s_child[threadIdx.x >> 1][threadIdx.x & 1] = -1;
-    for (int j = threadIdx.x; j < nphp; j += blockDim.x) stw[j] = tw[j];
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int c = c0; c < c1; ++c) {
-            int oct = (int)(ckey[c] & 7);
-            s_child[oct & 3][oct >> 2] = c;
-        }
-    const typename std::conditional<sizeof(C) == 8, float, double>::type inv = 1.0 / nphp;
-    for (int q = 0; q < 4; ++q) {
-        __syncthreads();
-        if (s_child[q][0] < 0 && s_child[q][1] < 0) continue;
-        for (int idx = threadIdx.x; idx < nr * nphp; idx += blockDim.x) {
-            int r = idx / nphp, j = idx % nphp;
-            int64_t g = (int64_t)(i0 + r) * nphp + j;
-            rows[r * ld + j] = cmul(cconj(Sxy[(int64_t)q * Kp + g]), Gp[(int64_t)P * Kp + g]);
-        }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
-            int r = idx % nr, mi = idx / nr;
-            int m = mi - Lc;
-            int step = ((-m) % nphp + nphp) % nphp;      // e^{+i m phi_j} = tw[(-m j) mod n]
-            int kk = 0;
-            C acc = cmake<C>(0, 0);
-            const C* row = rows + r * ld;
-            for (int j = 0; j < nphp; ++j) {
-                cfma(acc, row[j], stw[kk]);
-                kk += step;
-                if (kk >= nphp) kk -= nphp;
-            }
-            acc.x *= inv; acc.y *= inv;
-            for (int sz = 0; sz < 2; ++sz) {
-                int c = s_child[q][sz];
-                if (c < 0) continue;
-                Y[((int64_t)c * nm + mi) * nthp + i0 + r] = cmul(cconj(Sz[sz * nthp + i0 + r]), acc);
-            }
-        }
-    }
-}
-
-// L2L last step: G_c[i][j] += sum_mi H[c][mi][i] e^{-i m phi_j}
-template <typename C>
-__global__ void k_l2l_out(int64_t nbox, const C* __restrict__ H, int Lc, int nth, int nph, const C* __restrict__ tw, int RT,
-                          C* __restrict__ G) {
-    extern __shared__ unsigned char smem_raw[];
-    const int nm = 2 * Lc + 1;
-    C* h = reinterpret_cast<C*>(smem_raw);            // [RT][nm]
-    C* stw = h + RT * nm;
-    const int64_t c = blockIdx.x;
-    const int i0 = blockIdx.y * RT;
-    const int nr = min(RT, nth - i0);
-    for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
-        int r = idx % nr, mi = idx / nr;
-        h[r * nm + mi] = H[(c * nm + mi) * nth + i0 + r];
-    }
-    for (int j = threadIdx.x; j < nph; j += blockDim.x) stw[j] = tw[j];
-    __syncthreads();
-    const int64_t K = (int64_t)nth * nph;
-    for (int idx = threadIdx.x; idx < nr * nph; idx += blockDim.x) {
-        int r = idx / nph, j = idx % nph;
-        // e^{-i m phi_j} = tw[(m j) mod n], m from -Lc
-        int kk = (int)((((int64_t)(-Lc) * j) % nph + nph) % nph);
-        C acc = cmake<C>(0, 0);
-        const C* hr = h + r * nm;
-        for (int mi = 0; mi < nm; ++mi) {
-            cfma(acc, hr[mi], stw[kk]);
-            kk += j;
-            if (kk >= nph) kk -= nph;
-        }
-        int64_t g = c * K + (int64_t)(i0 + r) * nph + j;
-        G[g] = cadd(G[g], acc);
-    }
-}
-
 // ============================================================== pipeline
 template <typename R>
 static void far_pipeline(Plan& p, const void* qs_v, void* phis_v) {
@@ -415,12 +451,12 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v) {
     const C* qs = (const C*)qs_v;
     C* phis = (C*)phis_v;
     const R k = (R)p.k;
-    const size_t smem_cap = 96 * 1024;
     // ---- upward pass: C2M at every far level's leaves, M2M from the deepest level up
     for (int l = p.nlev; l >= p.top; --l) {
         FarLevel& F = p.far[l];
         TreeLevel& T = p.lev[l];
         if (T.nleaf > 0) {
+            StageTimer st(p, MLFMA_STAGE_C2M, l, 1);
             k_c2m<R, C><<<nblk(T.nleaf, 4), 128, 0, s>>>(T.nleaf, p.leaf_box + p.leaf_first[l], T.begin, T.end, T.center, p.pos,
                                                        qs, (const R*)F.dirs, F.K, k, (C*)F.F);
             MLFMA_LAUNCH_CHECK();
@@ -429,25 +465,27 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v) {
         FarLevel& Ch = p.far[l + 1];
         TreeLevel& TC = p.lev[l + 1];
         const int Lc = Ch.L, nm = 2 * Lc + 1;
-        // A: forward DFT of the children's rows
-        int RT = tile_rows(Ch.nth, (int)(40 * 1024 / sizeof(C)) - Ch.nph, Ch.nph + 1);
-        size_t sm = ((size_t)RT * (Ch.nph + 1) + Ch.nph) * sizeof(C);
-        k_dft_rows<C><<<dim3((unsigned)TC.nbox, nblk(Ch.nth, RT)), 128, sm, s>>>(TC.nbox, (const C*)Ch.F, Ch.nth, Ch.nph, Lc,
-                                                                                   1, (const C*)Ch.tw, (R)(1.0 / Ch.nph), RT,
-                                                                                   (C*)F.X, nullptr, 0);
+        StageTimer st(p, MLFMA_STAGE_M2M, l, 3);
+        const int64_t rows_c = TC.nbox * (int64_t)Ch.nth;
+        const int budget = (int)(44 * 1024 / sizeof(C));
+        // A: forward FFT of the children's rows, modes |m| <= Lc
+        int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - Ch.nph, 2 * Ch.nph);
+        size_t sm = ((size_t)2 * RB * Ch.nph + Ch.nph) * sizeof(C);
+        k_fft_fwd_rows<C, R><<<nblk(rows_c, RB), 128, sm, s>>>(rows_c, (const C*)Ch.F, Ch.nth, Lc, Ch.fft,
+                                                                  (const C*)Ch.tw, (R)(1.0 / Ch.nph), RB, (C*)F.X);
         MLFMA_LAUNCH_CHECK();
         // B: theta maps per mode
         sm = (size_t)kMapCB * Ch.nth * sizeof(C);
         k_theta_map<R, C><<<dim3(nblk(TC.nbox, kMapCB), nm), 128, sm, s>>>(TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At,
                                                                               (const C*)F.X, (C*)F.Y);
         MLFMA_LAUNCH_CHECK();
-        // C: z-shift per mode, inverse DFT, xy-shift, sum over children
-        RT = tile_rows(F.nth, (int)(40 * 1024 / sizeof(C)) - F.nph, 4 * nm);
-        sm = ((size_t)4 * RT * nm + F.nph) * sizeof(C);
-        if (sm > smem_cap) fail(MLFMA_ERR_UNSUPPORTED, "M2M tile needs %zu bytes of shared memory", sm);
-        k_m2m_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(T.child_begin, T.child_end, TC.key, (const C*)F.Y,
-                                                                              Lc, F.nth, F.nph, (const C*)F.tw, (const C*)F.Sz,
-                                                                              (const C*)F.Sxy, RT, (C*)F.F);
+        // C: z-shift per mode, inverse FFT, xy-shift, sum over children
+        int RT = tile_rows(F.nth, budget - F.nph, 3 * F.nph);
+        sm = ((size_t)3 * RT * F.nph + F.nph) * sizeof(C);
+        k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(T.child_begin, T.child_end, TC.key,
+                                                                                  (const C*)F.Y, Lc, F.nth, F.fft,
+                                                                                  (const C*)F.tw, (const C*)F.Sz,
+                                                                                  (const C*)F.Sxy, RT, (C*)F.F);
         MLFMA_LAUNCH_CHECK();
     }
     // ---- downward pass: M2L, L2L, L2O
@@ -456,6 +494,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v) {
         TreeLevel& T = p.lev[l];
         TreeLevel& TP = p.lev[l - 1];
         {
+            StageTimer st(p, MLFMA_STAGE_M2L, l, 1);
             int tb = (int)std::min<int64_t>(256, ((F.K + 31) / 32) * 32);
             int ny = nblk(F.K, tb);
             k_m2l<R, C><<<dim3((unsigned)TP.nbox, ny), tb, 0, s>>>(TP.child_begin, TP.child_end, TP.coll, T.ijk, p.off343,
@@ -465,24 +504,27 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v) {
         if (l > p.top) {
             FarLevel& Pf = p.far[l - 1];
             const int Lc = F.L, nm = 2 * Lc + 1;
-            int RT = tile_rows(Pf.nth, (int)(40 * 1024 / sizeof(C)) - Pf.nph, Pf.nph + 1);
-            size_t sm = ((size_t)RT * (Pf.nph + 1) + Pf.nph) * sizeof(C);
-            k_l2l_in<C><<<dim3((unsigned)TP.nbox, nblk(Pf.nth, RT)), 128, sm, s>>>(TP.child_begin, TP.child_end, T.key,
-                                                                                   (const C*)Pf.G, Lc, Pf.nth, Pf.nph,
-                                                                                   (const C*)Pf.tw, (const C*)Pf.Sz,
-                                                                                   (const C*)Pf.Sxy, RT, (C*)Pf.Y);
+            StageTimer st(p, MLFMA_STAGE_L2L, l, 3);
+            const int budget = (int)(44 * 1024 / sizeof(C));
+            int RT = tile_rows(Pf.nth, budget - Pf.nph, 2 * Pf.nph);
+            size_t sm = ((size_t)2 * RT * Pf.nph + Pf.nph) * sizeof(C);
+            k_l2l_fft_in<C, R><<<dim3((unsigned)TP.nbox, nblk(Pf.nth, RT)), 128, sm, s>>>(
+                TP.child_begin, TP.child_end, T.key, (const C*)Pf.G, Lc, Pf.nth, Pf.fft, (const C*)Pf.tw, (const C*)Pf.Sz,
+                (const C*)Pf.Sxy, RT, (R)(1.0 / Pf.nph), (C*)Pf.Y);
             MLFMA_LAUNCH_CHECK();
             sm = (size_t)kMapCB * Pf.nth * sizeof(C);
             k_theta_map<R, C><<<dim3(nblk(T.nbox, kMapCB), nm), 128, sm, s>>>(T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt,
                                                                                 (const C*)Pf.Y, (C*)Pf.X);
             MLFMA_LAUNCH_CHECK();
-            RT = tile_rows(F.nth, (int)(40 * 1024 / sizeof(C)) - F.nph, nm);
-            sm = ((size_t)RT * nm + F.nph) * sizeof(C);
-            k_l2l_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(T.nbox, (const C*)Pf.X, Lc, F.nth, F.nph,
-                                                                                  (const C*)F.tw, RT, (C*)F.G);
+            const int64_t rows_c = T.nbox * (int64_t)F.nth;
+            int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * F.nph);
+            sm = ((size_t)2 * RB * F.nph + F.nph) * sizeof(C);
+            k_l2l_fft_out<C><<<nblk(rows_c, RB), 128, sm, s>>>(rows_c, (const C*)Pf.X, F.nth, Lc, F.fft, (const C*)F.tw, RB,
+                                                                (C*)F.G);
             MLFMA_LAUNCH_CHECK();
         }
         if (T.nleaf > 0) {
+            StageTimer st(p, MLFMA_STAGE_L2O, l, 1);
             k_l2o<R, C><<<nblk(T.nleaf, 4), 128, 0, s>>>(T.nleaf, p.leaf_box + p.leaf_first[l], T.begin, T.end, T.center, p.pos,
                                                        (const R*)F.dirs, F.K, k, (const C*)F.G, phis);
             MLFMA_LAUNCH_CHECK();

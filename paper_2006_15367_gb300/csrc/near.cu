@@ -143,6 +143,7 @@ static void near_apply(Plan& p, const void* qs, void* phis) {
         LR.center[l] = l <= p.nlev ? p.lev[l].center : nullptr;
     }
     const int64_t nl = p.nleaf_total;
+    StageTimer st(p, MLFMA_STAGE_P2P, 0, 1);
     k_p2p<R, C><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos,
                                                    (const C*)qs, (R)(p.k / M_PI), (C*)phis);
     MLFMA_LAUNCH_CHECK();

@@ -4,8 +4,9 @@
 // Sec. 3.2.3 (translation operators are precomputed per level and offset), Sec. 3.2.2
 // and 3.2.4 (global interpolation / anterpolation between the grids of two levels).
 // The grid of a level with truncation L is (L+1) Gauss-Legendre nodes in cos(theta)
-// (ascending) times 2L+2 uniform phi nodes, sample p = i (2L+2) + j, weight
-// w_p = w_i 2 pi / (2L+2).  Translation operator for the box offset X = c_t - c_s:
+// (ascending) times nph uniform phi nodes (nph = smallest even 7-smooth number
+// >= 2L+2, so that the phi transforms are mixed-radix FFTs), sample p = i nph + j,
+// weight w_p = w_i 2 pi / nph.  Translation operator for the box offset X = c_t - c_s:
 //   T_X(khat) = sum_{n=0}^{L} i^n (2n+1) h_n(k|X|) P_n(khat . Xhat),
 // the diagonal plane-wave form of the Gegenbauer addition theorem.
 // Interpolation child (Lc) -> parent (Lp), per Fourier mode m (|m| <= Lc):
@@ -18,6 +19,30 @@
 #include "common.cuh"
 
 namespace mlfma {
+
+// smallest even number >= m whose prime factors are all in {2, 3, 5, 7}
+int smooth_even(int m) {
+    for (;; ++m) {
+        int t = m;
+        for (int r : {2, 3, 5, 7})
+            while (t % r == 0) t /= r;
+        if (t == 1 && m % 2 == 0) return m;
+    }
+}
+
+FftPlan make_fft_plan(int n) {
+    FftPlan p;
+    p.n = n;
+    int m = n;
+    for (int r : {7, 5, 4, 3, 2})
+        while (m % r == 0) {
+            if (p.ns >= 16) fail(MLFMA_ERR_UNSUPPORTED, "FFT length %d has too many factors", n);
+            p.r[p.ns++] = r;
+            m /= r;
+        }
+    if (m != 1) fail(MLFMA_ERR_UNSUPPORTED, "FFT length %d is not 7-smooth", n);
+    return p;
+}
 
 int truncation_L(double edge, double k, int digits, int margin) {
     double kD = k * std::sqrt(3.0) * edge;
@@ -274,7 +299,8 @@ static void build_far_levels_t(Plan& p) {
         FarLevel& F = p.far[l];
         F.L = truncation_L(p.lev[l].edge, p.k, p.digits, p.margin);
         F.nth = F.L + 1;
-        F.nph = 2 * F.L + 2;
+        F.nph = smooth_even(2 * F.L + 2);
+        F.fft = make_fft_plan(F.nph);
         F.K = (int64_t)F.nth * F.nph;
         Lmax = std::max(Lmax, F.L);
     }

@@ -244,6 +244,7 @@ def test_mlfma_adaptive_vs_direct():
 
 def test_sample_count_quadruples_per_level():
     """K_l grows about four times per level up the tree (Sec. 2, H-FMM bullet)."""
-    Ks = [mlfma.Grid(mlfma.truncation_L(0.25 * 2 ** j, K, 3)).K for j in range(8)]
+    Ks = [mlfma.Grid(mlfma.truncation_L(0.25 * 2 ** j, K, 3)).K for j in range(10)]
     ratios = [Ks[j + 1] / Ks[j] for j in range(len(Ks) - 1)]
-    assert all(r > 1.8 for r in ratios) and abs(ratios[-1] - 4.0) < 0.5
+    # the excess bandwidth O((kD)^(1/3)) makes the ratio approach 4 from below
+    assert all(r > 1.5 for r in ratios) and ratios[-1] > ratios[0] and abs(ratios[-1] - 4.0) < 0.3
