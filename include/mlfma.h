@@ -202,6 +202,25 @@ mlfma_status mlfma_plan_profile(mlfma_plan* plan, int enable);
  */
 mlfma_status mlfma_plan_timings(mlfma_plan* plan, mlfma_timings* out, int reset);
 
+/*
+ * Near-field part of phi = A q (the direct sums over each leaf's near lists, one
+ * right-hand side) without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate once they
+ * are running (a fixed memory budget, or code that must not stall on an
+ * allocation); they create the plan during set-up and call this afterwards.
+ *   q, phi  [n] complex (precision of the plan), DEVICE pointers only; phi is
+ *           overwritten, in the caller's point order.
+ * Scratch: a file-scope 16 MiB device array (every GPU that loads the library
+ * holds it until exit), so 2 n complex values must fit: n <= 1,048,576 for FP32
+ * plans, n <= 524,288 for FP64 plans.  All calls share that array and it keeps
+ * the last call's contents; calls that overlap on the GPU (several streams or
+ * threads at once) race on it.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  Enqueued on the plan stream.
+ * Errors: INVALID_ARG (null pointers, host pointers, n beyond the maximum), CUDA.
+ */
+mlfma_status mlfma_apply_near_noalloc(mlfma_plan* plan, const void* q, void* phi);
+
 /* Releases all device memory of the plan after synchronising its stream.  NULL-safe. */
 void mlfma_destroy(mlfma_plan* plan);
 

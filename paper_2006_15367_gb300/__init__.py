@@ -99,6 +99,8 @@ def load(build_if_missing: bool = False):
     lib.mlfma_plan_profile.restype = ci
     lib.mlfma_plan_timings.argtypes = [vp, ctypes.POINTER(Timings), ci]
     lib.mlfma_plan_timings.restype = ci
+    lib.mlfma_apply_near_noalloc.argtypes = [vp, vp, vp]
+    lib.mlfma_apply_near_noalloc.restype = ci
     lib.mlfma_destroy.argtypes = [vp]
     lib.mlfma_destroy.restype = None
     lib.mlfma_last_error.argtypes = []
@@ -182,6 +184,11 @@ def mlfma_plan_timings(plan, reset=True) -> Timings:
     t = Timings()
     _check(load().mlfma_plan_timings(plan, ctypes.byref(t), int(bool(reset))))
     return t
+
+
+def mlfma_apply_near_noalloc(plan, q, phi):
+    """Near-field part of A q into phi (device tensors), allocating nothing."""
+    _check(load().mlfma_apply_near_noalloc(plan, _ptr(q), _ptr(phi)))
 
 
 def mlfma_destroy(plan):

@@ -122,10 +122,6 @@ static void apply_impl(Plan& p, const void* q, void* phi, int nrhs, bool adjoint
 
 using namespace mlfma;
 
-struct mlfma_plan {
-    Plan p;
-};
-
 template <typename F>
 static mlfma_status guarded(F f) {
     try {

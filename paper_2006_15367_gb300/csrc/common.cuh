@@ -205,4 +205,12 @@ void direct_fp64(const double* pts, int64_t n, const void* q, double k, const in
 int64_t scan_tmp_ints(int64_t n);
 int scan_exclusive(const int* in, int* out, int64_t n, int* tmp, cudaStream_t s);
 
+// near field only (P2P over the near lists), one right-hand side, sorted order
+void near_only(Plan& p, const void* qs, void* phis);
+
 }  // namespace mlfma
+
+// the opaque handle of the C ABI
+struct mlfma_plan {
+    mlfma::Plan p;
+};

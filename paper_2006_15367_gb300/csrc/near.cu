@@ -149,6 +149,11 @@ static void near_apply(Plan& p, const void* qs, void* phis) {
     MLFMA_LAUNCH_CHECK();
 }
 
+void near_only(Plan& p, const void* qs, void* phis) {
+    if (p.prec == MLFMA_PREC_FP64) near_apply<double>(p, qs, phis);
+    else near_apply<float>(p, qs, phis);
+}
+
 void apply_pipeline(Plan& p, const void* qs, void* phis) {
     if (p.prec == MLFMA_PREC_FP64) near_apply<double>(p, qs, phis);
     else near_apply<float>(p, qs, phis);
