@@ -196,6 +196,7 @@ mlfma_status mlfma_plan_create(const double* points, int64_t n, double k, int di
         build_tree(p, pts);
         build_lists(p);
         build_far_levels(p);
+        build_m2l_lists(p);
         p.near_dump = p.mem.get(p.n * csize(p));
         ensure_apply_buffers(p, 1);
         MLFMA_CUDA(cudaStreamSynchronize(p.stream));

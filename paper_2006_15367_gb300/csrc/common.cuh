@@ -97,6 +97,12 @@ struct TreeLevel {                 // one octree level (root = 1)
     int* v_src = nullptr;          // [nv]
     int64_t nv = 0;
     int64_t nleaf = 0;
+    // M2L work of the children of each box (this level acting as parent level):
+    // per box, the candidate sources with at least one far child, packed
+    // src << 32 | far-children mask << 8 | code, code = colleague slot (0..26) * 8 + source octant
+    int* m2l_off = nullptr;        // [nbox+1]
+    unsigned long long* m2l_src = nullptr;   // [m2l_n]
+    int64_t m2l_n = 0;
 };
 
 struct FftPlan {                   // mixed-radix factorisation of an FFT length (radices 2, 3, 4, 5, 7)
@@ -136,6 +142,7 @@ struct Plan {
     double x0[3] = {0, 0, 0}, scale = 0;
     int nlev = 0, top = 0;
     int* off343 = nullptr;         // [343] (dx+3)+7(dy+3)+49(dz+3) -> far-offset index 0..315, -1 if near
+    short* m2l_tab = nullptr;      // [216][9] (code, target octant) -> far-offset index, -1 if near or no target
     cudaStream_t stream = nullptr;
     Allocator mem;
     // per point (sorted order)
@@ -193,6 +200,7 @@ void build_lists(Plan& p);
 // setup.cu
 int truncation_L(double edge, double k, int digits, int margin);
 void build_far_levels(Plan& p);
+void build_m2l_lists(Plan& p);
 // far.cu / near.cu
 void apply_pipeline(Plan& p, const void* qs_r, void* phis_r);   // one right-hand side, sorted order
 void far_apply(Plan& p, const void* qs, void* phis);

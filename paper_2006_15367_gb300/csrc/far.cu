@@ -138,59 +138,91 @@ __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restric
     }
 }
 
-// ============================================================== M2L (CTA per parent: its children are the targets)
-constexpr int kMaxSrc = 26 * 8;
+// ============================================================== M2L (warp per parent: its children are the targets)
+// A CTA owns one 32-sample tile (blockIdx.y) and a run of parents (blockIdx.x).  The
+// tile's slice of the translation operators, T[316][32], is staged once in shared
+// memory; each warp then takes parents in turn, lane = sample.  Each source of the
+// parent's list is loaded once (the next one is prefetched) and applied to every child
+// it is far from: acc[t] += T_{o(s,t)}(p) F_s(p).  List entries carry the far-children
+// mask; tab[code][ct] gives the far-offset index.
+constexpr int kM2LWarps = 16;
+constexpr int kM2LParentsPerWarp = 4;
 
 template <typename R, typename C>
-__global__ void __launch_bounds__(256) k_m2l(const int* __restrict__ pcb, const int* __restrict__ pce, const int* __restrict__ pcoll,
-                                             const int* __restrict__ ijk, const int* __restrict__ off343,
-                                             const C* __restrict__ F, const C* __restrict__ T, int64_t K, C* __restrict__ G) {
-    __shared__ int s_src[kMaxSrc];
-    __shared__ signed short s_oi[kMaxSrc][8];
-    __shared__ int s_ns;
-    const int P = blockIdx.x;
-    const int t0 = pcb[P], t1 = pce[P];
-    if (t0 >= t1) return;
-    const int nt = t1 - t0;
-    if (threadIdx.x == 0) {
-        int ns = 0;
-        for (int sl = 0; sl < 27; ++sl) {
-            int q = pcoll[27 * P + sl];
-            if (q < 0 || q == P) continue;
-            for (int s = pcb[q]; s < pce[q]; ++s) s_src[ns++] = s;
-        }
-        s_ns = ns;
+__global__ void __launch_bounds__(32 * kM2LWarps) k_m2l(int64_t npar, const int* __restrict__ pcb, const int* __restrict__ pce,
+                                                       const int* __restrict__ loff, const unsigned long long* __restrict__ lsrc,
+                                                       const uint64_t* __restrict__ ckey, const short* __restrict__ tab_g,
+                                                       const C* __restrict__ F, const C* __restrict__ T, int64_t K,
+                                                       C* __restrict__ G) {
+    extern __shared__ unsigned char smem_raw[];
+    C* Ts = reinterpret_cast<C*>(smem_raw);                               // [316][32]
+    short* tab = reinterpret_cast<short*>(Ts + kNumOffsets * 32);         // [216][9]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t p0 = (int64_t)blockIdx.y * 32;
+    const int64_t P0 = (int64_t)blockIdx.x * (kM2LWarps * kM2LParentsPerWarp);
+    for (int i = threadIdx.x; i < 216 * 9; i += blockDim.x) tab[i] = tab_g[i];
+    for (int i = threadIdx.x; i < kNumOffsets * 32; i += blockDim.x) {
+        const int o = i >> 5, l = i & 31;
+        Ts[i] = p0 + l < K ? T[(int64_t)o * K + p0 + l] : cmake<C>(0, 0);
     }
     __syncthreads();
-    const int ns = s_ns;
-    for (int idx = threadIdx.x; idx < ns * 8; idx += blockDim.x) {
-        int si = idx >> 3, t = idx & 7;
-        int oi = -1;
-        if (t < nt) {
-            int s = s_src[si];
-            int dx = ijk[3 * (t0 + t)] - ijk[3 * s], dy = ijk[3 * (t0 + t) + 1] - ijk[3 * s + 1],
-                dz = ijk[3 * (t0 + t) + 2] - ijk[3 * s + 2];
-            if (max(abs(dx), max(abs(dy), abs(dz))) >= 2) oi = off343[(dx + 3) + 7 * (dy + 3) + 49 * (dz + 3)];
+    const int64_t p = p0 + lane;
+    const int64_t pp = p < K ? p : K - 1;
+    for (int pw = 0; pw < kM2LParentsPerWarp; ++pw) {
+        const int64_t P = P0 + (int64_t)pw * kM2LWarps + warp;
+        if (P >= npar) break;
+        const int t0 = pcb[P], nt = pce[P] - t0;
+        if (nt <= 0) continue;
+        int ct[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) ct[t] = t < nt ? (int)(ckey[t0 + t] & 7) : 0;
+        C acc[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[t] = cmake<C>(0, 0);
+        const int e0 = loff[P], e1 = loff[P + 1];
+        C fn = cmake<C>(0, 0);
+        unsigned long long wn = 0;
+        if (e0 < e1) {
+            wn = __ldg(lsrc + e0);
+            fn = F[(int64_t)(wn >> 32) * K + pp];
         }
-        s_oi[si][t] = (signed short)oi;
-    }
-    __syncthreads();
-    const int64_t p = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
-    if (p >= K) return;
-    C acc[8];
+        for (int e = e0; e < e1; ++e) {
+            const unsigned long long w = wn;
+            const C f = fn;
+            if (e + 1 < e1) {
+                wn = __ldg(lsrc + e + 1);
+                fn = F[(int64_t)(wn >> 32) * K + pp];
+            }
+            const unsigned lo = (unsigned)w;
+            const unsigned tmask = (lo >> 8) & 255u;
+            const short* tr = tab + (lo & 255u) * 9;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) acc[t] = cmake<C>(0, 0);
-    for (int si = 0; si < ns; ++si) {
-        const C f = F[(int64_t)s_src[si] * K + p];
+            for (int t = 0; t < 8; ++t)
+                if ((tmask >> t) & 1u) cfma(acc[t], Ts[tr[ct[t]] * 32 + lane], f);
+        }
+        if (p < K) {
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            int oi = s_oi[si][t];
-            if (oi >= 0) cfma(acc[t], T[(int64_t)oi * K + p], f);
+            for (int t = 0; t < 8; ++t)
+                if (t < nt) G[(int64_t)(t0 + t) * K + p] = acc[t];
         }
     }
-#pragma unroll
-    for (int t = 0; t < 8; ++t)
-        if (t < nt) G[(int64_t)(t0 + t) * K + p] = acc[t];
+}
+
+template <typename R, typename C>
+static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
+    const FarLevel& F = p.far[l];
+    const TreeLevel& T = p.lev[l];
+    const TreeLevel& TP = p.lev[l - 1];
+    const size_t sm = (size_t)kNumOffsets * 32 * sizeof(C) + 216 * 9 * sizeof(short);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(C) == 16]) {
+        MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr_set[sizeof(C) == 16] = true;
+    }
+    const dim3 grid(nblk(TP.nbox, kM2LWarps * kM2LParentsPerWarp), nblk(F.K, 32));
+    k_m2l<R, C><<<grid, 32 * kM2LWarps, sm, s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off, TP.m2l_src, T.key,
+                                                p.m2l_tab, (const C*)F.F, (const C*)F.T, F.K, (C*)F.G);
+    MLFMA_LAUNCH_CHECK();
 }
 
 // ============================================================== phi transforms: mixed-radix FFTs in shared memory
@@ -203,9 +235,37 @@ __device__ __forceinline__ C twid(const C* __restrict__ tw, int idx, bool inv) {
     return t;
 }
 
-template <int R, typename C>
+// e^{-2 pi i k / R} for the radices of the plan (k is a compile-time constant after unrolling)
+template <int R, typename T>
+__device__ __forceinline__ void root(int k, T& c, T& s) {
+    if (R == 2) {
+        const T cc[2] = {1, -1};
+        c = cc[k]; s = 0;
+    } else if (R == 3) {
+        const T cc[3] = {1, -0.5, -0.5};
+        const T ss[3] = {0, -0.86602540378443865, 0.86602540378443865};
+        c = cc[k]; s = ss[k];
+    } else if (R == 4) {
+        const T cc[4] = {1, 0, -1, 0};
+        const T ss[4] = {0, -1, 0, 1};
+        c = cc[k]; s = ss[k];
+    } else if (R == 5) {
+        const T cc[5] = {1, 0.30901699437494742, -0.80901699437494742, -0.80901699437494742, 0.30901699437494742};
+        const T ss[5] = {0, -0.95105651629515357, -0.58778525229247313, 0.58778525229247313, 0.95105651629515357};
+        c = cc[k]; s = ss[k];
+    } else {
+        const T cc[7] = {1, 0.62348980185873353, -0.22252093395631440, -0.90096886790241913, -0.90096886790241913,
+                         -0.22252093395631440, 0.62348980185873353};
+        const T ss[7] = {0, -0.78183148246802981, -0.97492791218182361, -0.43388373911755812, 0.43388373911755812,
+                         0.97492791218182361, 0.78183148246802981};
+        c = cc[k]; s = ss[k];
+    }
+}
+
+template <int R, bool INV, typename C>
 __device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict__ b, int j, int Ns, int n,
-                                         const C* __restrict__ tw, bool inv) {
+                                         const C* __restrict__ tw) {
+    using T = decltype(C::x);
     const int nb = n / R;
     const int k = j % Ns;
     const int tstep = n / (Ns * R);
@@ -213,16 +273,21 @@ __device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict_
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         C x = a[j + r * nb];
-        if (r > 0) x = cmul(x, twid(tw, k * r * tstep, inv));
+        if (r > 0) x = cmul(x, twid(tw, k * r * tstep, INV));
         v[r] = x;
     }
     const int idxD = (j / Ns) * Ns * R + k;
 #pragma unroll
     for (int kk = 0; kk < R; ++kk) {
-        C s = v[0];
+        C acc = v[0];
 #pragma unroll
-        for (int r = 1; r < R; ++r) cfma(s, v[r], twid(tw, ((r * kk) % R) * nb, inv));
-        b[idxD + kk * Ns] = s;
+        for (int r = 1; r < R; ++r) {
+            T c, s;
+            root<R, T>((r * kk) % R, c, s);
+            if (INV) s = -s;
+            cfma(acc, v[r], cmake<C>(c, s));
+        }
+        b[idxD + kk * Ns] = acc;
     }
 }
 
@@ -241,12 +306,22 @@ __device__ C* fft_rows(C* buf0, C* buf1, int nrows, const FftPlan& fp, const C* 
             const int row = idx / nb, j = idx - row * nb;
             const C* a = in + row * n;
             C* b = out + row * n;
-            switch (R) {
-                case 2: fft_bfly<2>(a, b, j, Ns, n, tw, inv); break;
-                case 3: fft_bfly<3>(a, b, j, Ns, n, tw, inv); break;
-                case 4: fft_bfly<4>(a, b, j, Ns, n, tw, inv); break;
-                case 5: fft_bfly<5>(a, b, j, Ns, n, tw, inv); break;
-                default: fft_bfly<7>(a, b, j, Ns, n, tw, inv); break;
+            if (inv) {
+                switch (R) {
+                    case 2: fft_bfly<2, true>(a, b, j, Ns, n, tw); break;
+                    case 3: fft_bfly<3, true>(a, b, j, Ns, n, tw); break;
+                    case 4: fft_bfly<4, true>(a, b, j, Ns, n, tw); break;
+                    case 5: fft_bfly<5, true>(a, b, j, Ns, n, tw); break;
+                    default: fft_bfly<7, true>(a, b, j, Ns, n, tw); break;
+                }
+            } else {
+                switch (R) {
+                    case 2: fft_bfly<2, false>(a, b, j, Ns, n, tw); break;
+                    case 3: fft_bfly<3, false>(a, b, j, Ns, n, tw); break;
+                    case 4: fft_bfly<4, false>(a, b, j, Ns, n, tw); break;
+                    case 5: fft_bfly<5, false>(a, b, j, Ns, n, tw); break;
+                    default: fft_bfly<7, false>(a, b, j, Ns, n, tw); break;
+                }
             }
         }
         __syncthreads();
@@ -258,189 +333,252 @@ __device__ C* fft_rows(C* buf0, C* buf1, int nrows, const FftPlan& fp, const C* 
 
 __device__ __forceinline__ int wrap(int m, int n) { return m < 0 ? m + n : m; }
 
-// M2M first step: X[c][mi][i] = scale sum_j F[c][i][j] e^{-i m phi_j}, |m| <= Lc, for the rows
-// (c, i) of all children (rows are contiguous in F).
+// shared-memory budget of one FFT CTA: small enough for several resident CTAs per SM
+constexpr size_t kFftSmemBytes = 20 * 1024;
+
+// M2M first step: X[mi][c][i] = scale sum_j F[c][i][j] e^{-i m phi_j}, |m| <= Lc, for the rows
+// r = c nth + i of all children (rows are contiguous in F; X is mode-major).
 template <typename C, typename R>
-__global__ void k_fft_fwd_rows(int64_t nrows_tot, const C* __restrict__ F, int nth, int Lc, FftPlan fp,
-                               const C* __restrict__ tw, R scale, int RB, C* __restrict__ X) {
+__global__ void k_fft_fwd_rows(int nrows_tot, const C* __restrict__ F, int Lc, FftPlan fp, const C* __restrict__ tw,
+                               R scale, int RB, C* __restrict__ X) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     C* buf1 = buf0 + RB * n;
     C* stw = buf1 + RB * n;
-    const int64_t r0 = (int64_t)blockIdx.x * RB;
-    const int nr = (int)((nrows_tot - r0) < RB ? (nrows_tot - r0) : RB);
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = F[r0 * n + idx];
+    const int r0 = blockIdx.x * RB;
+    const int nr = min(RB, nrows_tot - r0);
+    const C* src = F + (int64_t)r0 * n;
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = src[idx];
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
     for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
         const int row = idx % nr, mi = idx / nr;
-        const int64_t r = r0 + row;
-        const int64_t c = r / nth;
-        const int i = (int)(r - c * nth);
         C v = res[row * n + wrap(mi - Lc, n)];
         v.x *= scale; v.y *= scale;
-        X[(c * nm + mi) * nth + i] = v;
+        X[(int64_t)mi * nrows_tot + r0 + row] = v;
     }
 }
 
-// M2M last step, per parent P and tile of parent rows i':
-//   W_q[i'][m] = sum_{children c = (q, sz)} Sz[sz][i'] Y[c][mi][i']          (z part of the shift, per mode)
+// M2M last step, per parent P and tile of parent rows i' (the four xy-quadrants q are
+// transformed together, 4 nr rows per FFT pass):
+//   W_q[i'][m] = sum_{children c = (q, sz)} Sz[sz][i'] Y[mi][c][i']          (z part of the shift, per mode)
 //   F_P[i'][j'] = sum_q Sxy[q][i'][j'] sum_m W_q[i'][m] e^{+i m phi'_j'}     (inverse FFT, xy part of the shift)
 template <typename C>
 __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict__ ce, const uint64_t* __restrict__ ckey,
-                              const C* __restrict__ Y, int Lc, int nthp, FftPlan fp, const C* __restrict__ tw,
+                              int nbox_c, const C* __restrict__ Y, int Lc, int nthp, FftPlan fp, const C* __restrict__ tw,
                               const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, C* __restrict__ Fp) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_child[4][2];
     const int n = fp.n, nm = 2 * Lc + 1;
     const int64_t Kp = (int64_t)nthp * n;
-    C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + RT * n;
-    C* acc = buf1 + RT * n;
-    C* stw = acc + RT * n;
     const int P = blockIdx.x;
     const int c0 = cb[P], c1 = ce[P];
     if (c0 >= c1) return;
     const int i0 = blockIdx.y * RT;
     const int nr = min(RT, nthp - i0);
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + 4 * RT * n;
+    C* stw = buf1 + 4 * RT * n;
+    __shared__ int s_q[4], s_nq;
     if (threadIdx.x < 8) s_child[threadIdx.x >> 1][threadIdx.x & 1] = -1;
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) acc[idx] = cmake<C>(0, 0);
     __syncthreads();
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         for (int c = c0; c < c1; ++c) {
             const int oct = (int)(ckey[c] & 7);
             s_child[oct & 3][oct >> 2] = c;
         }
-    __syncthreads();
-    for (int q = 0; q < 4; ++q) {
-        const int ca = s_child[q][0], cz = s_child[q][1];
-        if (ca < 0 && cz < 0) continue;
-        for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
-            const int r = idx % nr, mi = idx / nr;
-            C w = cmake<C>(0, 0);
-            if (ca >= 0) cfma(w, Sz[i0 + r], Y[((int64_t)ca * nm + mi) * nthp + i0 + r]);
-            if (cz >= 0) cfma(w, Sz[nthp + i0 + r], Y[((int64_t)cz * nm + mi) * nthp + i0 + r]);
-            buf0[r * n + wrap(mi - Lc, n)] = w;
-        }
-        __syncthreads();
-        const C* res = fft_rows(buf0, buf1, nr, fp, stw, true);
-        for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
-            const int r = idx / n, j = idx - r * n;
-            cfma(acc[idx], Sxy[(int64_t)q * Kp + (int64_t)(i0 + r) * n + j], res[idx]);
-        }
-        __syncthreads();
+        int nq = 0;
+        for (int q = 0; q < 4; ++q)
+            if (s_child[q][0] >= 0 || s_child[q][1] >= 0) s_q[nq++] = q;
+        s_nq = nq;
     }
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) Fp[(int64_t)P * Kp + (int64_t)i0 * n + idx] = acc[idx];
+    __syncthreads();
+    const int nq = s_nq;
+    for (int idx = threadIdx.x; idx < nq * nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
+    __syncthreads();
+    // rows of the qi-th present quadrant occupy buf0[(qi * nr + r) * n ...]
+    for (int idx = threadIdx.x; idx < nq * nr * nm; idx += blockDim.x) {
+        const int r = idx % nr, t = idx / nr;
+        const int qi = t % nq, mi = t / nq;
+        const int q = s_q[qi];
+        const int ca = s_child[q][0], cz = s_child[q][1];
+        const C* Ym = Y + (int64_t)mi * nbox_c * nthp;
+        C w = cmake<C>(0, 0);
+        if (ca >= 0) cfma(w, Sz[i0 + r], Ym[(int64_t)ca * nthp + i0 + r]);
+        if (cz >= 0) cfma(w, Sz[nthp + i0 + r], Ym[(int64_t)cz * nthp + i0 + r]);
+        buf0[(qi * nr + r) * n + wrap(mi - Lc, n)] = w;
+    }
+    __syncthreads();
+    const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true);
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
+        const int r = idx / n, j = idx - r * n;
+        C acc = cmake<C>(0, 0);
+        for (int qi = 0; qi < nq; ++qi)
+            cfma(acc, Sxy[(int64_t)s_q[qi] * Kp + (int64_t)(i0 + r) * n + j], res[(qi * nr + r) * n + j]);
+        Fp[(int64_t)P * Kp + (int64_t)i0 * n + idx] = acc;
+    }
 }
 
-// L2L first step, per parent P, tile of parent rows i' and xy-quadrant q with children:
+// L2L first step, per parent P and tile of parent rows i' (four xy-quadrants in one FFT pass):
 //   V_q[i'][m] = (1/n) sum_j' conj(Sxy[q][i'][j']) G_P[i'][j'] e^{+i m phi'_j'},  |m| <= Lc
-//   Y[c][mi][i'] = conj(Sz[sz][i']) V_q[i'][m] for each child c = (q, sz)
+//   Y[mi][c][i'] = conj(Sz[sz][i']) V_q[i'][m] for each child c = (q, sz)
 template <typename C, typename R>
 __global__ void k_l2l_fft_in(const int* __restrict__ cb, const int* __restrict__ ce, const uint64_t* __restrict__ ckey,
-                             const C* __restrict__ Gp, int Lc, int nthp, FftPlan fp, const C* __restrict__ tw,
+                             int nbox_c, const C* __restrict__ Gp, int Lc, int nthp, FftPlan fp, const C* __restrict__ tw,
                              const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, R inv_n, C* __restrict__ Y) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_child[4][2];
     const int n = fp.n, nm = 2 * Lc + 1;
     const int64_t Kp = (int64_t)nthp * n;
-    C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + RT * n;
-    C* stw = buf1 + RT * n;
     const int P = blockIdx.x;
     const int c0 = cb[P], c1 = ce[P];
     if (c0 >= c1) return;
     const int i0 = blockIdx.y * RT;
     const int nr = min(RT, nthp - i0);
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + 4 * RT * n;
+    C* stw = buf1 + 4 * RT * n;
+    __shared__ int s_q[4], s_nq;
     if (threadIdx.x < 8) s_child[threadIdx.x >> 1][threadIdx.x & 1] = -1;
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
     __syncthreads();
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         for (int c = c0; c < c1; ++c) {
             const int oct = (int)(ckey[c] & 7);
             s_child[oct & 3][oct >> 2] = c;
         }
+        int nq = 0;
+        for (int q = 0; q < 4; ++q)
+            if (s_child[q][0] >= 0 || s_child[q][1] >= 0) s_q[nq++] = q;
+        s_nq = nq;
+    }
     __syncthreads();
-    for (int q = 0; q < 4; ++q) {
+    const int nq = s_nq;
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
+        const int64_t g = (int64_t)i0 * n + idx;
+        const C gv = Gp[(int64_t)P * Kp + g];
+        const int r = idx / n, j = idx - r * n;
+        for (int qi = 0; qi < nq; ++qi)
+            buf0[(qi * nr + r) * n + j] = cmul(cconj(Sxy[(int64_t)s_q[qi] * Kp + g]), gv);
+    }
+    __syncthreads();
+    const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true);
+    for (int idx = threadIdx.x; idx < nq * nr * nm; idx += blockDim.x) {
+        const int r = idx % nr, t = idx / nr;
+        const int qi = t % nq, mi = t / nq;
+        const int q = s_q[qi];
         const int ca = s_child[q][0], cz = s_child[q][1];
-        if (ca < 0 && cz < 0) continue;
-        for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
-            const int64_t g = (int64_t)i0 * n + idx;
-            buf0[idx] = cmul(cconj(Sxy[(int64_t)q * Kp + g]), Gp[(int64_t)P * Kp + g]);
-        }
-        __syncthreads();
-        const C* res = fft_rows(buf0, buf1, nr, fp, stw, true);
-        for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
-            const int r = idx % nr, mi = idx / nr;
-            C v = res[r * n + wrap(mi - Lc, n)];
-            v.x *= inv_n; v.y *= inv_n;
-            if (ca >= 0) Y[((int64_t)ca * nm + mi) * nthp + i0 + r] = cmul(cconj(Sz[i0 + r]), v);
-            if (cz >= 0) Y[((int64_t)cz * nm + mi) * nthp + i0 + r] = cmul(cconj(Sz[nthp + i0 + r]), v);
-        }
-        __syncthreads();
+        C v = res[(qi * nr + r) * n + wrap(mi - Lc, n)];
+        v.x *= inv_n; v.y *= inv_n;
+        C* Ym = Y + (int64_t)mi * nbox_c * nthp;
+        if (ca >= 0) Ym[(int64_t)ca * nthp + i0 + r] = cmul(cconj(Sz[i0 + r]), v);
+        if (cz >= 0) Ym[(int64_t)cz * nthp + i0 + r] = cmul(cconj(Sz[nthp + i0 + r]), v);
     }
 }
 
-// L2L last step: G[c][i][j] += sum_m H[c][mi][i] e^{-i m phi_j} for the rows (c, i) of all children.
+// L2L last step: G[c][i][j] += sum_m H[mi][c][i] e^{-i m phi_j} for the rows r = c nth + i of all children.
 template <typename C>
-__global__ void k_l2l_fft_out(int64_t nrows_tot, const C* __restrict__ H, int nth, int Lc, FftPlan fp,
-                              const C* __restrict__ tw, int RB, C* __restrict__ G) {
+__global__ void k_l2l_fft_out(int nrows_tot, const C* __restrict__ H, int Lc, FftPlan fp, const C* __restrict__ tw, int RB,
+                              C* __restrict__ G) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     C* buf1 = buf0 + RB * n;
     C* stw = buf1 + RB * n;
-    const int64_t r0 = (int64_t)blockIdx.x * RB;
-    const int nr = (int)((nrows_tot - r0) < RB ? (nrows_tot - r0) : RB);
+    const int r0 = blockIdx.x * RB;
+    const int nr = min(RB, nrows_tot - r0);
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
     __syncthreads();
     for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
         const int row = idx % nr, mi = idx / nr;
-        const int64_t r = r0 + row;
-        const int64_t c = r / nth;
-        const int i = (int)(r - c * nth);
-        buf0[row * n + wrap(mi - Lc, n)] = H[(c * nm + mi) * nth + i];
+        buf0[row * n + wrap(mi - Lc, n)] = H[(int64_t)mi * nrows_tot + r0 + row];
     }
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
-        C* g = G + r0 * n + idx;
-        *g = cadd(*g, res[idx]);
+    C* g0 = G + (int64_t)r0 * n;
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) g0[idx] = cadd(g0[idx], res[idx]);
+}
+
+// ============================================================== theta maps
+// Per Fourier mode, a batched GEMM (complex x real):
+//   out[mi][c][o] = sum_i M[|m|][i][o] in[mi][c][i],   m = mi - Lc
+// Tile BM boxes x BN outputs per CTA (BM * BN = 4096), 256 threads, 4 x 4 per thread,
+// reduction in chunks of 16 staged through shared memory.
+constexpr int kMapBK = 16;
+
+template <typename R, typename C, int BN>
+__global__ void __launch_bounds__(256) k_theta_map(int nbox, int Lc, int nin, int nout, const R* __restrict__ M,
+                                                   const C* __restrict__ in, C* __restrict__ out) {
+    constexpr int BM = 4096 / BN;
+    constexpr int TX = BN / 4;            // threads along outputs
+    __shared__ C As[kMapBK][BM + 1];
+    __shared__ R Bs[kMapBK][BN];
+    const int mi = blockIdx.z;
+    const int m = abs(mi - Lc);
+    const int c0 = blockIdx.x * BM, o0 = blockIdx.y * BN;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const C* inm = in + (int64_t)mi * nbox * nin;
+    const R* Mm = M + (int64_t)m * nin * nout;
+    C acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = cmake<C>(0, 0);
+    for (int k0 = 0; k0 < nin; k0 += kMapBK) {
+        for (int idx = threadIdx.x; idx < BM * kMapBK; idx += 256) {
+            const int cl = idx / kMapBK, kk = idx % kMapBK;
+            const int c = c0 + cl, i = k0 + kk;
+            As[kk][cl] = (c < nbox && i < nin) ? inm[(int64_t)c * nin + i] : cmake<C>(0, 0);
+        }
+        for (int idx = threadIdx.x; idx < kMapBK * BN; idx += 256) {
+            const int kk = idx / BN, ol = idx % BN;
+            const int i = k0 + kk, o = o0 + ol;
+            Bs[kk][ol] = (i < nin && o < nout) ? Mm[(int64_t)i * nout + o] : (R)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kMapBK; ++kk) {
+            C av[4];
+            R bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) crfma(acc[a][b], bv[b], av[a]);
+        }
+        __syncthreads();
+    }
+    C* outm = out + (int64_t)mi * nbox * nout;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int c = c0 + ty * 4 + a;
+        if (c >= nbox) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int o = o0 + tx * 4 + b;
+            if (o < nout) outm[(int64_t)c * nout + o] = acc[a][b];
+        }
     }
 }
 
-// theta map per mode: out[c][mi][o] = sum_in M[|m|][in][o] in[c][mi][in]
-constexpr int kMapCB = 8;
-
 template <typename R, typename C>
-__global__ void k_theta_map(int64_t nbox, int Lc, int nin, int nout, const R* __restrict__ M, const C* __restrict__ in,
-                            C* __restrict__ out) {
-    extern __shared__ unsigned char smem_raw[];
-    C* xin = reinterpret_cast<C*>(smem_raw);
-    const int mi = blockIdx.y;
+static void launch_theta_map(int64_t nbox, int Lc, int nin, int nout, const R* M, const C* in, C* out, cudaStream_t s) {
     const int nm = 2 * Lc + 1;
-    const int m = abs(mi - Lc);
-    const int64_t c0 = (int64_t)blockIdx.x * kMapCB;
-    const int nc = (int)((nbox - c0) < kMapCB ? (nbox - c0) : kMapCB);
-    for (int idx = threadIdx.x; idx < nc * nin; idx += blockDim.x) {
-        int cl = idx / nin, i = idx % nin;
-        xin[cl * nin + i] = in[((c0 + cl) * nm + mi) * nin + i];
+    if (nout <= 16 && sizeof(C) == 8) {          // the 256-box tile of complex128 would exceed 48 KB
+        k_theta_map<R, C, 16><<<dim3(nblk(nbox, 256), nblk(nout, 16), nm), 256, 0, s>>>((int)nbox, Lc, nin, nout, M, in, out);
+    } else if (nout <= 32) {
+        k_theta_map<R, C, 32><<<dim3(nblk(nbox, 128), nblk(nout, 32), nm), 256, 0, s>>>((int)nbox, Lc, nin, nout, M, in, out);
+    } else {
+        k_theta_map<R, C, 64><<<dim3(nblk(nbox, 64), nblk(nout, 64), nm), 256, 0, s>>>((int)nbox, Lc, nin, nout, M, in, out);
     }
-    __syncthreads();
-    const R* Mm = M + (int64_t)m * nin * nout;
-    for (int idx = threadIdx.x; idx < nc * nout; idx += blockDim.x) {
-        int cl = idx / nout, o = idx % nout;
-        C acc = cmake<C>(0, 0);
-        const C* x = xin + cl * nin;
-        for (int i = 0; i < nin; ++i) crfma(acc, Mm[(int64_t)i * nout + o], x[i]);
-        out[((c0 + cl) * nm + mi) * nout + o] = acc;
-    }
+    MLFMA_LAUNCH_CHECK();
 }
 
 // ============================================================== pipeline
@@ -467,23 +605,21 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v) {
         const int Lc = Ch.L, nm = 2 * Lc + 1;
         StageTimer st(p, MLFMA_STAGE_M2M, l, 3);
         const int64_t rows_c = TC.nbox * (int64_t)Ch.nth;
-        const int budget = (int)(44 * 1024 / sizeof(C));
+        const int budget = (int)(kFftSmemBytes / sizeof(C));
         // A: forward FFT of the children's rows, modes |m| <= Lc
         int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - Ch.nph, 2 * Ch.nph);
         size_t sm = ((size_t)2 * RB * Ch.nph + Ch.nph) * sizeof(C);
-        k_fft_fwd_rows<C, R><<<nblk(rows_c, RB), 128, sm, s>>>(rows_c, (const C*)Ch.F, Ch.nth, Lc, Ch.fft,
-                                                                  (const C*)Ch.tw, (R)(1.0 / Ch.nph), RB, (C*)F.X);
+        k_fft_fwd_rows<C, R><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, (const C*)Ch.F, Lc, Ch.fft, (const C*)Ch.tw,
+                                                                  (R)(1.0 / Ch.nph), RB, (C*)F.X);
         MLFMA_LAUNCH_CHECK();
         // B: theta maps per mode
-        sm = (size_t)kMapCB * Ch.nth * sizeof(C);
-        k_theta_map<R, C><<<dim3(nblk(TC.nbox, kMapCB), nm), 128, sm, s>>>(TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At,
-                                                                              (const C*)F.X, (C*)F.Y);
-        MLFMA_LAUNCH_CHECK();
+        launch_theta_map<R, C>(TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, (const C*)F.X, (C*)F.Y, s);
         // C: z-shift per mode, inverse FFT, xy-shift, sum over children
-        int RT = tile_rows(F.nth, budget - F.nph, 3 * F.nph);
-        sm = ((size_t)3 * RT * F.nph + F.nph) * sizeof(C);
+        int RT = tile_rows(F.nth, budget - F.nph, 8 * F.nph);
+        sm = ((size_t)8 * RT * F.nph + F.nph) * sizeof(C);
         k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(T.child_begin, T.child_end, TC.key,
-                                                                                  (const C*)F.Y, Lc, F.nth, F.fft,
+                                                                                  (int)TC.nbox, (const C*)F.Y, Lc, F.nth,
+                                                                                  F.fft,
                                                                                   (const C*)F.tw, (const C*)F.Sz,
                                                                                   (const C*)F.Sxy, RT, (C*)F.F);
         MLFMA_LAUNCH_CHECK();
@@ -495,31 +631,24 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v) {
         TreeLevel& TP = p.lev[l - 1];
         {
             StageTimer st(p, MLFMA_STAGE_M2L, l, 1);
-            int tb = (int)std::min<int64_t>(256, ((F.K + 31) / 32) * 32);
-            int ny = nblk(F.K, tb);
-            k_m2l<R, C><<<dim3((unsigned)TP.nbox, ny), tb, 0, s>>>(TP.child_begin, TP.child_end, TP.coll, T.ijk, p.off343,
-                                                                  (const C*)F.F, (const C*)F.T, F.K, (C*)F.G);
-            MLFMA_LAUNCH_CHECK();
+            launch_m2l<R, C>(p, l, s);
         }
         if (l > p.top) {
             FarLevel& Pf = p.far[l - 1];
             const int Lc = F.L, nm = 2 * Lc + 1;
             StageTimer st(p, MLFMA_STAGE_L2L, l, 3);
-            const int budget = (int)(44 * 1024 / sizeof(C));
-            int RT = tile_rows(Pf.nth, budget - Pf.nph, 2 * Pf.nph);
-            size_t sm = ((size_t)2 * RT * Pf.nph + Pf.nph) * sizeof(C);
+            const int budget = (int)(kFftSmemBytes / sizeof(C));
+            int RT = tile_rows(Pf.nth, budget - Pf.nph, 8 * Pf.nph);
+            size_t sm = ((size_t)8 * RT * Pf.nph + Pf.nph) * sizeof(C);
             k_l2l_fft_in<C, R><<<dim3((unsigned)TP.nbox, nblk(Pf.nth, RT)), 128, sm, s>>>(
-                TP.child_begin, TP.child_end, T.key, (const C*)Pf.G, Lc, Pf.nth, Pf.fft, (const C*)Pf.tw, (const C*)Pf.Sz,
-                (const C*)Pf.Sxy, RT, (R)(1.0 / Pf.nph), (C*)Pf.Y);
+                TP.child_begin, TP.child_end, T.key, (int)T.nbox, (const C*)Pf.G, Lc, Pf.nth, Pf.fft, (const C*)Pf.tw,
+                (const C*)Pf.Sz, (const C*)Pf.Sxy, RT, (R)(1.0 / Pf.nph), (C*)Pf.Y);
             MLFMA_LAUNCH_CHECK();
-            sm = (size_t)kMapCB * Pf.nth * sizeof(C);
-            k_theta_map<R, C><<<dim3(nblk(T.nbox, kMapCB), nm), 128, sm, s>>>(T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt,
-                                                                                (const C*)Pf.Y, (C*)Pf.X);
-            MLFMA_LAUNCH_CHECK();
+            launch_theta_map<R, C>(T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, (const C*)Pf.Y, (C*)Pf.X, s);
             const int64_t rows_c = T.nbox * (int64_t)F.nth;
             int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * F.nph);
             sm = ((size_t)2 * RB * F.nph + F.nph) * sizeof(C);
-            k_l2l_fft_out<C><<<nblk(rows_c, RB), 128, sm, s>>>(rows_c, (const C*)Pf.X, F.nth, Lc, F.fft, (const C*)F.tw, RB,
+            k_l2l_fft_out<C><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, (const C*)Pf.X, Lc, F.fft, (const C*)F.tw, RB,
                                                                 (C*)F.G);
             MLFMA_LAUNCH_CHECK();
         }

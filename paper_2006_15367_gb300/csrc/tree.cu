@@ -742,3 +742,102 @@ void build_lists(Plan& p) {
 }
 
 }  // namespace mlfma
+
+namespace mlfma {
+
+// ============================================================== M2L work lists
+// For every box P that has children at the next level: the children of P's colleagues
+// (other than P) that are far from at least one child of P, in ascending box order,
+// packed as src << 32 | far-children mask << 8 | (colleague slot * 8 + source octant).  A child t of P and a
+// source s of slot (dx, dy, dz) are far when the offset
+//   ijk_t - ijk_s = -2 (dx, dy, dz) + bits(t) - bits(s)
+// has a component of magnitude >= 2 (they are then in each other's V lists).
+__device__ __forceinline__ bool far_pair(int slot, int cs, int ct) {
+    const int d[3] = {slot % 3 - 1, (slot / 3) % 3 - 1, slot / 9 - 1};
+    int m = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) m = max(m, abs(-2 * d[a] + ((ct >> a) & 1) - ((cs >> a) & 1)));
+    return m >= 2;
+}
+
+__global__ void k_m2l_lists(int64_t nb, const int* __restrict__ coll, const int* __restrict__ cb, const int* __restrict__ ce,
+                            const uint64_t* __restrict__ ckey, const int* __restrict__ off, int* __restrict__ cnt,
+                            unsigned long long* __restrict__ out) {
+    int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (P >= nb) return;
+    int c = 0;
+    if (cb[P] < ce[P]) {
+        // colleagues in ascending box order (= ascending key order)
+        int q[27], qs[27], m = 0;
+        for (int sl = 0; sl < 27; ++sl) {
+            int v = coll[27 * P + sl];
+            if (v < 0 || v == (int)P) continue;
+            int j = m++;
+            while (j > 0 && q[j - 1] > v) { q[j] = q[j - 1]; qs[j] = qs[j - 1]; --j; }
+            q[j] = v; qs[j] = sl;
+        }
+        const int w0 = off ? off[P] : 0;
+        for (int a = 0; a < m; ++a)
+            for (int s = cb[q[a]]; s < ce[q[a]]; ++s) {
+                const int cs = (int)(ckey[s] & 7);
+                unsigned far_t = 0;   // bit t: child t of P (in box order) is far from s
+                for (int t = cb[P]; t < ce[P]; ++t)
+                    if (far_pair(qs[a], cs, (int)(ckey[t] & 7))) far_t |= 1u << (t - cb[P]);
+                if (!far_t) continue;
+                if (out)
+                    out[w0 + c] = ((unsigned long long)s << 32) | ((unsigned long long)far_t << 8) |
+                                  (unsigned long long)(qs[a] * 8 + cs);
+                ++c;
+            }
+    }
+    if (cnt) cnt[P] = c;
+}
+
+void build_m2l_lists(Plan& p) {
+    cudaStream_t s = p.stream;
+    // (code, target octant) -> far-offset index
+    std::vector<short> tab(216 * 9, -1);
+    for (int code = 0; code < 216; ++code) {
+        const int slot = code / 8, cs = code % 8;
+        const int d[3] = {slot % 3 - 1, (slot / 3) % 3 - 1, slot / 9 - 1};
+        for (int ct = 0; ct < 8; ++ct) {
+            int o[3], m = 0;
+            for (int a = 0; a < 3; ++a) {
+                o[a] = -2 * d[a] + ((ct >> a) & 1) - ((cs >> a) & 1);
+                m = std::max(m, std::abs(o[a]));
+            }
+            if (m < 2) continue;
+            // compact index of offset (dx, dy, dz) in raster order dz, dy, dx over [-3,3]^3 minus [-1,1]^3
+            int ci = 0;
+            for (int dz = -3; dz <= 3; ++dz)
+                for (int dy = -3; dy <= 3; ++dy)
+                    for (int dx = -3; dx <= 3; ++dx) {
+                        if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) <= 1) continue;
+                        if (dx == o[0] && dy == o[1] && dz == o[2]) tab[code * 9 + ct] = (short)ci;
+                        ++ci;
+                    }
+        }
+    }
+    p.m2l_tab = p.mem.make<short>(216 * 9);
+    MLFMA_CUDA(cudaMemcpyAsync(p.m2l_tab, tab.data(), tab.size() * sizeof(short), cudaMemcpyHostToDevice, s));
+    int* tmp = p.mem.make<int>(scan_tmp_ints(std::max<int64_t>(p.n, 1 << 20)) + 8);
+    for (int l = std::max(p.top, 2); p.top && l <= p.nlev; ++l) {
+        TreeLevel& P = p.lev[l - 1];
+        TreeLevel& C = p.lev[l];
+        int* cnt = p.mem.make<int>(P.nbox + 1);
+        MLFMA_CUDA(cudaMemsetAsync(cnt, 0, (P.nbox + 1) * sizeof(int), s));
+        k_m2l_lists<<<nblk(P.nbox, 128), 128, 0, s>>>(P.nbox, P.coll, P.child_begin, P.child_end, C.key, nullptr, cnt,
+                                                      nullptr);
+        MLFMA_LAUNCH_CHECK();
+        P.m2l_off = p.mem.make<int>(P.nbox + 1);
+        int tot = scan_exclusive(cnt, P.m2l_off, P.nbox + 1, tmp, s);
+        P.m2l_n = tot;
+        P.m2l_src = p.mem.make<unsigned long long>(std::max(tot, 1));
+        k_m2l_lists<<<nblk(P.nbox, 128), 128, 0, s>>>(P.nbox, P.coll, P.child_begin, P.child_end, C.key, P.m2l_off, nullptr,
+                                                      P.m2l_src);
+        MLFMA_LAUNCH_CHECK();
+    }
+    MLFMA_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace mlfma

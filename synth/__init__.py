@@ -155,6 +155,11 @@ def workload(name: str):
         pts = sphere(n, 32.0, seed=2001)
         q = complex_normal(2002, n)
         return pts, q, dict(k=K_WAVE, digits=3, leaf_max=0)
+    if name == "sphere256k":         # N = 2^18 on a sphere of radius 16 (profiling-size case, 8 levels)
+        n = 1 << 18
+        pts = sphere(n, 16.0, seed=2101)
+        q = complex_normal(2102, n)
+        return pts, q, dict(k=K_WAVE, digits=3, leaf_max=0)
     if name == "ellipsoid256k":      # N = 262,144 on the (8, 4, 2) ellipsoid
         n = 262144
         pts = ellipsoid(n, 8.0, 4.0, 2.0, seed=5001)
