@@ -166,6 +166,18 @@ mlfma_status mlfma_apply(mlfma_plan* plan, const void* q, void* phi, int nrhs);
  */
 mlfma_status mlfma_apply_adjoint(mlfma_plan* plan, const void* r, void* g, int nrhs);
 
+/*
+ * phi = A q and grad_i = grad_{r_i} phi_i, the gradient of each potential with
+ * respect to its own target position (needed for derivatives of a loss with
+ * respect to the points).  Near field: q_j e^{ikR} (ikR - 1) / R^3 (r_i - r_j)
+ * per pair; far field: the L2O sum with the extra factor ik khat_p (Sec. 3.2.5).
+ *   q     [nrhs][n] complex, device
+ *   phi   [nrhs][n] complex, device, or NULL if only the gradient is wanted
+ *   grad  [nrhs][n][3] complex, device (x, y, z components interleaved per point)
+ * Errors: INVALID_ARG (null plan/q/grad, host pointers, nrhs < 1), CUDA.
+ */
+mlfma_status mlfma_apply_grad(mlfma_plan* plan, const void* q, void* phi, void* grad, int nrhs);
+
 /* Fills *info.  INVALID_ARG on null pointers. */
 mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info);
 

@@ -89,6 +89,8 @@ def load(build_if_missing: bool = False):
     lib.mlfma_apply.restype = ci
     lib.mlfma_apply_adjoint.argtypes = [vp, vp, vp, ci]
     lib.mlfma_apply_adjoint.restype = ci
+    lib.mlfma_apply_grad.argtypes = [vp, vp, vp, vp, ci]
+    lib.mlfma_apply_grad.restype = ci
     lib.mlfma_plan_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.mlfma_plan_info.restype = ci
     lib.mlfma_plan_export.argtypes = [vp, ci, ci, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
@@ -119,12 +121,14 @@ def _check(st):
 
 
 def _ptr(x):
-    """Address of a torch tensor or numpy array (must be contiguous)."""
+    """Address of a torch tensor or numpy array (must be contiguous, no lazy conjugation)."""
     if x is None:
         return None
     if hasattr(x, "data_ptr"):
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if (hasattr(x, "is_conj") and x.is_conj()) or (hasattr(x, "is_neg") and x.is_neg()):
+            raise ValueError("tensor is a lazy conjugate/negative view; call resolve_conj() first")
         return x.data_ptr()
     if isinstance(x, np.ndarray):
         if not x.flags.c_contiguous:
@@ -153,6 +157,10 @@ def mlfma_apply(plan, q, phi, nrhs):
 
 def mlfma_apply_adjoint(plan, r, g, nrhs):
     _check(load().mlfma_apply_adjoint(plan, _ptr(r), _ptr(g), int(nrhs)))
+
+
+def mlfma_apply_grad(plan, q, phi, grad, nrhs):
+    _check(load().mlfma_apply_grad(plan, _ptr(q), _ptr(phi), _ptr(grad), int(nrhs)))
 
 
 def mlfma_plan_info(plan) -> Info:
@@ -272,7 +280,8 @@ class Plan:
             raise TypeError(f"{name} must be {self.cdtype} for precision {self.precision}")
         if x.shape[-1] != self.n or x.dim() > 2:
             raise ValueError(f"{name} must be [n] or [nrhs, n] with n = {self.n}")
-        return x.contiguous()
+        # lazy conjugate / negative views keep unconjugated storage: materialise them
+        return x.resolve_conj().resolve_neg().contiguous()
 
     def apply(self, q, out=None, adjoint=False):
         q = self._vec(q, "q")
@@ -285,6 +294,16 @@ class Plan:
 
     def adjoint(self, r, out=None):
         return self.apply(r, out, adjoint=True)
+
+    def apply_grad(self, q, want_phi=True):
+        """(phi, grad) with grad[..., i, :] = gradient of phi_i with respect to r_i."""
+        q = self._vec(q, "q")
+        nrhs = 1 if q.dim() == 1 else q.shape[0]
+        phi = self.torch.empty_like(q) if want_phi else None
+        grad = self.torch.empty(tuple(q.shape) + (3,), dtype=q.dtype, device=q.device)
+        with self.torch.cuda.device(self.device):
+            mlfma_apply_grad(self.handle, q, phi, grad, nrhs)
+        return phi, grad
 
     def info(self) -> dict:
         i = mlfma_plan_info(self.handle)
@@ -342,3 +361,61 @@ def direct_fp64(points, q, k, targets, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream(pts.device)
     mlfma_direct_fp64(pts, pts.shape[0], qq, k, tg, tg.shape[0], out, s.cuda_stream)
     return out
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+def _function():
+    import torch
+
+    class MLFMAFunction(torch.autograd.Function):
+        """phi = A(r) q with gradients for the complex charges q and the positions r.
+
+        backward (PyTorch's convention, g = grad_output):
+          q.grad = A^H g = conj(A conj(g)) = conj(psi),  psi = A conj(g)
+          r.grad = Re[conj(g) * grad phi + q * grad psi]   (per point, 3 components)
+        where grad phi and grad psi are the target-position gradients from
+        mlfma_apply_grad; the tree of the plan is kept fixed.
+        """
+
+        @staticmethod
+        def forward(ctx, q, points, plan):
+            if points is not None and points.requires_grad:
+                phi, gphi = plan.apply_grad(q)
+            else:
+                phi, gphi = plan.apply(q), None
+            ctx.plan = plan
+            ctx.has_gphi = gphi is not None
+            ctx.save_for_backward(q, gphi if gphi is not None else q.new_zeros(0))
+            return phi
+
+        @staticmethod
+        def backward(ctx, g):
+            q, gphi = ctx.saved_tensors
+            plan = ctx.plan
+            cg = torch.conj_physical(g.to(q.dtype)).contiguous()
+            want_r = ctx.needs_input_grad[1]
+            if want_r:
+                psi, gpsi = plan.apply_grad(cg)
+            else:
+                psi, gpsi = plan.apply(cg), None
+            grad_q = torch.conj(psi) if ctx.needs_input_grad[0] else None
+            grad_r = None
+            if want_r:
+                t = torch.conj(g).to(q.dtype)[..., None] * gphi + q[..., None] * gpsi
+                grad_r = t.real.to(torch.float64)
+            return grad_q, grad_r, None
+
+    return MLFMAFunction
+
+
+_MLFMAFunction = None
+
+
+def mlfma(q, points, plan):
+    """Differentiable matvec: phi = A(points) q through ``plan`` (built on ``points``)."""
+    global _MLFMAFunction
+    if _MLFMAFunction is None:
+        _MLFMAFunction = _function()
+    return _MLFMAFunction.apply(q, points, plan)

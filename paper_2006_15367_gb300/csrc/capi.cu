@@ -80,12 +80,18 @@ static void ensure_apply_buffers(Plan& p, int nrhs) {
     p.nrhs_cap = nrhs;
 }
 
-static void apply_impl(Plan& p, const void* q, void* phi, int nrhs, bool adjoint) {
-    if (!q || !phi) fail(MLFMA_ERR_INVALID_ARG, "null q or phi");
+static void apply_impl(Plan& p, const void* q, void* phi, int nrhs, bool adjoint, void* grad = nullptr) {
+    if (!q || (!phi && !grad)) fail(MLFMA_ERR_INVALID_ARG, "null q or phi");
     if (nrhs < 1) fail(MLFMA_ERR_INVALID_ARG, "nrhs must be >= 1 (got %d)", nrhs);
     const size_t bytes = (size_t)nrhs * p.n * csize(p);
-    const bool dq = is_device_ptr(q), dphi = is_device_ptr(phi);
+    const bool dq = is_device_ptr(q), dphi = phi ? is_device_ptr(phi) : true;
+    if (grad && (!dq || !dphi || !is_device_ptr(grad)))
+        fail(MLFMA_ERR_INVALID_ARG, "mlfma_apply_grad takes device pointers only");
     ensure_apply_buffers(p, nrhs);
+    if (grad && p.nrhs_grad < nrhs) {
+        p.grads = p.mem.get((size_t)3 * nrhs * p.n * csize(p));
+        p.nrhs_grad = nrhs;
+    }
     const void* qd = q;
     void* phid = phi;
     if (!dq || !dphi) {
@@ -104,10 +110,12 @@ static void apply_impl(Plan& p, const void* q, void* phi, int nrhs, bool adjoint
         permute_in(p, qd, p.qs, nrhs, adjoint);
     }
     for (int r = 0; r < nrhs; ++r)
-        apply_pipeline(p, (const char*)p.qs + (size_t)r * p.n * csize(p), (char*)p.phis + (size_t)r * p.n * csize(p));
+        apply_pipeline(p, (const char*)p.qs + (size_t)r * p.n * csize(p), (char*)p.phis + (size_t)r * p.n * csize(p),
+                       grad ? (char*)p.grads + (size_t)3 * r * p.n * csize(p) : nullptr);
     {
         StageTimer st(p, MLFMA_STAGE_PERMUTE, 0, 1);
-        permute_out(p, p.phis, phid, nrhs, adjoint);
+        if (phid) permute_out(p, p.phis, phid, nrhs, adjoint);
+        if (grad) permute_out3(p, p.grads, grad, nrhs);
     }
     if (p.profiling) p.acc.applies += nrhs;
     if (!dphi) {
@@ -222,6 +230,14 @@ mlfma_status mlfma_apply_adjoint(mlfma_plan* plan, const void* r, void* g, int n
     return guarded([&] {
         if (!plan) fail(MLFMA_ERR_INVALID_ARG, "null plan");
         apply_impl(plan->p, r, g, nrhs, true);
+    });
+}
+
+mlfma_status mlfma_apply_grad(mlfma_plan* plan, const void* q, void* phi, void* grad, int nrhs) {
+    return guarded([&] {
+        if (!plan) fail(MLFMA_ERR_INVALID_ARG, "null plan");
+        if (!grad) fail(MLFMA_ERR_INVALID_ARG, "null grad");
+        apply_impl(plan->p, q, phi, nrhs, false, grad);
     });
 }
 

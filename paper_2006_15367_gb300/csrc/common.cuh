@@ -99,7 +99,7 @@ struct TreeLevel {                 // one octree level (root = 1)
     int64_t nleaf = 0;
     // M2L work of the children of each box (this level acting as parent level):
     // per box, the candidate sources with at least one far child, packed
-    // src << 32 | far-children mask << 8 | code, code = colleague slot (0..26) * 8 + source octant
+    // (src * K) << 32 | far-children mask << 8 | code, code = colleague slot (0..26) * 8 + source octant
     int* m2l_off = nullptr;        // [nbox+1]
     unsigned long long* m2l_src = nullptr;   // [m2l_n]
     int64_t m2l_n = 0;
@@ -166,6 +166,8 @@ struct Plan {
     void* qs = nullptr;            // [nrhs_cap][n] complex, sorted order
     void* phis = nullptr;          // [nrhs_cap][n] complex, sorted order
     void* near_dump = nullptr;     // [n] complex near-field part of the last apply
+    void* grads = nullptr;         // [nrhs_grad][n][3] complex, sorted order
+    int nrhs_grad = 0;
     int nrhs_cap = 0;
     void* host_stage = nullptr;    // device staging for host pointers: [2][nrhs_stage][n] complex
     int nrhs_stage = 0;
@@ -202,8 +204,10 @@ int truncation_L(double edge, double k, int digits, int margin);
 void build_far_levels(Plan& p);
 void build_m2l_lists(Plan& p);
 // far.cu / near.cu
-void apply_pipeline(Plan& p, const void* qs_r, void* phis_r);   // one right-hand side, sorted order
-void far_apply(Plan& p, const void* qs, void* phis);
+// one right-hand side in sorted order; grads_r (nullable): [n][3] complex gradient of phi
+void apply_pipeline(Plan& p, const void* qs_r, void* phis_r, void* grads_r);
+void far_apply(Plan& p, const void* qs, void* phis, void* grads);
+void permute_out3(Plan& p, const void* gs, void* g, int nrhs);
 void permute_in(Plan& p, const void* q, void* qs, int nrhs, bool conj);
 void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj);
 void direct_fp64(const double* pts, int64_t n, const void* q, double k, const int64_t* tg, int64_t nt,

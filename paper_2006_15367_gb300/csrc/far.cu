@@ -89,11 +89,12 @@ __global__ void __launch_bounds__(128) k_c2m(int64_t nleaf, const int* __restric
 }
 
 // ============================================================== L2O (warp per leaf, lanes = point x slice)
-template <typename R, typename C>
+// GRAD: also grad phi_i += (ik/4pi) sum_p w_p (ik khat_p) e^{ik khat_p.(r_i - c_b)} G_b(p).
+template <typename R, typename C, bool GRAD>
 __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restrict__ leaf_box, const int* __restrict__ begin,
                                              const int* __restrict__ end, const double* __restrict__ center,
                                              const double* __restrict__ pos, const R* __restrict__ dirs, int64_t K, R k,
-                                             const C* __restrict__ G, C* __restrict__ phis) {
+                                             const C* __restrict__ G, C* __restrict__ phis, C* __restrict__ grads) {
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t w = (int64_t)blockIdx.x * 4 + wl;
     if (w >= nleaf) return;
@@ -116,16 +117,34 @@ __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restric
             z = (R)(pos[3 * (int64_t)j + 2] - cz);
         }
         C acc = cmake<C>(0, 0);
+        C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
         for (int64_t p = sl; p < K; p += S) {
             R ph = k * (dirs[4 * p] * x + dirs[4 * p + 1] * y + dirs[4 * p + 2] * z);
             R s, c;
             sc(ph, s, c);
             R wp = dirs[4 * p + 3];
-            cfma(acc, cmake<C>(wp * c, wp * s), Gb[p]);
+            if (!GRAD) {
+                cfma(acc, cmake<C>(wp * c, wp * s), Gb[p]);
+            } else {
+                const C term = cmul(cmake<C>(wp * c, wp * s), Gb[p]);
+                acc = cadd(acc, term);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const R d = dirs[4 * p + a];
+                    ga[a] = cadd(ga[a], cmake<C>(d * term.x, d * term.y));
+                }
+            }
         }
         for (int o = 16; o >= P; o >>= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            if (GRAD) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    ga[a].x += __shfl_xor_sync(0xffffffffu, ga[a].x, o);
+                    ga[a].y += __shfl_xor_sync(0xffffffffu, ga[a].y, o);
+                }
+            }
         }
         if (sl == 0 && tp < np) {
             // (ik / 4 pi) * acc
@@ -134,6 +153,17 @@ __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restric
             v.x += -f * acc.y;
             v.y += f * acc.x;
             phis[j] = v;
+            if (GRAD) {
+                // (ik / 4 pi) (ik) = -k^2 / (4 pi)
+                const R f2 = -k * k / (R)(4.0 * M_PI);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    C g = grads[3 * (int64_t)j + a];
+                    g.x += f2 * ga[a].x;
+                    g.y += f2 * ga[a].y;
+                    grads[3 * (int64_t)j + a] = g;
+                }
+            }
         }
     }
 }
@@ -156,18 +186,22 @@ __global__ void __launch_bounds__(32 * kM2LWarps) k_m2l(int64_t npar, const int*
                                                        C* __restrict__ G) {
     extern __shared__ unsigned char smem_raw[];
     C* Ts = reinterpret_cast<C*>(smem_raw);                               // [316][32]
-    short* tab = reinterpret_cast<short*>(Ts + kNumOffsets * 32);         // [216][9]
+    short* tab = reinterpret_cast<short*>(Ts + kNumOffsets * 32);         // [216][9]: row offset oi * 32
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p0 = (int64_t)blockIdx.y * 32;
     const int64_t P0 = (int64_t)blockIdx.x * (kM2LWarps * kM2LParentsPerWarp);
-    for (int i = threadIdx.x; i < 216 * 9; i += blockDim.x) tab[i] = tab_g[i];
+    for (int i = threadIdx.x; i < 216 * 9; i += blockDim.x) {
+        const short v = tab_g[i];
+        tab[i] = v >= 0 ? (short)(v * 32) : (short)-1;
+    }
     for (int i = threadIdx.x; i < kNumOffsets * 32; i += blockDim.x) {
         const int o = i >> 5, l = i & 31;
         Ts[i] = p0 + l < K ? T[(int64_t)o * K + p0 + l] : cmake<C>(0, 0);
     }
     __syncthreads();
     const int64_t p = p0 + lane;
-    const int64_t pp = p < K ? p : K - 1;
+    const C* Fp = F + (p < K ? p : K - 1);       // lane's sample; + (src * K) per source
+    const C* Tl = Ts + lane;
     for (int pw = 0; pw < kM2LParentsPerWarp; ++pw) {
         const int64_t P = P0 + (int64_t)pw * kM2LWarps + warp;
         if (P >= npar) break;
@@ -179,26 +213,28 @@ __global__ void __launch_bounds__(32 * kM2LWarps) k_m2l(int64_t npar, const int*
         C acc[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) acc[t] = cmake<C>(0, 0);
-        const int e0 = loff[P], e1 = loff[P + 1];
+        const unsigned long long* le = lsrc + loff[P];
+        const int ne = loff[P + 1] - loff[P];
         C fn = cmake<C>(0, 0);
         unsigned long long wn = 0;
-        if (e0 < e1) {
-            wn = __ldg(lsrc + e0);
-            fn = F[(int64_t)(wn >> 32) * K + pp];
+        if (ne > 0) {
+            wn = __ldg(le);
+            fn = Fp[(unsigned)(wn >> 32)];
         }
-        for (int e = e0; e < e1; ++e) {
-            const unsigned long long w = wn;
+        for (int e = 0; e < ne; ++e) {
+            const unsigned lo = (unsigned)wn;
             const C f = fn;
-            if (e + 1 < e1) {
-                wn = __ldg(lsrc + e + 1);
-                fn = F[(int64_t)(wn >> 32) * K + pp];
+            if (e + 1 < ne) {
+                wn = __ldg(le + e + 1);
+                fn = Fp[(unsigned)(wn >> 32)];
             }
-            const unsigned lo = (unsigned)w;
-            const unsigned tmask = (lo >> 8) & 255u;
+            const unsigned tmask = lo >> 8;
             const short* tr = tab + (lo & 255u) * 9;
 #pragma unroll
-            for (int t = 0; t < 8; ++t)
-                if ((tmask >> t) & 1u) cfma(acc[t], Ts[tr[ct[t]] * 32 + lane], f);
+            for (int t = 0; t < 8; ++t) {
+                if (t >= nt) break;
+                if ((tmask >> t) & 1u) cfma(acc[t], Tl[tr[ct[t]]], f);
+            }
         }
         if (p < K) {
 #pragma unroll
@@ -583,7 +619,7 @@ static void launch_theta_map(int64_t nbox, int Lc, int nin, int nout, const R* M
 
 // ============================================================== pipeline
 template <typename R>
-static void far_pipeline(Plan& p, const void* qs_v, void* phis_v) {
+static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v) {
     using C = typename Cx<R>::T;
     cudaStream_t s = p.stream;
     const C* qs = (const C*)qs_v;
@@ -654,17 +690,23 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v) {
         }
         if (T.nleaf > 0) {
             StageTimer st(p, MLFMA_STAGE_L2O, l, 1);
-            k_l2o<R, C><<<nblk(T.nleaf, 4), 128, 0, s>>>(T.nleaf, p.leaf_box + p.leaf_first[l], T.begin, T.end, T.center, p.pos,
-                                                       (const R*)F.dirs, F.K, k, (const C*)F.G, phis);
+            if (grads_v)
+                k_l2o<R, C, true><<<nblk(T.nleaf, 4), 128, 0, s>>>(T.nleaf, p.leaf_box + p.leaf_first[l], T.begin, T.end,
+                                                                 T.center, p.pos, (const R*)F.dirs, F.K, k, (const C*)F.G,
+                                                                 phis, (C*)grads_v);
+            else
+                k_l2o<R, C, false><<<nblk(T.nleaf, 4), 128, 0, s>>>(T.nleaf, p.leaf_box + p.leaf_first[l], T.begin, T.end,
+                                                                  T.center, p.pos, (const R*)F.dirs, F.K, k, (const C*)F.G,
+                                                                  phis, nullptr);
             MLFMA_LAUNCH_CHECK();
         }
     }
 }
 
-void far_apply(Plan& p, const void* qs, void* phis) {
+void far_apply(Plan& p, const void* qs, void* phis, void* grads) {
     if (!p.top) return;
-    if (p.prec == MLFMA_PREC_FP64) far_pipeline<double>(p, qs, phis);
-    else far_pipeline<float>(p, qs, phis);
+    if (p.prec == MLFMA_PREC_FP64) far_pipeline<double>(p, qs, phis, grads);
+    else far_pipeline<float>(p, qs, phis, grads);
 }
 
 }  // namespace mlfma

@@ -29,11 +29,12 @@ struct LevelRanges {
     const double* center[kMaxLev + 1];
 };
 
-template <typename R, typename C>
+// GRAD: also grad phi_i = sum_j q_j e^{ikR} (ikR - 1) / R^3 (r_i - r_j), written to grads[3 i + a].
+template <typename R, typename C, bool GRAD>
 __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restrict__ leaf_level, const int* __restrict__ leaf_box,
                                              const int* __restrict__ near_off, const int* __restrict__ near_lev,
                                              const int* __restrict__ near_box, LevelRanges LR, const double* __restrict__ pos,
-                                             const C* __restrict__ qs, R kpi, C* __restrict__ phis) {
+                                             const C* __restrict__ qs, R kpi, C* __restrict__ phis, C* __restrict__ grads) {
     __shared__ R sx[4][32], sy[4][32], sz[4][32];
     __shared__ C sq[4][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -58,6 +59,8 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
             z = (R)(pos[3 * (int64_t)i + 2] - cz);
         }
         C acc = cmake<C>(0, 0);
+        C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
+        const R kk = kpi * (R)M_PI;
         for (int e = s_lo; e < s_hi; ++e) {
             const int ls = near_lev[e], bs = near_box[e];
             const int u0 = LR.begin[ls][bs], u1 = LR.end[ls][bs];
@@ -80,7 +83,18 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
                             R r = r2 * inv;
                             R s, c;
                             scpi(kpi * r, s, c);
-                            cfma(acc, sq[wl][jj], cmake<C>(c * inv, s * inv));
+                            if (!GRAD) {
+                                cfma(acc, sq[wl][jj], cmake<C>(c * inv, s * inv));
+                            } else {
+                                const C qe = cmul(sq[wl][jj], cmake<C>(c * inv, s * inv));   // q e^{ikR} / R
+                                acc = cadd(acc, qe);
+                                // q e^{ikR} (ikR - 1) / R^3 = qe (ikR - 1) / R^2
+                                const R i2 = inv * inv;
+                                const C g = cmul(qe, cmake<C>(-i2, kk * r * i2));
+                                ga[0] = cadd(ga[0], cmake<C>(g.x * dx, g.y * dx));
+                                ga[1] = cadd(ga[1], cmake<C>(g.x * dy, g.y * dy));
+                                ga[2] = cadd(ga[2], cmake<C>(g.x * dz, g.y * dz));
+                            }
                         }
                     }
                 }
@@ -90,8 +104,20 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
         for (int o = 16; o >= P; o >>= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            if (GRAD) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    ga[a].x += __shfl_xor_sync(0xffffffffu, ga[a].x, o);
+                    ga[a].y += __shfl_xor_sync(0xffffffffu, ga[a].y, o);
+                }
+            }
         }
-        if (sl == 0 && tp < np) phis[i] = acc;
+        if (sl == 0 && tp < np) {
+            phis[i] = acc;
+            if (GRAD)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) grads[3 * (int64_t)i + a] = ga[a];
+        }
     }
 }
 
@@ -134,7 +160,7 @@ void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj) {
 }
 
 template <typename R>
-static void near_apply(Plan& p, const void* qs, void* phis) {
+static void near_apply(Plan& p, const void* qs, void* phis, void* grads) {
     using C = typename Cx<R>::T;
     LevelRanges LR;
     for (int l = 0; l <= kMaxLev; ++l) {
@@ -144,21 +170,43 @@ static void near_apply(Plan& p, const void* qs, void* phis) {
     }
     const int64_t nl = p.nleaf_total;
     StageTimer st(p, MLFMA_STAGE_P2P, 0, 1);
-    k_p2p<R, C><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos,
-                                                   (const C*)qs, (R)(p.k / M_PI), (C*)phis);
+    if (grads)
+        k_p2p<R, C, true><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box,
+                                                             LR, p.pos, (const C*)qs, (R)(p.k / M_PI), (C*)phis, (C*)grads);
+    else
+        k_p2p<R, C, false><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box,
+                                                              LR, p.pos, (const C*)qs, (R)(p.k / M_PI), (C*)phis, nullptr);
     MLFMA_LAUNCH_CHECK();
 }
 
 void near_only(Plan& p, const void* qs, void* phis) {
-    if (p.prec == MLFMA_PREC_FP64) near_apply<double>(p, qs, phis);
-    else near_apply<float>(p, qs, phis);
+    if (p.prec == MLFMA_PREC_FP64) near_apply<double>(p, qs, phis, nullptr);
+    else near_apply<float>(p, qs, phis, nullptr);
 }
 
-void apply_pipeline(Plan& p, const void* qs, void* phis) {
-    if (p.prec == MLFMA_PREC_FP64) near_apply<double>(p, qs, phis);
-    else near_apply<float>(p, qs, phis);
+void apply_pipeline(Plan& p, const void* qs, void* phis, void* grads) {
+    if (p.prec == MLFMA_PREC_FP64) near_apply<double>(p, qs, phis, grads);
+    else near_apply<float>(p, qs, phis, grads);
     if (p.near_dump) MLFMA_CUDA(cudaMemcpyAsync(p.near_dump, phis, p.n * csize(p), cudaMemcpyDeviceToDevice, p.stream));
-    far_apply(p, qs, phis);
+    far_apply(p, qs, phis, grads);
+}
+
+template <typename C>
+__global__ void k_permute_out3(int64_t n, int nrhs, const int* __restrict__ perm, const C* __restrict__ gs, C* __restrict__ g) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * nrhs * 3) return;
+    int64_t a = idx % 3, t = idx / 3;
+    int64_t r = t / n, i = t % n;
+    g[(r * n + perm[i]) * 3 + a] = gs[idx];
+}
+
+void permute_out3(Plan& p, const void* gs, void* g, int nrhs) {
+    int64_t tot = p.n * nrhs * 3;
+    if (p.prec == MLFMA_PREC_FP64)
+        k_permute_out3<double2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const double2*)gs, (double2*)g);
+    else
+        k_permute_out3<float2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const float2*)gs, (float2*)g);
+    MLFMA_LAUNCH_CHECK();
 }
 
 // ============================================================== FP64 direct sum at selected targets

@@ -748,7 +748,8 @@ namespace mlfma {
 // ============================================================== M2L work lists
 // For every box P that has children at the next level: the children of P's colleagues
 // (other than P) that are far from at least one child of P, in ascending box order,
-// packed as src << 32 | far-children mask << 8 | (colleague slot * 8 + source octant).  A child t of P and a
+// packed as (src * K) << 32 | far-children mask << 8 | (colleague slot * 8 + source octant),
+// src * K being the element offset of the source's samples at that level (< 2^32).  A child t of P and a
 // source s of slot (dx, dy, dz) are far when the offset
 //   ijk_t - ijk_s = -2 (dx, dy, dz) + bits(t) - bits(s)
 // has a component of magnitude >= 2 (they are then in each other's V lists).
@@ -762,7 +763,7 @@ __device__ __forceinline__ bool far_pair(int slot, int cs, int ct) {
 
 __global__ void k_m2l_lists(int64_t nb, const int* __restrict__ coll, const int* __restrict__ cb, const int* __restrict__ ce,
                             const uint64_t* __restrict__ ckey, const int* __restrict__ off, int* __restrict__ cnt,
-                            unsigned long long* __restrict__ out) {
+                            unsigned long long* __restrict__ out, int64_t K) {
     int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (P >= nb) return;
     int c = 0;
@@ -785,7 +786,7 @@ __global__ void k_m2l_lists(int64_t nb, const int* __restrict__ coll, const int*
                     if (far_pair(qs[a], cs, (int)(ckey[t] & 7))) far_t |= 1u << (t - cb[P]);
                 if (!far_t) continue;
                 if (out)
-                    out[w0 + c] = ((unsigned long long)s << 32) | ((unsigned long long)far_t << 8) |
+                    out[w0 + c] = ((unsigned long long)((int64_t)s * K) << 32) | ((unsigned long long)far_t << 8) |
                                   (unsigned long long)(qs[a] * 8 + cs);
                 ++c;
             }
@@ -826,15 +827,18 @@ void build_m2l_lists(Plan& p) {
         TreeLevel& C = p.lev[l];
         int* cnt = p.mem.make<int>(P.nbox + 1);
         MLFMA_CUDA(cudaMemsetAsync(cnt, 0, (P.nbox + 1) * sizeof(int), s));
+        if ((int64_t)C.nbox * p.far[l].K >= ((int64_t)1 << 32))
+            fail(MLFMA_ERR_UNSUPPORTED, "level %d holds %lld samples, beyond 32-bit offsets", l,
+                 (long long)((int64_t)C.nbox * p.far[l].K));
         k_m2l_lists<<<nblk(P.nbox, 128), 128, 0, s>>>(P.nbox, P.coll, P.child_begin, P.child_end, C.key, nullptr, cnt,
-                                                      nullptr);
+                                                      nullptr, p.far[l].K);
         MLFMA_LAUNCH_CHECK();
         P.m2l_off = p.mem.make<int>(P.nbox + 1);
         int tot = scan_exclusive(cnt, P.m2l_off, P.nbox + 1, tmp, s);
         P.m2l_n = tot;
         P.m2l_src = p.mem.make<unsigned long long>(std::max(tot, 1));
         k_m2l_lists<<<nblk(P.nbox, 128), 128, 0, s>>>(P.nbox, P.coll, P.child_begin, P.child_end, C.key, P.m2l_off, nullptr,
-                                                      P.m2l_src);
+                                                      P.m2l_src, p.far[l].K);
         MLFMA_LAUNCH_CHECK();
     }
     MLFMA_CUDA(cudaStreamSynchronize(s));
