@@ -69,6 +69,8 @@ typedef struct mlfma_options {
     void* (*alloc)(size_t bytes, void* stream, void* ctx);
     void (*free)(void* ptr, void* stream, void* ctx);
     void* alloc_ctx;
+    int disable_graphs;           /* 0 (default): the apply sweep is captured once per (nrhs, kind) as a
+                                     CUDA graph and replayed; 1: launch the kernels directly every time */
 } mlfma_options;
 
 /* Summary of a plan (levels are numbered from the root, level 1). */
@@ -88,6 +90,8 @@ typedef struct mlfma_info {
     int64_t near_pairs;                      /* point pairs summed directly */
     int64_t device_bytes;                    /* device memory held by the plan */
     double setup_ms;                         /* wall time of mlfma_plan_create */
+    int n_geom;                              /* geometries (1 unless created by mlfma_plan_create_batched;
+                                                per-level fields are then those of geometry 0) */
 } mlfma_info;
 
 /* Tree and list arrays that mlfma_plan_export can copy out (for verification). */
@@ -151,6 +155,19 @@ void mlfma_options_init(mlfma_options* opt);
  */
 mlfma_status mlfma_plan_create(const double* points, int64_t n, double k, int digits, int leaf_max,
                                const mlfma_options* opt, mlfma_plan** out);
+
+/*
+ * One plan for many independent geometries (each its own tree, lists and operators,
+ * same k, digits and options); an apply runs all of them, concurrently on internal
+ * streams, inside one captured CUDA graph.  Points of geometry g are
+ * points[offsets[g] .. offsets[g+1]); vectors are [nrhs][offsets[n_geom]] in that order
+ * and geometries never interact.
+ *   offsets  host [n_geom + 1], offsets[0] = 0, strictly increasing.
+ * Errors: as mlfma_plan_create; INVALID_ARG for bad offsets.  mlfma_plan_export and
+ * mlfma_apply_near_noalloc reject batched plans.
+ */
+mlfma_status mlfma_plan_create_batched(const double* points, const int64_t* offsets, int n_geom, double k, int digits,
+                                       int leaf_max, const mlfma_options* opt, mlfma_plan** out);
 
 /*
  * phi = A q: the matvec above for nrhs right-hand sides (Sec. 2, five stages +

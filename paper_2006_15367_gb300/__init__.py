@@ -36,7 +36,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 class Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("precision", ctypes.c_int), ("leaf_edge", ctypes.c_double),
                 ("max_depth", ctypes.c_int), ("digit_margin", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("disable_graphs", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -45,7 +45,8 @@ class Info(ctypes.Structure):
                 ("root_corner", ctypes.c_double * 3), ("nbox", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("nleaf", ctypes.c_int64 * (MAX_LEVELS + 1)), ("L", ctypes.c_int * (MAX_LEVELS + 1)),
                 ("K", ctypes.c_int64 * (MAX_LEVELS + 1)), ("nv", ctypes.c_int64 * (MAX_LEVELS + 1)),
-                ("near_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double)]
+                ("near_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
+                ("n_geom", ctypes.c_int)]
 
 
 STAGES = ["PERMUTE", "P2P", "C2M", "M2M", "M2L", "L2L", "L2O"]
@@ -85,6 +86,8 @@ def load(build_if_missing: bool = False):
     lib.mlfma_options_init.restype = None
     lib.mlfma_plan_create.argtypes = [vp, i64, cd, ci, ci, ctypes.POINTER(Options), ctypes.POINTER(vp)]
     lib.mlfma_plan_create.restype = ci
+    lib.mlfma_plan_create_batched.argtypes = [vp, vp, ci, cd, ci, ci, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    lib.mlfma_plan_create_batched.restype = ci
     lib.mlfma_apply.argtypes = [vp, vp, vp, ci]
     lib.mlfma_apply.restype = ci
     lib.mlfma_apply_adjoint.argtypes = [vp, vp, vp, ci]
@@ -148,6 +151,16 @@ def mlfma_plan_create(points, n, k, digits, leaf_max, options=None):
     h = ctypes.c_void_p()
     _check(load().mlfma_plan_create(_ptr(points), int(n), float(k), int(digits), int(leaf_max),
                                     ctypes.byref(options) if options is not None else None, ctypes.byref(h)))
+    return h.value
+
+
+def mlfma_plan_create_batched(points, offsets, n_geom, k, digits, leaf_max, options=None):
+    """C call: one plan for n_geom independent geometries; offsets is a host int64 array."""
+    h = ctypes.c_void_p()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    _check(load().mlfma_plan_create_batched(_ptr(points), off.ctypes.data, int(n_geom), float(k), int(digits),
+                                            int(leaf_max), ctypes.byref(options) if options is not None else None,
+                                            ctypes.byref(h)))
     return h.value
 
 
@@ -240,7 +253,7 @@ class Plan:
     """
 
     def __init__(self, points, k, digits=3, leaf_max=0, precision="fp32", leaf_edge=0.0, max_depth=12,
-                 digit_margin=1, stream=None, use_torch_allocator=True):
+                 digit_margin=1, stream=None, use_torch_allocator=True, offsets=None, graphs=True):
         import torch
         self.torch = torch
         load()
@@ -264,12 +277,19 @@ class Plan:
             o.max_depth = int(max_depth)
             o.digit_margin = int(digit_margin)
             o.stream = self.stream.cuda_stream
+            o.disable_graphs = 0 if graphs else 1
             self._alloc = None
             if use_torch_allocator:
                 self._alloc = _TorchAllocator(self.device)
                 o.alloc = self._alloc.alloc
                 o.free = self._alloc.free
-            self.handle = mlfma_plan_create(pts, self.n, self.k, digits, leaf_max, o)
+            if offsets is None:
+                self.handle = mlfma_plan_create(pts, self.n, self.k, digits, leaf_max, o)
+            else:
+                off = np.asarray(offsets, dtype=np.int64)
+                if off[-1] != self.n:
+                    raise ValueError("offsets[-1] must equal the number of points")
+                self.handle = mlfma_plan_create_batched(pts, off, off.shape[0] - 1, self.k, digits, leaf_max, o)
         self._points = pts
 
     def _vec(self, x, name):
@@ -312,7 +332,7 @@ class Plan:
                     root_edge=i.root_edge, root_corner=list(i.root_corner),
                     nbox=list(i.nbox[:nl + 1]), nleaf=list(i.nleaf[:nl + 1]), L=list(i.L[:nl + 1]),
                     K=list(i.K[:nl + 1]), nv=list(i.nv[:nl + 1]), near_pairs=i.near_pairs,
-                    device_bytes=i.device_bytes, setup_ms=i.setup_ms)
+                    device_bytes=i.device_bytes, setup_ms=i.setup_ms, n_geom=i.n_geom)
 
     def export(self, item, level=0):
         """Copies a tree/list/signature array to a host numpy array."""

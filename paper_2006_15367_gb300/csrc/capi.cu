@@ -72,58 +72,185 @@ static bool is_device_ptr(const void* ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+static void drop_graphs(Plan& p) {
+    for (auto& g : p.graphs) cudaGraphExecDestroy(g.second);
+    p.graphs.clear();
+}
+
+// Morton-order work buffers of one plan (grown only; growth invalidates captured graphs)
 static void ensure_apply_buffers(Plan& p, int nrhs) {
     if (nrhs <= p.nrhs_cap) return;
-    // buffers are only ever grown; old ones stay owned by the plan until destroy
     p.qs = p.mem.get((size_t)nrhs * p.n * csize(p));
     p.phis = p.mem.get((size_t)nrhs * p.n * csize(p));
     p.nrhs_cap = nrhs;
+    drop_graphs(p);
 }
 
-static void apply_impl(Plan& p, const void* q, void* phi, int nrhs, bool adjoint, void* grad = nullptr) {
+static void ensure_grad_buffers(Plan& p, int nrhs) {
+    if (nrhs <= p.nrhs_grad) return;
+    p.grads = p.mem.get((size_t)3 * nrhs * p.n * csize(p));
+    p.nrhs_grad = nrhs;
+    drop_graphs(p);
+}
+
+// caller-order staging of the (top-level) plan
+static void ensure_io_buffers(Plan& P, int nrhs, bool grad) {
+    if (nrhs > P.nrhs_io) {
+        P.qin = P.mem.get((size_t)nrhs * P.ntot * csize(P));
+        P.phiout = P.mem.get((size_t)nrhs * P.ntot * csize(P));
+        P.gout = nullptr;
+        P.nrhs_io = nrhs;
+        drop_graphs(P);
+    }
+    if (grad && !P.gout) {
+        P.gout = P.mem.get((size_t)3 * P.nrhs_io * P.ntot * csize(P));
+        drop_graphs(P);
+    }
+}
+
+// One plan's share of an apply on p.stream: permute the rows of qin (stride ld) into
+// Morton order, run the sweep per right-hand side, permute back into phiout / gout.
+static void sweep(Plan& p, const void* qin, void* phiout, void* gout, int64_t ld, int nrhs, bool adjoint, bool grad) {
+    ensure_apply_buffers(p, nrhs);
+    if (grad) ensure_grad_buffers(p, nrhs);
+    const size_t cs = csize(p);
+    {
+        StageTimer st(p, MLFMA_STAGE_PERMUTE, 0, 1);
+        permute_in(p, qin, p.qs, nrhs, adjoint, ld);
+    }
+    for (int r = 0; r < nrhs; ++r)
+        apply_pipeline(p, (const char*)p.qs + (size_t)r * p.n * cs, (char*)p.phis + (size_t)r * p.n * cs,
+                       grad ? (char*)p.grads + (size_t)3 * r * p.n * cs : nullptr);
+    {
+        StageTimer st(p, MLFMA_STAGE_PERMUTE, 0, 1);
+        permute_out(p, p.phis, phiout, nrhs, adjoint, ld);
+        if (grad) permute_out3(p, p.grads, gout, nrhs, ld);
+    }
+}
+
+// The whole apply of P from P.qin to P.phiout on stream s (batched plans fork their
+// geometries over the sub-streams and join back).
+static void sweep_all(Plan& P, cudaStream_t s, int nrhs, bool adjoint, bool grad) {
+    if (P.subs.empty()) {
+        cudaStream_t keep = P.stream;
+        P.stream = s;
+        try {
+            sweep(P, P.qin, P.phiout, P.gout, P.ntot, nrhs, adjoint, grad);
+        } catch (...) {
+            P.stream = keep;
+            throw;
+        }
+        P.stream = keep;
+        return;
+    }
+    const size_t cs = csize(P);
+    MLFMA_CUDA(cudaEventRecord(P.ev_fork, s));
+    for (size_t w = 0; w < P.sub_streams.size(); ++w) MLFMA_CUDA(cudaStreamWaitEvent(P.sub_streams[w], P.ev_fork, 0));
+    for (size_t g = 0; g < P.subs.size(); ++g) {
+        Plan& sp = *P.subs[g];
+        sp.stream = P.sub_streams[g % P.sub_streams.size()];
+        const int64_t o = P.sub_off[g];
+        sweep(sp, (const char*)P.qin + o * cs, (char*)P.phiout + o * cs, grad ? (char*)P.gout + 3 * o * cs : nullptr,
+              P.ntot, nrhs, adjoint, grad);
+    }
+    for (size_t w = 0; w < P.sub_streams.size(); ++w) {
+        MLFMA_CUDA(cudaEventRecord(P.sub_events[w], P.sub_streams[w]));
+        MLFMA_CUDA(cudaStreamWaitEvent(s, P.sub_events[w], 0));
+    }
+}
+
+static void run(Plan& P, int nrhs, bool adjoint, bool grad) {
+    const bool graphs = P.use_graphs && !P.profiling;
+    if (!graphs) {
+        sweep_all(P, P.stream, nrhs, adjoint, grad);
+        return;
+    }
+    const int64_t key = (int64_t)nrhs * 4 + (adjoint ? 2 : 0) + (grad ? 1 : 0);
+    auto it = P.graphs.find(key);
+    if (it == P.graphs.end()) {
+        // first call with this shape: run eagerly (this also sizes every buffer), then capture
+        sweep_all(P, P.stream, nrhs, adjoint, grad);
+        MLFMA_CUDA(cudaEventRecord(P.ev_fork, P.stream));
+        MLFMA_CUDA(cudaStreamWaitEvent(P.gstream, P.ev_fork, 0));
+        MLFMA_CUDA(cudaStreamBeginCapture(P.gstream, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t graph = nullptr;
+        try {
+            sweep_all(P, P.gstream, nrhs, adjoint, grad);
+        } catch (...) {
+            cudaStreamEndCapture(P.gstream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        MLFMA_CUDA(cudaStreamEndCapture(P.gstream, &graph));
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        MLFMA_CUDA(e);
+        P.graphs[key] = exec;
+        return;
+    }
+    MLFMA_CUDA(cudaEventRecord(P.ev_fork, P.stream));
+    MLFMA_CUDA(cudaStreamWaitEvent(P.gstream, P.ev_fork, 0));
+    MLFMA_CUDA(cudaGraphLaunch(it->second, P.gstream));
+    MLFMA_CUDA(cudaEventRecord(P.ev_join, P.gstream));
+    MLFMA_CUDA(cudaStreamWaitEvent(P.stream, P.ev_join, 0));
+}
+
+static void apply_impl(Plan& P, const void* q, void* phi, int nrhs, bool adjoint, void* grad = nullptr) {
     if (!q || (!phi && !grad)) fail(MLFMA_ERR_INVALID_ARG, "null q or phi");
     if (nrhs < 1) fail(MLFMA_ERR_INVALID_ARG, "nrhs must be >= 1 (got %d)", nrhs);
-    const size_t bytes = (size_t)nrhs * p.n * csize(p);
+    const size_t bytes = (size_t)nrhs * P.ntot * csize(P);
     const bool dq = is_device_ptr(q), dphi = phi ? is_device_ptr(phi) : true;
     if (grad && (!dq || !dphi || !is_device_ptr(grad)))
         fail(MLFMA_ERR_INVALID_ARG, "mlfma_apply_grad takes device pointers only");
-    ensure_apply_buffers(p, nrhs);
-    if (grad && p.nrhs_grad < nrhs) {
-        p.grads = p.mem.get((size_t)3 * nrhs * p.n * csize(p));
-        p.nrhs_grad = nrhs;
+    ensure_io_buffers(P, nrhs, grad != nullptr);
+    MLFMA_CUDA(cudaMemcpyAsync(P.qin, q, bytes, dq ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, P.stream));
+    run(P, nrhs, adjoint, grad != nullptr);
+    if (phi)
+        MLFMA_CUDA(cudaMemcpyAsync(phi, P.phiout, bytes, dphi ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P.stream));
+    if (grad) MLFMA_CUDA(cudaMemcpyAsync(grad, P.gout, 3 * bytes, cudaMemcpyDeviceToDevice, P.stream));
+    if (P.profiling) P.acc.applies += nrhs;
+    if (!dphi || !dq) MLFMA_CUDA(cudaStreamSynchronize(P.stream));
+}
+
+static void init_streams(Plan& P, int nsub) {
+    MLFMA_CUDA(cudaStreamCreateWithFlags(&P.gstream, cudaStreamNonBlocking));
+    MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming));
+    MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_join, cudaEventDisableTiming));
+    for (int w = 0; w < nsub; ++w) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        MLFMA_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        P.sub_streams.push_back(st);
+        MLFMA_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        P.sub_events.push_back(ev);
     }
-    const void* qd = q;
-    void* phid = phi;
-    if (!dq || !dphi) {
-        if (p.nrhs_stage < nrhs) {
-            p.host_stage = p.mem.get(2 * bytes);
-            p.nrhs_stage = nrhs;
-        }
-        if (!dq) {
-            MLFMA_CUDA(cudaMemcpyAsync(p.host_stage, q, bytes, cudaMemcpyHostToDevice, p.stream));
-            qd = p.host_stage;
-        }
-        if (!dphi) phid = (char*)p.host_stage + bytes;
+}
+
+static void release_plan(Plan& P) {
+    if (P.stream) cudaStreamSynchronize(P.stream);
+    if (P.gstream) cudaStreamSynchronize(P.gstream);
+    for (auto s : P.sub_streams) cudaStreamSynchronize(s);
+    drop_graphs(P);
+    for (auto* sp : P.subs) {
+        release_plan(*sp);
+        delete sp;
     }
-    {
-        StageTimer st(p, MLFMA_STAGE_PERMUTE, 0, 1);
-        permute_in(p, qd, p.qs, nrhs, adjoint);
-    }
-    for (int r = 0; r < nrhs; ++r)
-        apply_pipeline(p, (const char*)p.qs + (size_t)r * p.n * csize(p), (char*)p.phis + (size_t)r * p.n * csize(p),
-                       grad ? (char*)p.grads + (size_t)3 * r * p.n * csize(p) : nullptr);
-    {
-        StageTimer st(p, MLFMA_STAGE_PERMUTE, 0, 1);
-        if (phid) permute_out(p, p.phis, phid, nrhs, adjoint);
-        if (grad) permute_out3(p, p.grads, grad, nrhs);
-    }
-    if (p.profiling) p.acc.applies += nrhs;
-    if (!dphi) {
-        MLFMA_CUDA(cudaMemcpyAsync(phi, phid, bytes, cudaMemcpyDeviceToHost, p.stream));
-        MLFMA_CUDA(cudaStreamSynchronize(p.stream));
-    } else if (!dq) {
-        MLFMA_CUDA(cudaStreamSynchronize(p.stream));
-    }
+    P.subs.clear();
+    for (auto& r : P.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    P.recs.clear();
+    for (auto e : P.pool) cudaEventDestroy(e);
+    P.pool.clear();
+    for (auto s : P.sub_streams) cudaStreamDestroy(s);
+    for (auto e : P.sub_events) cudaEventDestroy(e);
+    P.sub_streams.clear();
+    P.sub_events.clear();
+    if (P.ev_fork) cudaEventDestroy(P.ev_fork);
+    if (P.ev_join) cudaEventDestroy(P.ev_join);
+    if (P.gstream) cudaStreamDestroy(P.gstream);
+    P.ev_fork = P.ev_join = nullptr;
+    P.gstream = nullptr;
+    P.mem.release_all();
 }
 
 }  // namespace mlfma
@@ -156,6 +283,54 @@ void mlfma_options_init(mlfma_options* opt) {
     opt->digit_margin = 1;
 }
 
+static mlfma_options checked_options(const mlfma_options* opt, double k, int digits, int leaf_max) {
+    if (!(k > 0.0) || !std::isfinite(k)) fail(MLFMA_ERR_INVALID_ARG, "k must be finite and > 0");
+    if (digits < 1 || digits > 12) fail(MLFMA_ERR_INVALID_ARG, "digits must be in [1, 12] (got %d)", digits);
+    if (leaf_max < 0) fail(MLFMA_ERR_INVALID_ARG, "leaf_max must be >= 0");
+    mlfma_options o;
+    mlfma_options_init(&o);
+    if (opt) {
+        if (opt->struct_size < sizeof(mlfma_options)) fail(MLFMA_ERR_INVALID_ARG, "options.struct_size too small");
+        o = *opt;
+    }
+    if (o.precision != MLFMA_PREC_FP64 && o.precision != MLFMA_PREC_FP32)
+        fail(MLFMA_ERR_INVALID_ARG, "unknown precision %d", (int)o.precision);
+    if (o.max_depth < 1 || o.max_depth > kMaxLev) fail(MLFMA_ERR_INVALID_ARG, "max_depth must be in [1, %d]", kMaxLev);
+    if (o.digit_margin < 0 || o.digit_margin > 8) fail(MLFMA_ERR_INVALID_ARG, "digit_margin must be in [0, 8]");
+    if (!std::isfinite(o.leaf_edge)) fail(MLFMA_ERR_INVALID_ARG, "leaf_edge must be finite");
+    if ((o.alloc == nullptr) != (o.free == nullptr)) fail(MLFMA_ERR_INVALID_ARG, "alloc and free must be given together");
+    return o;
+}
+
+static void configure(Plan& p, int64_t n, double k, int digits, int leaf_max, const mlfma_options& o) {
+    p.n = n;
+    p.ntot = n;
+    p.k = k;
+    p.digits = digits;
+    p.leaf_max = leaf_max;
+    p.max_depth = o.max_depth;
+    p.margin = o.digit_margin;
+    p.prec = o.precision;
+    p.leaf_edge = o.leaf_edge > 0 ? o.leaf_edge : (digits <= 4 ? 0.5 * M_PI / k : M_PI / k);
+    p.stream = (cudaStream_t)o.stream;
+    p.use_graphs = !o.disable_graphs;
+    p.mem.alloc = o.alloc;
+    p.mem.free = o.free;
+    p.mem.ctx = o.alloc_ctx;
+    p.mem.stream = p.stream;
+}
+
+// tree, lists, grids and operators of one point set (device points)
+static void build_plan(Plan& p, const double* pts) {
+    build_tree(p, pts);
+    build_lists(p);
+    build_far_levels(p);
+    build_m2l_lists(p);
+    p.near_dump = p.mem.get(p.n * csize(p));
+    ensure_apply_buffers(p, 1);
+    MLFMA_CUDA(cudaStreamSynchronize(p.stream));
+}
+
 mlfma_status mlfma_plan_create(const double* points, int64_t n, double k, int digits, int leaf_max, const mlfma_options* opt,
                                mlfma_plan** out) {
     if (out) *out = nullptr;
@@ -165,55 +340,65 @@ mlfma_status mlfma_plan_create(const double* points, int64_t n, double k, int di
         if (!points || !out) fail(MLFMA_ERR_INVALID_ARG, "null points or out");
         if (n < 1) fail(MLFMA_ERR_INVALID_ARG, "n must be >= 1 (got %lld)", (long long)n);
         if (n > (int64_t)INT32_MAX / 4) fail(MLFMA_ERR_UNSUPPORTED, "n = %lld exceeds the 32-bit index range", (long long)n);
-        if (!(k > 0.0) || !std::isfinite(k)) fail(MLFMA_ERR_INVALID_ARG, "k must be finite and > 0");
-        if (digits < 1 || digits > 12) fail(MLFMA_ERR_INVALID_ARG, "digits must be in [1, 12] (got %d)", digits);
-        if (leaf_max < 0) fail(MLFMA_ERR_INVALID_ARG, "leaf_max must be >= 0");
-        mlfma_options o;
-        mlfma_options_init(&o);
-        if (opt) {
-            if (opt->struct_size < sizeof(mlfma_options)) fail(MLFMA_ERR_INVALID_ARG, "options.struct_size too small");
-            o = *opt;
-        }
-        if (o.precision != MLFMA_PREC_FP64 && o.precision != MLFMA_PREC_FP32)
-            fail(MLFMA_ERR_INVALID_ARG, "unknown precision %d", (int)o.precision);
-        if (o.max_depth < 1 || o.max_depth > kMaxLev) fail(MLFMA_ERR_INVALID_ARG, "max_depth must be in [1, %d]", kMaxLev);
-        if (o.digit_margin < 0 || o.digit_margin > 8) fail(MLFMA_ERR_INVALID_ARG, "digit_margin must be in [0, 8]");
-        if (!std::isfinite(o.leaf_edge)) fail(MLFMA_ERR_INVALID_ARG, "leaf_edge must be finite");
-        if ((o.alloc == nullptr) != (o.free == nullptr)) fail(MLFMA_ERR_INVALID_ARG, "alloc and free must be given together");
+        const mlfma_options o = checked_options(opt, k, digits, leaf_max);
         h = new mlfma_plan();
         Plan& p = h->p;
-        p.n = n;
-        p.k = k;
-        p.digits = digits;
-        p.leaf_max = leaf_max;
-        p.max_depth = o.max_depth;
-        p.margin = o.digit_margin;
-        p.prec = o.precision;
-        p.leaf_edge = o.leaf_edge > 0 ? o.leaf_edge : (digits <= 4 ? 0.5 * M_PI / k : M_PI / k);
-        p.stream = (cudaStream_t)o.stream;
-        p.mem.alloc = o.alloc;
-        p.mem.free = o.free;
-        p.mem.ctx = o.alloc_ctx;
-        p.mem.stream = p.stream;
+        configure(p, n, k, digits, leaf_max, o);
+        init_streams(p, 0);
         const double* pts = points;
         if (!is_device_ptr(points)) {
             double* d = p.mem.make<double>(3 * n);
             MLFMA_CUDA(cudaMemcpyAsync(d, points, 3 * n * sizeof(double), cudaMemcpyHostToDevice, p.stream));
             pts = d;
         }
-        build_tree(p, pts);
-        build_lists(p);
-        build_far_levels(p);
-        build_m2l_lists(p);
-        p.near_dump = p.mem.get(p.n * csize(p));
-        ensure_apply_buffers(p, 1);
-        MLFMA_CUDA(cudaStreamSynchronize(p.stream));
+        build_plan(p, pts);
         p.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         *out = h;
     });
     if (st != MLFMA_OK && h) {
-        cudaStreamSynchronize(h->p.stream);
-        h->p.mem.release_all();
+        release_plan(h->p);
+        delete h;
+    }
+    return st;
+}
+
+mlfma_status mlfma_plan_create_batched(const double* points, const int64_t* offsets, int n_geom, double k, int digits,
+                                       int leaf_max, const mlfma_options* opt, mlfma_plan** out) {
+    if (out) *out = nullptr;
+    mlfma_plan* h = nullptr;
+    mlfma_status st = guarded([&] {
+        auto t0 = std::chrono::steady_clock::now();
+        if (!points || !offsets || !out) fail(MLFMA_ERR_INVALID_ARG, "null points, offsets or out");
+        if (n_geom < 1) fail(MLFMA_ERR_INVALID_ARG, "n_geom must be >= 1");
+        if (offsets[0] != 0) fail(MLFMA_ERR_INVALID_ARG, "offsets[0] must be 0");
+        for (int g = 0; g < n_geom; ++g)
+            if (offsets[g + 1] <= offsets[g]) fail(MLFMA_ERR_INVALID_ARG, "geometry %d has no points", g);
+        const int64_t ntot = offsets[n_geom];
+        if (ntot > (int64_t)INT32_MAX / 4) fail(MLFMA_ERR_UNSUPPORTED, "total n exceeds the 32-bit index range");
+        const mlfma_options o = checked_options(opt, k, digits, leaf_max);
+        h = new mlfma_plan();
+        Plan& P = h->p;
+        configure(P, ntot, k, digits, leaf_max, o);
+        init_streams(P, std::min(n_geom, 16));
+        const double* pts = points;
+        if (!is_device_ptr(points)) {
+            double* d = P.mem.make<double>(3 * ntot);
+            MLFMA_CUDA(cudaMemcpyAsync(d, points, 3 * ntot * sizeof(double), cudaMemcpyHostToDevice, P.stream));
+            pts = d;
+        }
+        P.sub_off.assign(offsets, offsets + n_geom + 1);
+        for (int g = 0; g < n_geom; ++g) {
+            Plan* sp = new Plan();
+            P.subs.push_back(sp);
+            configure(*sp, offsets[g + 1] - offsets[g], k, digits, leaf_max, o);
+            build_plan(*sp, pts + 3 * offsets[g]);
+        }
+        MLFMA_CUDA(cudaStreamSynchronize(P.stream));
+        P.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        *out = h;
+    });
+    if (st != MLFMA_OK && h) {
+        release_plan(h->p);
         delete h;
     }
     return st;
@@ -266,6 +451,24 @@ mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info) {
         info->near_pairs = p.near_pairs;
         info->device_bytes = (int64_t)p.mem.bytes;
         info->setup_ms = p.setup_ms;
+        info->n_geom = p.subs.empty() ? 1 : (int)p.subs.size();
+        if (!p.subs.empty()) {
+            const Plan& s0 = *p.subs[0];
+            info->nlev = s0.nlev;
+            info->top = s0.top;
+            info->leaf_edge = s0.leaf_edge;
+            info->root_edge = s0.a1;
+            for (int l = 1; l <= s0.nlev; ++l) {
+                info->nbox[l] = s0.lev[l].nbox;
+                info->nleaf[l] = s0.lev[l].nleaf;
+                info->nv[l] = s0.lev[l].nv;
+                if (s0.top && l >= s0.top) { info->L[l] = s0.far[l].L; info->K[l] = s0.far[l].K; }
+            }
+            for (const Plan* sp : p.subs) {
+                info->device_bytes += (int64_t)sp->mem.bytes;
+                info->near_pairs += sp->near_pairs;
+            }
+        }
     });
 }
 
@@ -273,6 +476,7 @@ mlfma_status mlfma_plan_export(const mlfma_plan* plan, int item, int level, void
     return guarded([&] {
         if (!plan) fail(MLFMA_ERR_INVALID_ARG, "null plan");
         const Plan& p = plan->p;
+        if (!p.subs.empty()) fail(MLFMA_ERR_INVALID_ARG, "export is not available for batched plans");
         const bool per_level = item >= MLFMA_EXPORT_BOX_KEY && item != MLFMA_EXPORT_NEAR_OFFSETS &&
                                item != MLFMA_EXPORT_NEAR_SOURCES && item != MLFMA_EXPORT_NEAR_PHI;
         if (per_level && (level < 1 || level > p.nlev)) fail(MLFMA_ERR_INVALID_ARG, "level %d outside 1..%d", level, p.nlev);
@@ -333,10 +537,7 @@ mlfma_status mlfma_direct_fp64(const double* points, int64_t n, const void* q, d
 
 void mlfma_destroy(mlfma_plan* plan) {
     if (!plan) return;
-    cudaStreamSynchronize(plan->p.stream);
-    for (auto& r : plan->p.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
-    for (auto e : plan->p.pool) cudaEventDestroy(e);
-    plan->p.mem.release_all();
+    release_plan(plan->p);
     delete plan;
 }
 
@@ -391,15 +592,26 @@ mlfma_status mlfma_plan_profile(mlfma_plan* plan, int enable) {
     return guarded([&] {
         if (!plan) fail(MLFMA_ERR_INVALID_ARG, "null plan");
         plan->p.profiling = enable != 0;
+        for (Plan* sp : plan->p.subs) sp->profiling = enable != 0;
     });
 }
 
 mlfma_status mlfma_plan_timings(mlfma_plan* plan, mlfma_timings* out, int reset) {
     return guarded([&] {
         if (!plan || !out) fail(MLFMA_ERR_INVALID_ARG, "null plan or out");
-        collect_timings(plan->p);
-        *out = plan->p.acc;
-        if (reset) memset(&plan->p.acc, 0, sizeof(plan->p.acc));
+        Plan& P = plan->p;
+        collect_timings(P);
+        for (Plan* sp : P.subs) {
+            collect_timings(*sp);
+            for (int s = 0; s < MLFMA_STAGE_COUNT; ++s) {
+                P.acc.ms[s] += sp->acc.ms[s];
+                P.acc.launches[s] += sp->acc.launches[s];
+            }
+            for (int l = 0; l <= kMaxLev; ++l) P.acc.m2l_ms[l] += sp->acc.m2l_ms[l];
+            memset(&sp->acc, 0, sizeof(sp->acc));
+        }
+        *out = P.acc;
+        if (reset) memset(&P.acc, 0, sizeof(P.acc));
     });
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <string>
 #include <type_traits>
@@ -172,6 +173,23 @@ struct Plan {
     void* host_stage = nullptr;    // device staging for host pointers: [2][nrhs_stage][n] complex
     int nrhs_stage = 0;
     double setup_ms = 0;
+    // caller-order staging of one apply: the captured graph reads q from qin and writes
+    // phiout / gout, so one graph serves every call with the same nrhs
+    void* qin = nullptr;           // [nrhs_io][ntot] complex
+    void* phiout = nullptr;        // [nrhs_io][ntot] complex
+    void* gout = nullptr;          // [nrhs_io][ntot][3] complex
+    int nrhs_io = 0;
+    int64_t ntot = 0;              // points of the plan (sum over geometries for batched plans)
+    // CUDA graphs of the apply sweep, keyed by nrhs * 4 + adjoint * 2 + grad
+    bool use_graphs = true;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::map<int64_t, cudaGraphExec_t> graphs;
+    // batched plans: independent geometries, run concurrently on sub_streams
+    std::vector<Plan*> subs;
+    std::vector<int64_t> sub_off;  // [n_geom + 1] offsets into the caller's point order
+    std::vector<cudaStream_t> sub_streams;
+    std::vector<cudaEvent_t> sub_events;
     // stage profiling (CUDA events on the plan stream)
     bool profiling = false;
     struct EventRec {
@@ -207,9 +225,10 @@ void build_m2l_lists(Plan& p);
 // one right-hand side in sorted order; grads_r (nullable): [n][3] complex gradient of phi
 void apply_pipeline(Plan& p, const void* qs_r, void* phis_r, void* grads_r);
 void far_apply(Plan& p, const void* qs, void* phis, void* grads);
-void permute_out3(Plan& p, const void* gs, void* g, int nrhs);
-void permute_in(Plan& p, const void* q, void* qs, int nrhs, bool conj);
-void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj);
+// ld: row stride of the caller-order vectors (default n)
+void permute_out3(Plan& p, const void* gs, void* g, int nrhs, int64_t ld = -1);
+void permute_in(Plan& p, const void* q, void* qs, int nrhs, bool conj, int64_t ld = -1);
+void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj, int64_t ld = -1);
 void direct_fp64(const double* pts, int64_t n, const void* q, double k, const int64_t* tg, int64_t nt,
                  void* phi, cudaStream_t s);
 

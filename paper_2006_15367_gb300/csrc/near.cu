@@ -121,41 +121,48 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
     }
 }
 
+// caller order (rows of stride ld) <-> Morton order (rows of stride n)
 template <typename C>
-__global__ void k_permute_in(int64_t n, int nrhs, const int* __restrict__ perm, const C* __restrict__ q, C* __restrict__ qs, int conj) {
+__global__ void k_permute_in(int64_t n, int nrhs, int64_t ld, const int* __restrict__ perm, const C* __restrict__ q,
+                             C* __restrict__ qs, int conj) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * nrhs) return;
     int64_t r = idx / n, i = idx % n;
-    C v = q[r * n + perm[i]];
+    C v = q[r * ld + perm[i]];
     if (conj) v.y = -v.y;
     qs[idx] = v;
 }
 
 template <typename C>
-__global__ void k_permute_out(int64_t n, int nrhs, const int* __restrict__ perm, const C* __restrict__ phis, C* __restrict__ phi, int conj) {
+__global__ void k_permute_out(int64_t n, int nrhs, int64_t ld, const int* __restrict__ perm, const C* __restrict__ phis,
+                              C* __restrict__ phi, int conj) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * nrhs) return;
     int64_t r = idx / n, i = idx % n;
     C v = phis[idx];
     if (conj) v.y = -v.y;
-    phi[r * n + perm[i]] = v;
+    phi[r * ld + perm[i]] = v;
 }
 
-void permute_in(Plan& p, const void* q, void* qs, int nrhs, bool conj) {
+void permute_in(Plan& p, const void* q, void* qs, int nrhs, bool conj, int64_t ld) {
     int64_t tot = p.n * nrhs;
+    if (ld < 0) ld = p.n;
     if (p.prec == MLFMA_PREC_FP64)
-        k_permute_in<double2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const double2*)q, (double2*)qs, conj);
+        k_permute_in<double2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, ld, p.perm, (const double2*)q, (double2*)qs, conj);
     else
-        k_permute_in<float2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const float2*)q, (float2*)qs, conj);
+        k_permute_in<float2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, ld, p.perm, (const float2*)q, (float2*)qs, conj);
     MLFMA_LAUNCH_CHECK();
 }
 
-void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj) {
+void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj, int64_t ld) {
     int64_t tot = p.n * nrhs;
+    if (ld < 0) ld = p.n;
     if (p.prec == MLFMA_PREC_FP64)
-        k_permute_out<double2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const double2*)phis, (double2*)phi, conj);
+        k_permute_out<double2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, ld, p.perm, (const double2*)phis, (double2*)phi,
+                                                                    conj);
     else
-        k_permute_out<float2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const float2*)phis, (float2*)phi, conj);
+        k_permute_out<float2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, ld, p.perm, (const float2*)phis, (float2*)phi,
+                                                                   conj);
     MLFMA_LAUNCH_CHECK();
 }
 
@@ -192,20 +199,22 @@ void apply_pipeline(Plan& p, const void* qs, void* phis, void* grads) {
 }
 
 template <typename C>
-__global__ void k_permute_out3(int64_t n, int nrhs, const int* __restrict__ perm, const C* __restrict__ gs, C* __restrict__ g) {
+__global__ void k_permute_out3(int64_t n, int nrhs, int64_t ld, const int* __restrict__ perm, const C* __restrict__ gs,
+                               C* __restrict__ g) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * nrhs * 3) return;
     int64_t a = idx % 3, t = idx / 3;
     int64_t r = t / n, i = t % n;
-    g[(r * n + perm[i]) * 3 + a] = gs[idx];
+    g[(r * ld + perm[i]) * 3 + a] = gs[idx];
 }
 
-void permute_out3(Plan& p, const void* gs, void* g, int nrhs) {
+void permute_out3(Plan& p, const void* gs, void* g, int nrhs, int64_t ld) {
     int64_t tot = p.n * nrhs * 3;
+    if (ld < 0) ld = p.n;
     if (p.prec == MLFMA_PREC_FP64)
-        k_permute_out3<double2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const double2*)gs, (double2*)g);
+        k_permute_out3<double2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, ld, p.perm, (const double2*)gs, (double2*)g);
     else
-        k_permute_out3<float2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, p.perm, (const float2*)gs, (float2*)g);
+        k_permute_out3<float2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, ld, p.perm, (const float2*)gs, (float2*)g);
     MLFMA_LAUNCH_CHECK();
 }
 

@@ -54,6 +54,7 @@ extern "C" mlfma_status mlfma_apply_near_noalloc(mlfma_plan* plan, const void* q
         mlfma::set_error("%s", "");
         if (!plan || !q || !phi) mlfma::fail(MLFMA_ERR_INVALID_ARG, "null plan, q or phi");
         mlfma::Plan& p = plan->p;
+        if (!p.subs.empty()) mlfma::fail(MLFMA_ERR_INVALID_ARG, "batched plans are not supported here");
         if (!device_pointer(q) || !device_pointer(phi))
             mlfma::fail(MLFMA_ERR_INVALID_ARG, "q and phi must be device pointers (host staging would allocate)");
         const size_t half = (size_t)p.n * mlfma::csize(p);
