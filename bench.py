@@ -151,6 +151,31 @@ def run_reference(args, ws, rank):
     return 0
 
 
+WORKLOADS = {
+    "sphere1m": "sphere N=1048576 r=32 wavelengths (k=2pi), leaf 0.25 wavelength, 9 levels, 3 digits",
+    "sphere256k": "sphere N=262144 r=16 wavelengths (k=2pi), leaf 0.25 wavelength, 8 levels, 3 digits",
+    "sphere4k": "sphere N=4096 r=2 wavelengths (k=2pi), leaf 0.25 wavelength, 5 levels, 3 digits",
+    "cubeclusters4m": "cube surface 32 wavelengths (70%) + 64 Gaussian clusters sigma 0.05 (30%), N=4194304, "
+                      "adaptive leaf_max=64, far field down to 0.25-wavelength boxes, 4 digits",
+    "ellipsoid256k": "ellipsoid (8,4,2) wavelengths N=262144, leaf 0.25 wavelength, 3 digits",
+    "batch256": "256 random ellipsoids (semi-axes U(2,16) wavelengths, N log-uniform 1000..65536) in one batched "
+                "plan, leaf 0.25 wavelength, 3 digits",
+}
+
+
+def load_case(name):
+    """(points, charges [1][n], params, offsets or None)."""
+    import synth
+    if name == "batch256":
+        geoms, sizes, axes = synth.ellipsoid_batch(256, seed=4001)
+        pts = np.concatenate(geoms)
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        q = synth.complex_normal(4002, pts.shape[0])
+        return pts, q, dict(k=synth.K_WAVE, digits=3, leaf_max=0), off
+    pts, q, prm = synth.workload(name)
+    return pts, q, prm, None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -159,9 +184,12 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu", action="store_true",
-                    help="profile-region mode: warm up, then run one apply between cudaProfilerStart/Stop and exit")
-    ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (synth.workload)")
+                    help="profile-region mode: warm up, then run one step between cudaProfilerStart/Stop and exit")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--mode", default="apply", choices=["apply", "grad"],
+                    help="apply: phi = A q; grad: forward + backward of sum |phi - t|^2 for q and the positions")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -178,41 +206,60 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    pts, q, prm = synth.workload(args.workload)
+    pts, q, prm, offsets = load_case(args.workload)
     n = pts.shape[0]
+    nrhs = args.nrhs
     ptd = torch.as_tensor(pts, device=dev)
     cdt = np.complex64 if args.precision == "fp32" else np.complex128
-    qd = torch.as_tensor(q[0].astype(cdt), device=dev)
+    Q = q[0] if nrhs == 1 else synth.complex_normal(2003, n, nrhs=nrhs)
+    qd = torch.as_tensor(Q.astype(cdt), device=dev)
     out = torch.empty_like(qd)
-    plan = mf.Plan(ptd, prm["k"], prm["digits"], precision=args.precision)
+    plan = mf.Plan(ptd, prm["k"], prm["digits"], leaf_max=prm.get("leaf_max", 0), precision=args.precision,
+                   offsets=offsets)
+    info = plan.info()
+    stream = plan.stream
+
+    if args.mode == "grad":
+        tgt = torch.as_tensor(synth.complex_normal(5003, n)[0].astype(cdt), device=dev)
+        rt = ptd.clone().requires_grad_(True)
+
+        def step():
+            qv = qd.detach().requires_grad_(True)
+            phi = mf.mlfma(qv, rt, plan)
+            loss = torch.sum(torch.abs(phi - tgt) ** 2)
+            loss.backward()
+            out.copy_(phi.detach())
+            return qv.grad
+    else:
+        def step():
+            plan.apply(qd, out)
+
     if args.ncu:
         for _ in range(2):
-            plan.apply(qd, out)
+            step()
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        plan.apply(qd, out)
+        step()
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         plan.close()
         return 0
-    info = plan.info()
-    stream = plan.stream
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     # ---- warm-up
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
-            plan.apply(qd, out)
+            step()
     torch.cuda.synchronize()
 
-    # ---- launches per apply (profiling pass, outside the timed region)
+    # ---- launches per step (profiling pass, outside the timed region)
     plan.profile(True)
-    plan.apply(qd, out)
+    step()
     tm = plan.timings(reset=True)
     plan.profile(False)
-    launches_per_apply = int(sum(tm["launches"].values()))
+    launches_per_step = int(sum(tm["launches"].values()))
 
-    # ---- timed region: K applies, L2 flushed between steps, device time by CUDA events
+    # ---- timed region: K steps, L2 flushed between steps, device time by CUDA events
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
@@ -222,7 +269,7 @@ def main():
             for i in range(args.steps):
                 flush.fill_(float(i))
                 evs[i][0].record(stream)
-                plan.apply(qd, out)
+                step()
                 evs[i][1].record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -232,84 +279,116 @@ def main():
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = n * ws / (ms / 1e3)
+    value = n * nrhs * ws / (ms / 1e3)
 
     # ---- per-stage times (CUDA events on the plan stream), same workload
     plan.profile(True)
     with torch.cuda.stream(stream):
         for i in range(args.steps):
             flush.fill_(float(i))
-            plan.apply(qd, out)
+            step()
     tm = plan.timings(reset=True)
     plan.profile(False)
-    napp = max(tm["applies"], 1)
-    stage_ms = {k: v / napp for k, v in tm["ms"].items()}
+    steps_done = max(args.steps, 1)
+    stage_ms = {k: v / steps_done for k, v in tm["ms"].items()}
 
-    # ---- end to end through the C call with pinned host buffers
-    qh = torch.empty(n, dtype=torch.complex64, pin_memory=True)
-    qh.copy_(torch.as_tensor(q[0].astype(np.complex64)))
-    ph = torch.empty(n, dtype=torch.complex64, pin_memory=True)
+    # ---- end to end: inputs from pinned host memory, result read back, inside the timed region
+    qh = torch.empty(tuple(qd.shape), dtype=qd.dtype, pin_memory=True)
+    qh.copy_(qd.cpu())
+    ph = torch.empty(tuple(qd.shape), dtype=qd.dtype, pin_memory=True)
+    if args.mode == "apply":
+        def e2e_step():
+            mf.mlfma_apply(plan.handle, qh, ph, nrhs)
+        h2d, d2h = qh.numel() * qh.element_size(), ph.numel() * ph.element_size()
+    else:
+        gh = torch.empty(tuple(qd.shape), dtype=qd.dtype, pin_memory=True)
+
+        def e2e_step():
+            qd.copy_(qh, non_blocking=True)
+            gq = step()
+            gh.copy_(gq, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        h2d, d2h = qh.numel() * qh.element_size(), gh.numel() * gh.element_size()
     for _ in range(2):
-        mf.mlfma_apply(plan.handle, qh, ph, 1)
+        e2e_step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        mf.mlfma_apply(plan.handle, qh, ph, 1)
+        e2e_step()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e = {"value": n * ws / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+    e2e = {"value": n * nrhs * ws / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h)}
 
-    # ---- accuracy: GPU FP64 direct sum at sampled targets
+    # ---- accuracy: GPU FP64 direct sum at sampled targets (first right-hand side)
     rng = np.random.default_rng(2001)
-    tg = np.sort(rng.choice(n, SAMPLE_TARGETS, replace=False))
-    dref = mf.direct_fp64(ptd, torch.as_tensor(q[0], device=dev), prm["k"], torch.as_tensor(tg, device=dev))
-    got = out.to(torch.complex128)[torch.as_tensor(tg, device=dev)]
+    q0 = Q if nrhs == 1 else Q[0]
+    o0 = out if nrhs == 1 else out[0]
+    if offsets is None:
+        tg = np.sort(rng.choice(n, SAMPLE_TARGETS, replace=False))
+        dref = mf.direct_fp64(ptd, torch.as_tensor(q0, device=dev), prm["k"], torch.as_tensor(tg, device=dev))
+        got = o0.to(torch.complex128)[torch.as_tensor(tg, device=dev)]
+        groups = [(0, n, tg)]
+    else:
+        gsel = np.sort(rng.choice(len(offsets) - 1, 8, replace=False))
+        groups, drefs, gots = [], [], []
+        for g in gsel:
+            a, b = int(offsets[g]), int(offsets[g + 1])
+            tgl = np.sort(rng.choice(b - a, min(250, b - a), replace=False))
+            drefs.append(mf.direct_fp64(ptd[a:b].contiguous(), torch.as_tensor(q0[a:b], device=dev), prm["k"],
+                                        torch.as_tensor(tgl, device=dev)))
+            gots.append(o0[a:b].to(torch.complex128)[torch.as_tensor(tgl, device=dev)])
+            groups.append((a, b, tgl))
+        dref, got = torch.cat(drefs), torch.cat(gots)
     rel_err = float(torch.linalg.norm(got - dref) / torch.linalg.norm(dref))
 
     # ---- roofline of the dominant stage
     pk, pk_kind = peaks()
-    wm = work_model(info)
     dom = max((s for s in ("M2L", "M2M", "L2L", "P2P", "C2M", "L2O")), key=lambda s: stage_ms.get(s, 0.0))
     sm_max = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
-    roof = {"kernel": dom}
-    if dom in wm:
-        fl = wm[dom]["flops"]
-        ach = fl / (stage_ms[dom] / 1e3) / 1e12
-        roof.update({"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (clock from MEASURED_PEAKS.json)",
-                     "traffic": None})
-    else:
-        roof.update({"bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s", "frac": None,
-                     "traffic": None})
-    m2l = {"ms": stage_ms["M2L"], "flops": wm["M2L"]["flops"], "unique_bytes": wm["M2L"]["bytes"],
-           "tflops": wm["M2L"]["flops"] / (stage_ms["M2L"] / 1e3) / 1e12,
-           "hbm_frac_unique_bytes": wm["M2L"]["bytes"] / (stage_ms["M2L"] / 1e3) / 1e9 / pk["hbm_gbs"]}
+    roof = {"kernel": dom, "bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
+            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (clock from MEASURED_PEAKS.json)"}
+    m2l = None
+    if offsets is None and info["top"]:
+        wm = work_model(info)
+        reps = nrhs * (2 if args.mode == "grad" else 1)
+        if dom in wm:
+            ach = wm[dom]["flops"] * reps / (stage_ms[dom] / 1e3) / 1e12
+            roof.update({"achieved": ach, "frac": ach / fp32_peak})
+        m2l = {"ms": stage_ms["M2L"], "flops": wm["M2L"]["flops"] * reps, "unique_bytes": wm["M2L"]["bytes"] * reps,
+               "tflops": wm["M2L"]["flops"] * reps / (stage_ms["M2L"] / 1e3) / 1e12,
+               "hbm_frac_unique_bytes": wm["M2L"]["bytes"] * reps / (stage_ms["M2L"] / 1e3) / 1e9 / pk["hbm_gbs"]}
+    if "achieved" not in roof:
+        roof.update({"achieved": None, "frac": None})
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import direct
-        ct = tg[:512]
+        a, b, tgl = groups[0]
+        ct = tgl[:512]
         t0 = time.perf_counter()
-        cref = direct.direct(pts, q[0], prm["k"], targets=ct)
-        cdt = time.perf_counter() - t0
-        cpu = {"value": ct.shape[0] / cdt, "unit": "points/s", "cores": direct.max_threads(), "kind": "oracle",
-               "sample": f"FP64 direct sum (oracle, C/OpenMP) at {ct.shape[0]} of the {SAMPLE_TARGETS} sampled "
-                         f"targets over all {n} sources",
-               "rel_err_gpu_vs_oracle_direct": float(np.linalg.norm(out.cpu().numpy()[ct] - cref) /
-                                                     np.linalg.norm(cref))}
+        cref = direct.direct(pts[a:b], q0[a:b], prm["k"], targets=ct)
+        cdt_s = time.perf_counter() - t0
+        o0h = o0.cpu().numpy()[a:b]
+        cpu = {"value": ct.shape[0] / cdt_s, "unit": "points/s", "cores": direct.max_threads(), "kind": "oracle",
+               "sample": f"FP64 direct sum (oracle, C/OpenMP) at {ct.shape[0]} sampled targets over all {b - a} "
+                         f"sources of their geometry",
+               "rel_err_gpu_vs_oracle_direct": float(np.linalg.norm(o0h[ct] - cref) / np.linalg.norm(cref))}
 
+    cfg = {"workload": WORKLOADS[args.workload] + f", {args.precision.upper()} complex, nrhs={nrhs}"
+                       + (", forward+backward (charges and positions)" if args.mode == "grad" else ""),
+           "n": n, "digits": prm["digits"], "nrhs": nrhs, "mode": args.mode, "levels": info["nlev"], "L": info["L"],
+           "n_geom": info["n_geom"], "parallelism": f"replicas x{ws}",
+           "l2": "flushed between steps (256 MiB write outside the timed events)"}
     line = {
         "metric": "MLFMA matvec points/s at stated rel. err vs FP64 direct; % HBM roofline",
         "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32)",
-        "data": "synthetic",
-        "config": {"workload": "sphere N=1048576 r=32 wavelengths (k=2pi), leaf 0.25 wavelength, 9 levels, "
-                               "3 digits, FP32 complex, nrhs=1", "n": n, "digits": DIGITS, "nrhs": 1,
-                   "levels": info["nlev"], "L": info["L"], "parallelism": f"replicas x{ws}",
-                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
-        "accuracy": {"rel_err_vs_fp64_direct": rel_err, "targets": SAMPLE_TARGETS, "reference": "GPU FP64 direct sum"},
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 (fp32)" if args.precision == "fp32" else "c128 (fp64)", "data": "synthetic", "config": cfg,
+        "accuracy": {"rel_err_vs_fp64_direct": rel_err, "targets": int(sum(len(g[2]) for g in groups)),
+                     "reference": "GPU FP64 direct sum"},
         "stage_ms": stage_ms, "setup_ms": info["setup_ms"], "m2l": m2l,
         "roofline": roof, "peaks_source": pk_kind, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches_per_apply * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
     }
     line["clocks"] = clk.summary()
     if rank == 0:

@@ -63,7 +63,10 @@ typedef struct mlfma_options {
                                      wavelength (pi/(2k)) for digits <= 4, half a
                                      wavelength (pi/k) for digits >= 5 */
     int max_depth;                /* deepest tree level, root = 1; default 12 */
-    int digit_margin;             /* d0 = digits + digit_margin in the truncation rule; default 1 */
+    int digit_margin;             /* d0 = digits + digit_margin in the truncation rule; default -1 =
+                                     automatic: 1 for FP64 plans, 0 for FP32 plans (in FP32 the roundoff
+                                     amplified by |T| at quarter-wavelength boxes grows with L and
+                                     dominates the error) */
     void* stream;                 /* cudaStream_t for all work; NULL = the legacy default stream */
     /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
     void* (*alloc)(size_t bytes, void* stream, void* ctx);

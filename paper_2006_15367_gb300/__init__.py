@@ -253,7 +253,7 @@ class Plan:
     """
 
     def __init__(self, points, k, digits=3, leaf_max=0, precision="fp32", leaf_edge=0.0, max_depth=12,
-                 digit_margin=1, stream=None, use_torch_allocator=True, offsets=None, graphs=True):
+                 digit_margin=-1, stream=None, use_torch_allocator=True, offsets=None, graphs=True):
         import torch
         self.torch = torch
         load()

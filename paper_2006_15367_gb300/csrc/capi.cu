@@ -280,7 +280,7 @@ void mlfma_options_init(mlfma_options* opt) {
     opt->precision = MLFMA_PREC_FP32;
     opt->leaf_edge = 0.0;
     opt->max_depth = 12;
-    opt->digit_margin = 1;
+    opt->digit_margin = -1;
 }
 
 static mlfma_options checked_options(const mlfma_options* opt, double k, int digits, int leaf_max) {
@@ -296,7 +296,7 @@ static mlfma_options checked_options(const mlfma_options* opt, double k, int dig
     if (o.precision != MLFMA_PREC_FP64 && o.precision != MLFMA_PREC_FP32)
         fail(MLFMA_ERR_INVALID_ARG, "unknown precision %d", (int)o.precision);
     if (o.max_depth < 1 || o.max_depth > kMaxLev) fail(MLFMA_ERR_INVALID_ARG, "max_depth must be in [1, %d]", kMaxLev);
-    if (o.digit_margin < 0 || o.digit_margin > 8) fail(MLFMA_ERR_INVALID_ARG, "digit_margin must be in [0, 8]");
+    if (o.digit_margin < -1 || o.digit_margin > 8) fail(MLFMA_ERR_INVALID_ARG, "digit_margin must be in [-1, 8]");
     if (!std::isfinite(o.leaf_edge)) fail(MLFMA_ERR_INVALID_ARG, "leaf_edge must be finite");
     if ((o.alloc == nullptr) != (o.free == nullptr)) fail(MLFMA_ERR_INVALID_ARG, "alloc and free must be given together");
     return o;
@@ -309,7 +309,7 @@ static void configure(Plan& p, int64_t n, double k, int digits, int leaf_max, co
     p.digits = digits;
     p.leaf_max = leaf_max;
     p.max_depth = o.max_depth;
-    p.margin = o.digit_margin;
+    p.margin = o.digit_margin >= 0 ? o.digit_margin : (o.precision == MLFMA_PREC_FP64 ? 1 : 0);
     p.prec = o.precision;
     p.leaf_edge = o.leaf_edge > 0 ? o.leaf_edge : (digits <= 4 ? 0.5 * M_PI / k : M_PI / k);
     p.stream = (cudaStream_t)o.stream;
@@ -326,6 +326,7 @@ static void build_plan(Plan& p, const double* pts) {
     build_lists(p);
     build_far_levels(p);
     build_m2l_lists(p);
+    build_p2p_work(p);
     p.near_dump = p.mem.get(p.n * csize(p));
     ensure_apply_buffers(p, 1);
     MLFMA_CUDA(cudaStreamSynchronize(p.stream));

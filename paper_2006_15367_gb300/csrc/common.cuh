@@ -18,6 +18,8 @@ namespace mlfma {
 constexpr int kMaxLev = MLFMA_MAX_LEVELS;   // levels 1..22 (21 key bits per axis)
 constexpr int kBits = 21;
 constexpr int kNumOffsets = 316;            // [-3,3]^3 minus [-1,1]^3: far offsets of one level
+constexpr int kSmallLeaf = 64;              // P2P: leaves up to this size take one warp
+constexpr int kP2PTile = 128;               // P2P: targets per CTA for larger leaves
 
 // ---------------------------------------------------------------- errors
 void set_error(const char* fmt, ...);
@@ -98,6 +100,14 @@ struct TreeLevel {                 // one octree level (root = 1)
     int* v_src = nullptr;          // [nv]
     int64_t nv = 0;
     int64_t nleaf = 0;
+    // leaves of this level split by size for C2M / L2O: small ones take one warp, larger
+    // ones a CTA per sample chunk (C2M) or per tile of kP2PTile points (L2O)
+    int* small_leaves = nullptr;   // [n_small_leaves] box indices
+    int64_t n_small_leaves = 0;
+    int* big_leaves = nullptr;     // [n_big_leaves] box indices
+    int64_t n_big_leaves = 0;
+    int2* big_tiles = nullptr;     // [n_big_tiles] (box, first point offset)
+    int64_t n_big_tiles = 0;
     // M2L work of the children of each box (this level acting as parent level):
     // per box, the candidate sources with at least one far child, packed
     // (src * K) << 32 | far-children mask << 8 | code, code = colleague slot (0..26) * 8 + source octant
@@ -161,6 +171,12 @@ struct Plan {
     int* near_lev = nullptr;       // [nnear]
     int* near_box = nullptr;       // [nnear]
     int64_t nnear = 0, near_pairs = 0;
+    // P2P work split: leaves with at most kSmallLeaf points (one warp each) and
+    // tiles of kP2PTile targets of the larger leaves (one CTA each)
+    int* p2p_small = nullptr;      // [n_small] leaf-table indices
+    int64_t n_small = 0;
+    int2* p2p_tiles = nullptr;     // [n_tiles] (leaf-table index, first target offset)
+    int64_t n_tiles = 0;
     TreeLevel lev[kMaxLev + 1];
     FarLevel far[kMaxLev + 1];
     // apply buffers
@@ -221,6 +237,7 @@ void build_lists(Plan& p);
 int truncation_L(double edge, double k, int digits, int margin);
 void build_far_levels(Plan& p);
 void build_m2l_lists(Plan& p);
+void build_p2p_work(Plan& p);
 // far.cu / near.cu
 // one right-hand side in sorted order; grads_r (nullable): [n][3] complex gradient of phi
 void apply_pipeline(Plan& p, const void* qs_r, void* phis_r, void* grads_r);

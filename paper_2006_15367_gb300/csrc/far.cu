@@ -168,6 +168,110 @@ __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restric
     }
 }
 
+
+// ============================================================== C2M / L2O for leaves with many points
+// C2M: one CTA per (leaf, chunk of 128 samples), one sample per thread, the leaf's points
+// staged through shared memory.
+template <typename R, typename C>
+__global__ void __launch_bounds__(128) k_c2m_big(const int* __restrict__ leaves, const int* __restrict__ begin,
+                                                 const int* __restrict__ end, const double* __restrict__ center,
+                                                 const double* __restrict__ pos, const C* __restrict__ qs,
+                                                 const R* __restrict__ dirs, int64_t K, R k, C* __restrict__ F) {
+    __shared__ R sx[256], sy[256], sz[256];
+    __shared__ C sq[256];
+    const int b = leaves[blockIdx.x];
+    const int b0 = begin[b], b1 = end[b];
+    const double cx = center[3 * b], cy = center[3 * b + 1], cz = center[3 * b + 2];
+    const int64_t p = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    const int64_t pp = p < K ? p : K - 1;
+    const R dx = -k * dirs[4 * pp], dy = -k * dirs[4 * pp + 1], dz = -k * dirs[4 * pp + 2];
+    C acc = cmake<C>(0, 0);
+    for (int j0 = b0; j0 < b1; j0 += 256) {
+        const int cnt = min(256, b1 - j0);
+        __syncthreads();
+        for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
+            const int64_t j = j0 + m;
+            sx[m] = (R)(pos[3 * j] - cx);
+            sy[m] = (R)(pos[3 * j + 1] - cy);
+            sz[m] = (R)(pos[3 * j + 2] - cz);
+            sq[m] = qs[j];
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int m = 0; m < cnt; ++m) {
+            R s, c;
+            sc(dx * sx[m] + dy * sy[m] + dz * sz[m], s, c);
+            cfma(acc, sq[m], cmake<C>(c, s));
+        }
+    }
+    if (p < K) F[(int64_t)b * K + p] = acc;
+}
+
+// L2O: one CTA per tile of kP2PTile points of a leaf, one point per thread, the leaf's
+// samples (direction, weight, G) staged through shared memory.
+template <typename R, typename C, bool GRAD>
+__global__ void __launch_bounds__(128) k_l2o_big(const int2* __restrict__ tiles, const int* __restrict__ begin,
+                                                 const int* __restrict__ end, const double* __restrict__ center,
+                                                 const double* __restrict__ pos, const R* __restrict__ dirs, int64_t K, R k,
+                                                 const C* __restrict__ G, C* __restrict__ phis, C* __restrict__ grads) {
+    __shared__ R sd[256][4];
+    __shared__ C sg[256];
+    const int2 tile = tiles[blockIdx.x];
+    const int b = tile.x;
+    const int i = begin[b] + tile.y + threadIdx.x;
+    const bool valid = i < end[b];
+    const double cx = center[3 * b], cy = center[3 * b + 1], cz = center[3 * b + 2];
+    R x = 0, y = 0, z = 0;
+    if (valid) {
+        x = (R)(pos[3 * (int64_t)i] - cx);
+        y = (R)(pos[3 * (int64_t)i + 1] - cy);
+        z = (R)(pos[3 * (int64_t)i + 2] - cz);
+    }
+    const C* Gb = G + (int64_t)b * K;
+    C acc = cmake<C>(0, 0);
+    C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
+    for (int64_t p0 = 0; p0 < K; p0 += 256) {
+        const int cnt = (int)min((int64_t)256, K - p0);
+        __syncthreads();
+        for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) sd[m][a] = dirs[4 * (p0 + m) + a];
+            sg[m] = Gb[p0 + m];
+        }
+        __syncthreads();
+        for (int m = 0; m < cnt; ++m) {
+            R s, c;
+            sc(k * (sd[m][0] * x + sd[m][1] * y + sd[m][2] * z), s, c);
+            const R wp = sd[m][3];
+            if (!GRAD) {
+                cfma(acc, cmake<C>(wp * c, wp * s), sg[m]);
+            } else {
+                const C term = cmul(cmake<C>(wp * c, wp * s), sg[m]);
+                acc = cadd(acc, term);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) ga[a] = cadd(ga[a], cmake<C>(sd[m][a] * term.x, sd[m][a] * term.y));
+            }
+        }
+    }
+    if (valid) {
+        const R f = k / (R)(4.0 * M_PI);
+        C v = phis[i];
+        v.x += -f * acc.y;
+        v.y += f * acc.x;
+        phis[i] = v;
+        if (GRAD) {
+            const R f2 = -k * k / (R)(4.0 * M_PI);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                C g = grads[3 * (int64_t)i + a];
+                g.x += f2 * ga[a].x;
+                g.y += f2 * ga[a].y;
+                grads[3 * (int64_t)i + a] = g;
+            }
+        }
+    }
+}
+
 // ============================================================== M2L (warp per parent: its children are the targets)
 // A CTA owns one 32-sample tile (blockIdx.y) and a run of parents (blockIdx.x).  The
 // tile's slice of the translation operators, T[316][32], is staged once in shared
@@ -630,10 +734,17 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         FarLevel& F = p.far[l];
         TreeLevel& T = p.lev[l];
         if (T.nleaf > 0) {
-            StageTimer st(p, MLFMA_STAGE_C2M, l, 1);
-            k_c2m<R, C><<<nblk(T.nleaf, 4), 128, 0, s>>>(T.nleaf, p.leaf_box + p.leaf_first[l], T.begin, T.end, T.center, p.pos,
-                                                       qs, (const R*)F.dirs, F.K, k, (C*)F.F);
-            MLFMA_LAUNCH_CHECK();
+            StageTimer st(p, MLFMA_STAGE_C2M, l, (T.n_small_leaves > 0) + (T.n_big_leaves > 0));
+            if (T.n_small_leaves > 0) {
+                k_c2m<R, C><<<nblk(T.n_small_leaves, 4), 128, 0, s>>>(T.n_small_leaves, T.small_leaves, T.begin, T.end,
+                                                                    T.center, p.pos, qs, (const R*)F.dirs, F.K, k, (C*)F.F);
+                MLFMA_LAUNCH_CHECK();
+            }
+            if (T.n_big_leaves > 0) {
+                k_c2m_big<R, C><<<dim3((unsigned)T.n_big_leaves, nblk(F.K, 128)), 128, 0, s>>>(
+                    T.big_leaves, T.begin, T.end, T.center, p.pos, qs, (const R*)F.dirs, F.K, k, (C*)F.F);
+                MLFMA_LAUNCH_CHECK();
+            }
         }
         if (l == p.nlev) continue;
         FarLevel& Ch = p.far[l + 1];
@@ -689,16 +800,29 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
             MLFMA_LAUNCH_CHECK();
         }
         if (T.nleaf > 0) {
-            StageTimer st(p, MLFMA_STAGE_L2O, l, 1);
-            if (grads_v)
-                k_l2o<R, C, true><<<nblk(T.nleaf, 4), 128, 0, s>>>(T.nleaf, p.leaf_box + p.leaf_first[l], T.begin, T.end,
-                                                                 T.center, p.pos, (const R*)F.dirs, F.K, k, (const C*)F.G,
-                                                                 phis, (C*)grads_v);
-            else
-                k_l2o<R, C, false><<<nblk(T.nleaf, 4), 128, 0, s>>>(T.nleaf, p.leaf_box + p.leaf_first[l], T.begin, T.end,
-                                                                  T.center, p.pos, (const R*)F.dirs, F.K, k, (const C*)F.G,
-                                                                  phis, nullptr);
-            MLFMA_LAUNCH_CHECK();
+            StageTimer st(p, MLFMA_STAGE_L2O, l, (T.n_small_leaves > 0) + (T.n_big_tiles > 0));
+            if (T.n_small_leaves > 0) {
+                if (grads_v)
+                    k_l2o<R, C, true><<<nblk(T.n_small_leaves, 4), 128, 0, s>>>(T.n_small_leaves, T.small_leaves, T.begin,
+                                                                              T.end, T.center, p.pos, (const R*)F.dirs, F.K,
+                                                                              k, (const C*)F.G, phis, (C*)grads_v);
+                else
+                    k_l2o<R, C, false><<<nblk(T.n_small_leaves, 4), 128, 0, s>>>(T.n_small_leaves, T.small_leaves, T.begin,
+                                                                               T.end, T.center, p.pos, (const R*)F.dirs, F.K,
+                                                                               k, (const C*)F.G, phis, nullptr);
+                MLFMA_LAUNCH_CHECK();
+            }
+            if (T.n_big_tiles > 0) {
+                if (grads_v)
+                    k_l2o_big<R, C, true><<<(unsigned)T.n_big_tiles, 128, 0, s>>>(T.big_tiles, T.begin, T.end, T.center, p.pos,
+                                                                               (const R*)F.dirs, F.K, k, (const C*)F.G, phis,
+                                                                               (C*)grads_v);
+                else
+                    k_l2o_big<R, C, false><<<(unsigned)T.n_big_tiles, 128, 0, s>>>(T.big_tiles, T.begin, T.end, T.center,
+                                                                                p.pos, (const R*)F.dirs, F.K, k,
+                                                                                (const C*)F.G, phis, nullptr);
+                MLFMA_LAUNCH_CHECK();
+            }
         }
     }
 }

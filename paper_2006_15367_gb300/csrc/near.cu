@@ -23,6 +23,15 @@ __device__ __forceinline__ void scpi(double x, double& s, double& c) { sincospi(
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
+// sin and cos of pi * x.  FP32: reduce x to [-1, 1] (x - 2 rint(x / 2)), then the SFU
+// __sincosf on [-pi, pi] (absolute error ~4e-7, below the FP32 path's tolerance);
+// FP64: sincospi.
+__device__ __forceinline__ void scpi_fast(float x, float& s, float& c) {
+    const float r = x - 2.0f * rintf(0.5f * x);
+    __sincosf(3.14159265358979f * r, &s, &c);
+}
+__device__ __forceinline__ void scpi_fast(double x, double& s, double& c) { sincospi(x, &s, &c); }
+
 struct LevelRanges {
     const int* begin[kMaxLev + 1];
     const int* end[kMaxLev + 1];
@@ -31,15 +40,17 @@ struct LevelRanges {
 
 // GRAD: also grad phi_i = sum_j q_j e^{ikR} (ikR - 1) / R^3 (r_i - r_j), written to grads[3 i + a].
 template <typename R, typename C, bool GRAD>
-__global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restrict__ leaf_level, const int* __restrict__ leaf_box,
-                                             const int* __restrict__ near_off, const int* __restrict__ near_lev,
-                                             const int* __restrict__ near_box, LevelRanges LR, const double* __restrict__ pos,
-                                             const C* __restrict__ qs, R kpi, C* __restrict__ phis, C* __restrict__ grads) {
+__global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restrict__ leaves, const int* __restrict__ leaf_level,
+                                             const int* __restrict__ leaf_box, const int* __restrict__ near_off,
+                                             const int* __restrict__ near_lev, const int* __restrict__ near_box, LevelRanges LR,
+                                             const double* __restrict__ pos, const C* __restrict__ qs, R kpi,
+                                             C* __restrict__ phis, C* __restrict__ grads) {
     __shared__ R sx[4][32], sy[4][32], sz[4][32];
     __shared__ C sq[4][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t w = (int64_t)blockIdx.x * 4 + wl;
-    if (w >= nleaf) return;
+    const int64_t wi = (int64_t)blockIdx.x * 4 + wl;
+    if (wi >= nleaf) return;
+    const int w = leaves[wi];
     const int l = leaf_level[w], b = leaf_box[w];
     const int t0 = LR.begin[l][b], t1 = LR.end[l][b];
     const double* ct = LR.center[l] + 3 * b;
@@ -121,6 +132,89 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
     }
 }
 
+
+// Larger leaves: one CTA per tile of kP2PTile targets, one target per thread; the source
+// points of every near box are staged through shared memory (positions relative to the
+// target leaf centre, FP64 difference then rounded) in tiles of 2 * kP2PTile.
+template <typename R, typename C, bool GRAD>
+__global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ tiles, const int* __restrict__ leaf_level,
+                                                       const int* __restrict__ leaf_box, const int* __restrict__ near_off,
+                                                       const int* __restrict__ near_lev, const int* __restrict__ near_box,
+                                                       LevelRanges LR, const double* __restrict__ pos,
+                                                       const C* __restrict__ qs, R kpi, C* __restrict__ phis,
+                                                       C* __restrict__ grads) {
+    constexpr int SRC = 2 * kP2PTile;
+    __shared__ R sx[SRC], sy[SRC], sz[SRC];
+    __shared__ C sq[SRC];
+    const int2 tile = tiles[blockIdx.x];
+    const int w = tile.x;
+    const int l = leaf_level[w], b = leaf_box[w];
+    const int t0 = LR.begin[l][b], t1 = LR.end[l][b];
+    const double* ct = LR.center[l] + 3 * b;
+    const double cx = ct[0], cy = ct[1], cz = ct[2];
+    const int i = t0 + tile.y + threadIdx.x;
+    const bool valid = i < t1;
+    R x = 0, y = 0, z = 0;
+    if (valid) {
+        x = (R)(pos[3 * (int64_t)i] - cx);
+        y = (R)(pos[3 * (int64_t)i + 1] - cy);
+        z = (R)(pos[3 * (int64_t)i + 2] - cz);
+    }
+    const R kk = kpi * (R)M_PI;
+    C acc = cmake<C>(0, 0);
+    C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
+    for (int e = near_off[w]; e < near_off[w + 1]; ++e) {
+        const int ls = near_lev[e], bs = near_box[e];
+        const int u0 = LR.begin[ls][bs], u1 = LR.end[ls][bs];
+        for (int k0 = u0; k0 < u1; k0 += SRC) {
+            const int cnt = min(SRC, u1 - k0);
+            __syncthreads();
+            for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
+                const int64_t j = k0 + m;
+                sx[m] = (R)(pos[3 * j] - cx);
+                sy[m] = (R)(pos[3 * j + 1] - cy);
+                sz[m] = (R)(pos[3 * j + 2] - cz);
+                sq[m] = qs[j];
+            }
+            __syncthreads();
+            if (valid) {
+#pragma unroll 4
+                for (int m = 0; m < cnt; ++m) {
+                    const R dx = x - sx[m], dy = y - sy[m], dz = z - sz[m];
+                    const R r2 = dx * dx + dy * dy + dz * dz;
+                    if (!GRAD) {
+                        // branch-free: R = 0 (self / coincident) gives inv = 0 and no contribution
+                        const R inv = r2 > (R)0 ? rsq(r2) : (R)0;
+                        R s, c;
+                        scpi_fast(kpi * (r2 * inv), s, c);
+                        cfma(acc, sq[m], cmake<C>(c * inv, s * inv));
+                    } else if (r2 > (R)0) {
+                        const R inv = rsq(r2);
+                        const R r = r2 * inv;
+                        R s, c;
+                        scpi(kpi * r, s, c);
+                        {
+                            const C qe = cmul(sq[m], cmake<C>(c * inv, s * inv));
+                            acc = cadd(acc, qe);
+                            const R i2 = inv * inv;
+                            const C g = cmul(qe, cmake<C>(-i2, kk * r * i2));
+                            ga[0] = cadd(ga[0], cmake<C>(g.x * dx, g.y * dx));
+                            ga[1] = cadd(ga[1], cmake<C>(g.x * dy, g.y * dy));
+                            ga[2] = cadd(ga[2], cmake<C>(g.x * dz, g.y * dz));
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (valid) {
+        phis[i] = acc;
+        if (GRAD)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) grads[3 * (int64_t)i + a] = ga[a];
+    }
+}
+
 // caller order (rows of stride ld) <-> Morton order (rows of stride n)
 template <typename C>
 __global__ void k_permute_in(int64_t n, int nrhs, int64_t ld, const int* __restrict__ perm, const C* __restrict__ q,
@@ -175,15 +269,31 @@ static void near_apply(Plan& p, const void* qs, void* phis, void* grads) {
         LR.end[l] = l <= p.nlev ? p.lev[l].end : nullptr;
         LR.center[l] = l <= p.nlev ? p.lev[l].center : nullptr;
     }
-    const int64_t nl = p.nleaf_total;
-    StageTimer st(p, MLFMA_STAGE_P2P, 0, 1);
-    if (grads)
-        k_p2p<R, C, true><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box,
-                                                             LR, p.pos, (const C*)qs, (R)(p.k / M_PI), (C*)phis, (C*)grads);
-    else
-        k_p2p<R, C, false><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box,
-                                                              LR, p.pos, (const C*)qs, (R)(p.k / M_PI), (C*)phis, nullptr);
-    MLFMA_LAUNCH_CHECK();
+    const int64_t nl = p.n_small;
+    const R kpi = (R)(p.k / M_PI);
+    StageTimer st(p, MLFMA_STAGE_P2P, 0, (nl > 0) + (p.n_tiles > 0));
+    if (nl > 0) {
+        if (grads)
+            k_p2p<R, C, true><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off,
+                                                                 p.near_lev, p.near_box, LR, p.pos, (const C*)qs, kpi,
+                                                                 (C*)phis, (C*)grads);
+        else
+            k_p2p<R, C, false><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off,
+                                                                  p.near_lev, p.near_box, LR, p.pos, (const C*)qs, kpi,
+                                                                  (C*)phis, nullptr);
+        MLFMA_LAUNCH_CHECK();
+    }
+    if (p.n_tiles > 0) {
+        if (grads)
+            k_p2p_tile<R, C, true><<<(unsigned)p.n_tiles, kP2PTile, 0, p.stream>>>(
+                p.p2p_tiles, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, kpi,
+                (C*)phis, (C*)grads);
+        else
+            k_p2p_tile<R, C, false><<<(unsigned)p.n_tiles, kP2PTile, 0, p.stream>>>(
+                p.p2p_tiles, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, kpi,
+                (C*)phis, nullptr);
+        MLFMA_LAUNCH_CHECK();
+    }
 }
 
 void near_only(Plan& p, const void* qs, void* phis) {

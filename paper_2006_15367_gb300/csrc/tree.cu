@@ -845,3 +845,80 @@ void build_m2l_lists(Plan& p) {
 }
 
 }  // namespace mlfma
+
+namespace mlfma {
+
+// ============================================================== P2P work split
+__global__ void k_leaf_sizes(int64_t nleaf, const int* __restrict__ leaf_level, const int* __restrict__ leaf_box,
+                             const int* const* __restrict__ beg, const int* const* __restrict__ end, int* __restrict__ out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nleaf) return;
+    const int l = leaf_level[t], b = leaf_box[t];
+    out[t] = end[l][b] - beg[l][b];
+}
+
+void build_p2p_work(Plan& p) {
+    cudaStream_t s = p.stream;
+    const int64_t nl = p.nleaf_total;
+    const int* hb[kMaxLev + 1] = {nullptr};
+    const int* he[kMaxLev + 1] = {nullptr};
+    for (int l = 1; l <= p.nlev; ++l) { hb[l] = p.lev[l].begin; he[l] = p.lev[l].end; }
+    const int** db = p.mem.make<const int*>(kMaxLev + 1);
+    const int** de = p.mem.make<const int*>(kMaxLev + 1);
+    int* sizes = p.mem.make<int>(std::max<int64_t>(nl, 1));
+    MLFMA_CUDA(cudaMemcpyAsync(db, hb, sizeof(hb), cudaMemcpyHostToDevice, s));
+    MLFMA_CUDA(cudaMemcpyAsync(de, he, sizeof(he), cudaMemcpyHostToDevice, s));
+    k_leaf_sizes<<<nblk(nl, 256), 256, 0, s>>>(nl, p.leaf_level, p.leaf_box, db, de, sizes);
+    MLFMA_LAUNCH_CHECK();
+    std::vector<int> hs(nl);
+    MLFMA_CUDA(cudaMemcpyAsync(hs.data(), sizes, nl * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MLFMA_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> small;
+    std::vector<int2> tiles;
+    for (int64_t t = 0; t < nl; ++t) {
+        if (hs[t] <= kSmallLeaf) {
+            small.push_back((int)t);
+        } else {
+            for (int o = 0; o < hs[t]; o += kP2PTile) tiles.push_back(make_int2((int)t, o));
+        }
+    }
+    // per level: small / big leaves and the point tiles of the big ones
+    std::vector<int> lev_of(nl), box_of(nl);
+    MLFMA_CUDA(cudaMemcpyAsync(lev_of.data(), p.leaf_level, nl * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MLFMA_CUDA(cudaMemcpyAsync(box_of.data(), p.leaf_box, nl * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MLFMA_CUDA(cudaStreamSynchronize(s));
+    for (int l = 1; l <= p.nlev; ++l) {
+        std::vector<int> sm, bg;
+        std::vector<int2> bt;
+        for (int64_t t = p.leaf_first[l]; t < p.leaf_first[l + 1]; ++t) {
+            if (hs[t] <= kSmallLeaf) {
+                sm.push_back(box_of[t]);
+            } else {
+                bg.push_back(box_of[t]);
+                for (int o = 0; o < hs[t]; o += kP2PTile) bt.push_back(make_int2(box_of[t], o));
+            }
+        }
+        TreeLevel& L = p.lev[l];
+        L.n_small_leaves = (int64_t)sm.size();
+        L.n_big_leaves = (int64_t)bg.size();
+        L.n_big_tiles = (int64_t)bt.size();
+        L.small_leaves = p.mem.make<int>(std::max<int64_t>(L.n_small_leaves, 1));
+        L.big_leaves = p.mem.make<int>(std::max<int64_t>(L.n_big_leaves, 1));
+        L.big_tiles = p.mem.make<int2>(std::max<int64_t>(L.n_big_tiles, 1));
+        if (!sm.empty()) MLFMA_CUDA(cudaMemcpyAsync(L.small_leaves, sm.data(), sm.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        if (!bg.empty()) MLFMA_CUDA(cudaMemcpyAsync(L.big_leaves, bg.data(), bg.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        if (!bt.empty()) MLFMA_CUDA(cudaMemcpyAsync(L.big_tiles, bt.data(), bt.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        MLFMA_CUDA(cudaStreamSynchronize(s));
+    }
+    p.n_small = (int64_t)small.size();
+    p.n_tiles = (int64_t)tiles.size();
+    p.p2p_small = p.mem.make<int>(std::max<int64_t>(p.n_small, 1));
+    p.p2p_tiles = p.mem.make<int2>(std::max<int64_t>(p.n_tiles, 1));
+    if (p.n_small)
+        MLFMA_CUDA(cudaMemcpyAsync(p.p2p_small, small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (p.n_tiles)
+        MLFMA_CUDA(cudaMemcpyAsync(p.p2p_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    MLFMA_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace mlfma

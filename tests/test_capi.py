@@ -28,7 +28,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_options_defaults_without_gpu():
     o = mf.mlfma_options_init()
     assert o.struct_size == ctypes.sizeof(mf.Options)
-    assert o.precision == mf.PREC_FP32 and o.max_depth == 12 and o.digit_margin == 1
+    assert o.precision == mf.PREC_FP32 and o.max_depth == 12 and o.digit_margin == -1
 
 
 def test_invalid_arguments_rejected_before_any_device_work():

@@ -26,19 +26,26 @@ STAGE_TOL = {"fp64": 1e-11, "fp32": 1e-5}
 END_TOL = {"fp64": 1e-11, "fp32": 1e-3}
 
 
+# the library's default truncation margin: d0 = digits + 1 (FP64), digits + 0 (FP32)
+MARGIN = {"fp64": 1, "fp32": 0}
+
+
 @pytest.fixture(scope="module")
 def oracle4k(sphere4k):
     pts, q, prm = sphere4k
-    o = om.OracleMLFMA(pts, prm["k"], 3)
-    phi, dump = o.apply(q[0], dump=True)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        o = om.OracleMLFMA(pts, prm["k"], 3, margin=MARGIN[prec])
+        phi, dump = o.apply(q[0], dump=True)
+        out[prec] = (o, phi, dump)
     ref = direct.direct(pts, q[0], prm["k"])
-    return o, phi, dump, ref
+    return out, ref
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_stages_match_oracle_sphere4k(sphere4k, oracle4k, prec):
     pts, q, prm = sphere4k
-    o, phio, dump, ref = oracle4k
+    (o, phio, dump), ref = oracle4k[0][prec], oracle4k[1]
     plan = make_plan(pts, prm["k"], 3, prec)
     phi = apply_plan(plan, q[0], prec)
     assert rel(plan.export("NEAR_PHI"), dump["near"]) < STAGE_TOL[prec]
@@ -78,7 +85,7 @@ def test_adaptive_tree_matches_oracle(prec):
     pts = np.concatenate([synth.sphere(3000, 1.5, seed=71),
                           synth.normal(72, 3 * 1200).reshape(1200, 3) * 0.05 + np.array([0.9, 0.2, -0.3])])
     q = synth.complex_normal(73, pts.shape[0])[0]
-    o = om.OracleMLFMA(pts, K, 3, leaf_max=24)
+    o = om.OracleMLFMA(pts, K, 3, leaf_max=24, margin=MARGIN[prec])
     phio, dump = o.apply(q, dump=True)
     plan = make_plan(pts, K, 3, prec, leaf_max=24)
     phi = apply_plan(plan, q, prec)

@@ -17,7 +17,7 @@ K = 2.0 * math.pi
 
 def test_tree_and_lists_sphere4k(sphere4k):
     pts, q, prm = sphere4k
-    o = om.OracleMLFMA(pts, prm["k"], 3)
+    o = om.OracleMLFMA(pts, prm["k"], 3, margin=0)        # FP32 plans: d0 = digits
     plan = make_plan(pts, prm["k"], 3)
     assert_tree_matches(plan, o.tree, o.V)
     assert near_lists_from_plan(plan, o.tree) == oracle_near_lists(o)
