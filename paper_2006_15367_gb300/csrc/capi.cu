@@ -327,6 +327,7 @@ static void build_plan(Plan& p, const double* pts) {
     build_far_levels(p);
     build_m2l_lists(p);
     build_p2p_work(p);
+    prepare_kernels(p);
     p.near_dump = p.mem.get(p.n * csize(p));
     ensure_apply_buffers(p, 1);
     MLFMA_CUDA(cudaStreamSynchronize(p.stream));

@@ -153,7 +153,6 @@ struct Plan {
     double x0[3] = {0, 0, 0}, scale = 0;
     int nlev = 0, top = 0;
     int* off343 = nullptr;         // [343] (dx+3)+7(dy+3)+49(dz+3) -> far-offset index 0..315, -1 if near
-    short* m2l_tab = nullptr;      // [216][9] (code, target octant) -> far-offset index, -1 if near or no target
     cudaStream_t stream = nullptr;
     Allocator mem;
     // per point (sorted order)
@@ -238,6 +237,7 @@ int truncation_L(double edge, double k, int digits, int margin);
 void build_far_levels(Plan& p);
 void build_m2l_lists(Plan& p);
 void build_p2p_work(Plan& p);
+void prepare_kernels(Plan& p);
 // far.cu / near.cu
 // one right-hand side in sorted order; grads_r (nullable): [n][3] complex gradient of phi
 void apply_pipeline(Plan& p, const void* qs_r, void* phis_r, void* grads_r);

@@ -272,97 +272,130 @@ __global__ void __launch_bounds__(128) k_l2o_big(const int2* __restrict__ tiles,
     }
 }
 
-// ============================================================== M2L (warp per parent: its children are the targets)
-// A CTA owns one 32-sample tile (blockIdx.y) and a run of parents (blockIdx.x).  The
-// tile's slice of the translation operators, T[316][32], is staged once in shared
-// memory; each warp then takes parents in turn, lane = sample.  Each source of the
-// parent's list is loaded once (the next one is prefetched) and applied to every child
-// it is far from: acc[t] += T_{o(s,t)}(p) F_s(p).  List entries carry the far-children
-// mask; tab[code][ct] gives the far-offset index.
-constexpr int kM2LWarps = 16;
+// ============================================================== M2L (Eq. 9)
+// G_t = sum over s in V(t) of T_{t-s} F_s, organised per parent P: a warp takes P and a
+// 32U-sample slice of the grid (p = tile * 32U + lane + 32u), walks the list of P's
+// colleagues' children that are far from some child of P (entries (src * K) << 32 |
+// far-children mask << 16 | base), loads each source's samples once and adds them to every
+// child of P it is far from.  The operators of the slice are staged in shared memory as the
+// full 7^3 offset cube Ts[343][32U] (the 27 near rows zero), so the row of a (child, source)
+// pair is base(source) + c(child).  The child count NT is a template argument, so each entry
+// costs NT predicated child slots.
 constexpr int kM2LParentsPerWarp = 4;
 
-template <typename R, typename C>
-__global__ void __launch_bounds__(32 * kM2LWarps) k_m2l(int64_t npar, const int* __restrict__ pcb, const int* __restrict__ pce,
-                                                       const int* __restrict__ loff, const unsigned long long* __restrict__ lsrc,
-                                                       const uint64_t* __restrict__ ckey, const short* __restrict__ tab_g,
-                                                       const C* __restrict__ F, const C* __restrict__ T, int64_t K,
-                                                       C* __restrict__ G) {
-    extern __shared__ unsigned char smem_raw[];
-    C* Ts = reinterpret_cast<C*>(smem_raw);                               // [316][32]
-    short* tab = reinterpret_cast<short*>(Ts + kNumOffsets * 32);         // [216][9]: row offset oi * 32
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t p0 = (int64_t)blockIdx.y * 32;
-    const int64_t P0 = (int64_t)blockIdx.x * (kM2LWarps * kM2LParentsPerWarp);
-    for (int i = threadIdx.x; i < 216 * 9; i += blockDim.x) {
-        const short v = tab_g[i];
-        tab[i] = v >= 0 ? (short)(v * 32) : (short)-1;
+template <typename C, int U, int NT>
+__device__ __forceinline__ void m2l_parent(int lane, int t0, const uint64_t* __restrict__ ckey,
+                                           const unsigned long long* __restrict__ le, int ne, const C* const (&Fp)[U],
+                                           const C* Tl, const bool (&ok)[U], int64_t K, int64_t p0, C* __restrict__ G) {
+    constexpr int TS = 32 * U;
+    int cr[NT];     // child part of the row index, times TS
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int ct = (int)(ckey[t0 + t] & 7);
+        cr[t] = ((ct & 1) + 7 * ((ct >> 1) & 1) + 49 * (ct >> 2)) * TS;
     }
-    for (int i = threadIdx.x; i < kNumOffsets * 32; i += blockDim.x) {
-        const int o = i >> 5, l = i & 31;
-        Ts[i] = p0 + l < K ? T[(int64_t)o * K + p0 + l] : cmake<C>(0, 0);
+    C acc[NT][U];
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[t][u] = cmake<C>(0, 0);
+    // the lanes fetch 32 list entries at once and broadcast them one by one
+    for (int eb = 0; eb < ne; eb += 32) {
+        const unsigned long long mine = eb + lane < ne ? __ldg(le + eb + lane) : 0ull;
+        const int cnt = ne - eb < 32 ? ne - eb : 32;
+        for (int j = 0; j < cnt; ++j) {
+            const unsigned long long w = __shfl_sync(0xffffffffu, mine, j);
+            const unsigned lo = (unsigned)w;
+            C f[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) f[u] = Fp[u][(unsigned)(w >> 32)];
+            const C* Tb = Tl + (lo & 511u) * TS;
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+                if (lo & (0x10000u << t)) {
+                    const C* Tr = Tb + cr[t];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) cfma(acc[t][u], Tr[32 * u], f[u]);
+                }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (ok[u]) G[(int64_t)(t0 + t) * K + p0 + lane + 32 * u] = acc[t][u];
+}
+
+template <typename R, typename C, int U, int NW>
+__global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __restrict__ pcb, const int* __restrict__ pce,
+                                                   const int* __restrict__ loff, const unsigned long long* __restrict__ lsrc,
+                                                   const uint64_t* __restrict__ ckey, const int* __restrict__ off343,
+                                                   const C* __restrict__ F, const C* __restrict__ T, int64_t K,
+                                                   C* __restrict__ G) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TS = 32 * U;
+    C* Ts = reinterpret_cast<C*>(smem_raw);                               // [343][TS]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t p0 = (int64_t)blockIdx.y * TS;
+    const int64_t P0 = (int64_t)blockIdx.x * (NW * kM2LParentsPerWarp);
+    for (int i = threadIdx.x; i < 343 * TS; i += blockDim.x) {
+        const int r = i / TS, l = i - r * TS;
+        const int o = off343[r];
+        Ts[i] = (o >= 0 && p0 + l < K) ? T[(int64_t)o * K + p0 + l] : cmake<C>(0, 0);
     }
     __syncthreads();
-    const int64_t p = p0 + lane;
-    const C* Fp = F + (p < K ? p : K - 1);       // lane's sample; + (src * K) per source
+    const C* Fp[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t p = p0 + lane + 32 * u;
+        ok[u] = p < K;
+        Fp[u] = F + (ok[u] ? p : K - 1);       // lane's sample; + (src * K) per source
+    }
     const C* Tl = Ts + lane;
     for (int pw = 0; pw < kM2LParentsPerWarp; ++pw) {
-        const int64_t P = P0 + (int64_t)pw * kM2LWarps + warp;
+        const int64_t P = P0 + (int64_t)pw * NW + warp;
         if (P >= npar) break;
         const int t0 = pcb[P], nt = pce[P] - t0;
-        if (nt <= 0) continue;
-        int ct[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) ct[t] = t < nt ? (int)(ckey[t0 + t] & 7) : 0;
-        C acc[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) acc[t] = cmake<C>(0, 0);
         const unsigned long long* le = lsrc + loff[P];
         const int ne = loff[P + 1] - loff[P];
-        C fn = cmake<C>(0, 0);
-        unsigned long long wn = 0;
-        if (ne > 0) {
-            wn = __ldg(le);
-            fn = Fp[(unsigned)(wn >> 32)];
-        }
-        for (int e = 0; e < ne; ++e) {
-            const unsigned lo = (unsigned)wn;
-            const C f = fn;
-            if (e + 1 < ne) {
-                wn = __ldg(le + e + 1);
-                fn = Fp[(unsigned)(wn >> 32)];
-            }
-            const unsigned tmask = lo >> 8;
-            const short* tr = tab + (lo & 255u) * 9;
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                if (t >= nt) break;
-                if ((tmask >> t) & 1u) cfma(acc[t], Tl[tr[ct[t]]], f);
-            }
-        }
-        if (p < K) {
-#pragma unroll
-            for (int t = 0; t < 8; ++t)
-                if (t < nt) G[(int64_t)(t0 + t) * K + p] = acc[t];
+        switch (nt) {
+#define M2L_NT(n) case n: m2l_parent<C, U, n>(lane, t0, ckey, le, ne, Fp, Tl, ok, K, p0, G); break;
+            M2L_NT(1) M2L_NT(2) M2L_NT(3) M2L_NT(4) M2L_NT(5) M2L_NT(6) M2L_NT(7) M2L_NT(8)
+#undef M2L_NT
+            default: break;
         }
     }
 }
 
+// one sample per lane; 32 warps share the 88 KB complex64 operator slice, 16 the 176 KB
+// complex128 one
+template <typename C> struct M2LShape { static constexpr int U = 1, NW = sizeof(C) == 8 ? 32 : 16; };
+
+template <typename R, typename C>
+static size_t m2l_smem() { return (size_t)343 * 32 * M2LShape<C>::U * sizeof(C); }
+
 template <typename R, typename C>
 static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
+    constexpr int U = M2LShape<C>::U, NW = M2LShape<C>::NW;
     const FarLevel& F = p.far[l];
     const TreeLevel& T = p.lev[l];
     const TreeLevel& TP = p.lev[l - 1];
-    const size_t sm = (size_t)kNumOffsets * 32 * sizeof(C) + 216 * 9 * sizeof(short);
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(C) == 16]) {
-        MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr_set[sizeof(C) == 16] = true;
-    }
-    const dim3 grid(nblk(TP.nbox, kM2LWarps * kM2LParentsPerWarp), nblk(F.K, 32));
-    k_m2l<R, C><<<grid, 32 * kM2LWarps, sm, s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off, TP.m2l_src, T.key,
-                                                p.m2l_tab, (const C*)F.F, (const C*)F.T, F.K, (C*)F.G);
+    const dim3 grid(nblk(TP.nbox, NW * kM2LParentsPerWarp), nblk(F.K, 32 * U));
+    k_m2l<R, C, U, NW><<<grid, 32 * NW, m2l_smem<R, C>(), s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off,
+                                                               TP.m2l_src, T.key, p.off343, (const C*)F.F, (const C*)F.T,
+                                                               F.K, (C*)F.G);
     MLFMA_LAUNCH_CHECK();
+}
+
+// raise the dynamic shared-memory limit of the M2L kernel once (before any capture)
+void prepare_kernels(Plan& p) {
+    if (p.prec == MLFMA_PREC_FP64)
+        MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<double, double2, M2LShape<double2>::U, M2LShape<double2>::NW>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_smem<double, double2>()));
+    else
+        MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<float, float2, M2LShape<float2>::U, M2LShape<float2>::NW>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_smem<float, float2>()));
 }
 
 // ============================================================== phi transforms: mixed-radix FFTs in shared memory
@@ -749,7 +782,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         if (l == p.nlev) continue;
         FarLevel& Ch = p.far[l + 1];
         TreeLevel& TC = p.lev[l + 1];
-        const int Lc = Ch.L, nm = 2 * Lc + 1;
+        const int Lc = Ch.L;
         StageTimer st(p, MLFMA_STAGE_M2M, l, 3);
         const int64_t rows_c = TC.nbox * (int64_t)Ch.nth;
         const int budget = (int)(kFftSmemBytes / sizeof(C));
@@ -782,7 +815,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         }
         if (l > p.top) {
             FarLevel& Pf = p.far[l - 1];
-            const int Lc = F.L, nm = 2 * Lc + 1;
+            const int Lc = F.L;
             StageTimer st(p, MLFMA_STAGE_L2L, l, 3);
             const int budget = (int)(kFftSmemBytes / sizeof(C));
             int RT = tile_rows(Pf.nth, budget - Pf.nph, 8 * Pf.nph);

@@ -748,11 +748,15 @@ namespace mlfma {
 // ============================================================== M2L work lists
 // For every box P that has children at the next level: the children of P's colleagues
 // (other than P) that are far from at least one child of P, in ascending box order,
-// packed as (src * K) << 32 | far-children mask << 8 | (colleague slot * 8 + source octant),
+// packed as (src * K) << 32 | far-children mask << 16 | base,
 // src * K being the element offset of the source's samples at that level (< 2^32).  A child t of P and a
 // source s of slot (dx, dy, dz) are far when the offset
 //   ijk_t - ijk_s = -2 (dx, dy, dz) + bits(t) - bits(s)
-// has a component of magnitude >= 2 (they are then in each other's V lists).
+// has a component of magnitude >= 2 (they are then in each other's V lists).  The offset's
+// raster index (ox+3) + 7 (oy+3) + 49 (oz+3) in the 7^3 cube splits into a source part
+//   base = (3 - 2 dx - sx) + 7 (3 - 2 dy - sy) + 49 (3 - 2 dz - sz)     (0 .. 285)
+// and a child part tx + 7 ty + 49 tz (0 .. 57), so the M2L kernel finds the translation
+// row of every (child, source) pair by one addition.
 __device__ __forceinline__ bool far_pair(int slot, int cs, int ct) {
     const int d[3] = {slot % 3 - 1, (slot / 3) % 3 - 1, slot / 9 - 1};
     int m = 0;
@@ -785,9 +789,13 @@ __global__ void k_m2l_lists(int64_t nb, const int* __restrict__ coll, const int*
                 for (int t = cb[P]; t < ce[P]; ++t)
                     if (far_pair(qs[a], cs, (int)(ckey[t] & 7))) far_t |= 1u << (t - cb[P]);
                 if (!far_t) continue;
-                if (out)
-                    out[w0 + c] = ((unsigned long long)((int64_t)s * K) << 32) | ((unsigned long long)far_t << 8) |
-                                  (unsigned long long)(qs[a] * 8 + cs);
+                if (out) {
+                    const int sl = qs[a];
+                    const int base = (3 - 2 * (sl % 3 - 1) - (cs & 1)) + 7 * (3 - 2 * ((sl / 3) % 3 - 1) - ((cs >> 1) & 1)) +
+                                     49 * (3 - 2 * (sl / 9 - 1) - ((cs >> 2) & 1));
+                    out[w0 + c] = ((unsigned long long)((int64_t)s * K) << 32) | ((unsigned long long)far_t << 16) |
+                                  (unsigned long long)base;
+                }
                 ++c;
             }
     }
@@ -796,31 +804,6 @@ __global__ void k_m2l_lists(int64_t nb, const int* __restrict__ coll, const int*
 
 void build_m2l_lists(Plan& p) {
     cudaStream_t s = p.stream;
-    // (code, target octant) -> far-offset index
-    std::vector<short> tab(216 * 9, -1);
-    for (int code = 0; code < 216; ++code) {
-        const int slot = code / 8, cs = code % 8;
-        const int d[3] = {slot % 3 - 1, (slot / 3) % 3 - 1, slot / 9 - 1};
-        for (int ct = 0; ct < 8; ++ct) {
-            int o[3], m = 0;
-            for (int a = 0; a < 3; ++a) {
-                o[a] = -2 * d[a] + ((ct >> a) & 1) - ((cs >> a) & 1);
-                m = std::max(m, std::abs(o[a]));
-            }
-            if (m < 2) continue;
-            // compact index of offset (dx, dy, dz) in raster order dz, dy, dx over [-3,3]^3 minus [-1,1]^3
-            int ci = 0;
-            for (int dz = -3; dz <= 3; ++dz)
-                for (int dy = -3; dy <= 3; ++dy)
-                    for (int dx = -3; dx <= 3; ++dx) {
-                        if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) <= 1) continue;
-                        if (dx == o[0] && dy == o[1] && dz == o[2]) tab[code * 9 + ct] = (short)ci;
-                        ++ci;
-                    }
-        }
-    }
-    p.m2l_tab = p.mem.make<short>(216 * 9);
-    MLFMA_CUDA(cudaMemcpyAsync(p.m2l_tab, tab.data(), tab.size() * sizeof(short), cudaMemcpyHostToDevice, s));
     int* tmp = p.mem.make<int>(scan_tmp_ints(std::max<int64_t>(p.n, 1 << 20)) + 8);
     for (int l = std::max(p.top, 2); p.top && l <= p.nlev; ++l) {
         TreeLevel& P = p.lev[l - 1];
