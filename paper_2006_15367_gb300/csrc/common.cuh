@@ -116,10 +116,34 @@ struct TreeLevel {                 // one octree level (root = 1)
     int64_t m2l_n = 0;
 };
 
+// x / d for 0 <= x < 2^31 by multiply-high and shift (round-up multiplier, Granlund and
+// Montgomery 1994): q = (umulhi(x, m) + x) >> l with l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1
+struct FastDiv {
+    unsigned m = 1;
+    int l = 0;
+    static FastDiv make(unsigned d) {
+        FastDiv f;
+        while ((1ull << f.l) < d) ++f.l;
+        f.m = (unsigned)(((1ull << 32) * ((1ull << f.l) - d)) / d + 1);
+        return f;
+    }
+    __host__ __device__ __forceinline__ unsigned div(unsigned x) const {
+#ifdef __CUDA_ARCH__
+        return (__umulhi(x, m) + x) >> l;
+#else
+        return (unsigned)((((unsigned long long)x * m) >> 32) + x) >> l;
+#endif
+    }
+};
+
 struct FftPlan {                   // mixed-radix factorisation of an FFT length (radices 2, 3, 4, 5, 7)
     int n = 0;
     int ns = 0;
     int r[16] = {0};
+    // per Stockham stage st: Ns = r[0] ... r[st-1], nb = n / r[st] butterflies per row,
+    // tstep = n / (Ns r[st]) twiddle stride
+    int Ns[16] = {0}, nb[16] = {0}, tstep[16] = {0};
+    FastDiv dNs[16], dnb[16];
 };
 FftPlan make_fft_plan(int n);
 int smooth_even(int m);

@@ -29,6 +29,11 @@ static inline int tile_rows(int nrows, int budget, int per_row) {
     int r = budget > 0 ? budget / per_row : 1;
     return std::max(1, std::min(nrows, r));
 }
+// the smallest tile that covers nrows in as many tiles as tiles of rmax do
+static inline int balanced_rows(int nrows, int rmax) {
+    const int nt = (nrows + rmax - 1) / rmax;
+    return (nrows + nt - 1) / nt;
+}
 
 // ============================================================== C2M (warp per leaf)
 constexpr int kC2MPass = 4;   // samples per lane per pass
@@ -283,6 +288,18 @@ __global__ void __launch_bounds__(128) k_l2o_big(const int2* __restrict__ tiles,
 // costs NT predicated child slots.
 constexpr int kM2LParentsPerWarp = 4;
 
+// cp.async of B bytes global -> shared; v = false fills the B bytes with zeros (nothing is read)
+template <int B>
+__device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, bool v) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = v ? B : 0;
+    if constexpr (B == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(src), "n"(B), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename C, int U, int NT>
 __device__ __forceinline__ void m2l_parent(int lane, int t0, const uint64_t* __restrict__ ckey,
                                            const unsigned long long* __restrict__ le, int ne, const C* const (&Fp)[U],
@@ -338,10 +355,23 @@ __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p0 = (int64_t)blockIdx.y * TS;
     const int64_t P0 = (int64_t)blockIdx.x * (NW * kM2LParentsPerWarp);
-    for (int i = threadIdx.x; i < 343 * TS; i += blockDim.x) {
-        const int r = i / TS, l = i - r * TS;
-        const int o = off343[r];
-        Ts[i] = (o >= 0 && p0 + l < K) ? T[(int64_t)o * K + p0 + l] : cmake<C>(0, 0);
+    // stage the slice with asynchronous copies: warp w takes rows w, w + NW, ...; the far-offset
+    // index of each row is fetched once per warp; near rows and samples past K are zero-filled
+    static_assert(343 <= 32 * NW, "one far-offset index per lane");
+    {
+        const int nrw = (343 - warp + NW - 1) / NW;
+        const int myo = lane < nrw ? off343[warp + NW * lane] : -1;
+        for (int j = 0; j < nrw; ++j) {
+            const int r = warp + NW * j;
+            const int o = __shfl_sync(0xffffffffu, myo, j);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int l = lane + 32 * u;
+                const bool v = o >= 0 && p0 + l < K;
+                cp_async_zfill<sizeof(C)>(Ts + r * TS + l, v ? T + (int64_t)o * K + p0 + l : T, v);
+            }
+        }
+        cp_async_wait_all();
     }
     __syncthreads();
     const C* Fp[U];
@@ -435,13 +465,13 @@ __device__ __forceinline__ void root(int k, T& c, T& s) {
     }
 }
 
+// one radix-R butterfly of a Stockham stage: inputs a[j + r nb], outputs b[q Ns R + k + kk Ns]
+// with q = j / Ns, k = j mod Ns, twiddles tw[k r tstep]
 template <int R, bool INV, typename C>
-__device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict__ b, int j, int Ns, int n,
+__device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict__ b, int j, int nb, int Ns, int q, int tstep,
                                          const C* __restrict__ tw) {
     using T = decltype(C::x);
-    const int nb = n / R;
-    const int k = j % Ns;
-    const int tstep = n / (Ns * R);
+    const int k = j - q * Ns;
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -449,7 +479,7 @@ __device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict_
         if (r > 0) x = cmul(x, twid(tw, k * r * tstep, INV));
         v[r] = x;
     }
-    const int idxD = (j / Ns) * Ns * R + k;
+    const int idxD = q * Ns * R + k;
 #pragma unroll
     for (int kk = 0; kk < R; ++kk) {
         C acc = v[0];
@@ -464,42 +494,37 @@ __device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict_
     }
 }
 
+template <bool INV, typename C>
+__device__ __forceinline__ void fft_stage(const C* __restrict__ in, C* __restrict__ out, int nrows, const FftPlan& fp, int st,
+                                          const C* __restrict__ tw) {
+    const int n = fp.n, R = fp.r[st], nb = fp.nb[st], Ns = fp.Ns[st], tstep = fp.tstep[st];
+    const FastDiv dnb = fp.dnb[st], dNs = fp.dNs[st];
+    for (int idx = threadIdx.x; idx < nrows * nb; idx += blockDim.x) {
+        const int row = (int)dnb.div((unsigned)idx), j = idx - row * nb;
+        const int q = (int)dNs.div((unsigned)j);
+        const C* a = in + row * n;
+        C* b = out + row * n;
+        switch (R) {
+            case 2: fft_bfly<2, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
+            case 3: fft_bfly<3, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
+            case 4: fft_bfly<4, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
+            case 5: fft_bfly<5, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
+            default: fft_bfly<7, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
+        }
+    }
+}
+
 // Transforms nrows rows of length fp.n stored contiguously in buf0; returns the buffer
 // holding the result (buf0 or buf1).  All threads of the block take part.
 template <typename C>
 __device__ C* fft_rows(C* buf0, C* buf1, int nrows, const FftPlan& fp, const C* __restrict__ tw, bool inv) {
-    const int n = fp.n;
     C* in = buf0;
     C* out = buf1;
-    int Ns = 1;
     for (int st = 0; st < fp.ns; ++st) {
-        const int R = fp.r[st];
-        const int nb = n / R;
-        for (int idx = threadIdx.x; idx < nrows * nb; idx += blockDim.x) {
-            const int row = idx / nb, j = idx - row * nb;
-            const C* a = in + row * n;
-            C* b = out + row * n;
-            if (inv) {
-                switch (R) {
-                    case 2: fft_bfly<2, true>(a, b, j, Ns, n, tw); break;
-                    case 3: fft_bfly<3, true>(a, b, j, Ns, n, tw); break;
-                    case 4: fft_bfly<4, true>(a, b, j, Ns, n, tw); break;
-                    case 5: fft_bfly<5, true>(a, b, j, Ns, n, tw); break;
-                    default: fft_bfly<7, true>(a, b, j, Ns, n, tw); break;
-                }
-            } else {
-                switch (R) {
-                    case 2: fft_bfly<2, false>(a, b, j, Ns, n, tw); break;
-                    case 3: fft_bfly<3, false>(a, b, j, Ns, n, tw); break;
-                    case 4: fft_bfly<4, false>(a, b, j, Ns, n, tw); break;
-                    case 5: fft_bfly<5, false>(a, b, j, Ns, n, tw); break;
-                    default: fft_bfly<7, false>(a, b, j, Ns, n, tw); break;
-                }
-            }
-        }
+        if (inv) fft_stage<true>(in, out, nrows, fp, st, tw);
+        else fft_stage<false>(in, out, nrows, fp, st, tw);
         __syncthreads();
         C* t = in; in = out; out = t;
-        Ns *= R;
     }
     return in;
 }
@@ -510,10 +535,10 @@ __device__ __forceinline__ int wrap(int m, int n) { return m < 0 ? m + n : m; }
 constexpr size_t kFftSmemBytes = 20 * 1024;
 
 // M2M first step: X[mi][c][i] = scale sum_j F[c][i][j] e^{-i m phi_j}, |m| <= Lc, for the rows
-// r = c nth + i of all children (rows are contiguous in F; X is mode-major).
+// r = c nth + i of all children (rows are contiguous in F; X is mode-major).  dRB divides by RB.
 template <typename C, typename R>
 __global__ void k_fft_fwd_rows(int nrows_tot, const C* __restrict__ F, int Lc, FftPlan fp, const C* __restrict__ tw,
-                               R scale, int RB, C* __restrict__ X) {
+                               R scale, int RB, FastDiv dRB, C* __restrict__ X) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
     C* buf0 = reinterpret_cast<C*>(smem_raw);
@@ -522,28 +547,55 @@ __global__ void k_fft_fwd_rows(int nrows_tot, const C* __restrict__ F, int Lc, F
     const int r0 = blockIdx.x * RB;
     const int nr = min(RB, nrows_tot - r0);
     const C* src = F + (int64_t)r0 * n;
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = src[idx];
-    for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) cp_async_zfill<sizeof(C)>(buf0 + idx, src + idx, true);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) cp_async_zfill<sizeof(C)>(stw + j, tw + j, true);
+    cp_async_wait_all();
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
-    for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
-        const int row = idx % nr, mi = idx / nr;
+    for (int idx = threadIdx.x; idx < RB * nm; idx += blockDim.x) {
+        const int mi = (int)dRB.div((unsigned)idx), row = idx - mi * RB;
+        if (row >= nr) continue;
         C v = res[row * n + wrap(mi - Lc, n)];
         v.x *= scale; v.y *= scale;
         X[(int64_t)mi * nrows_tot + r0 + row] = v;
     }
 }
 
-// M2M last step, per parent P and tile of parent rows i' (the four xy-quadrants q are
-// transformed together, 4 nr rows per FFT pass):
+// children of parent P by xy-quadrant q = oct & 3 and z half oct >> 2 (-1: absent); the
+// present quadrants in ascending order.  Ends with a barrier.
+__device__ __forceinline__ int parent_quadrants(int c0, int c1, const uint64_t* __restrict__ ckey, int (*s_child)[2],
+                                                int* s_q, int* s_nq) {
+    if (threadIdx.x < 8) s_child[threadIdx.x >> 1][threadIdx.x & 1] = -1;
+    __syncthreads();
+    if ((int)threadIdx.x < c1 - c0) {
+        const int c = c0 + threadIdx.x;
+        const int oct = (int)(ckey[c] & 7);
+        s_child[oct & 3][oct >> 2] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nq = 0;
+        for (int q = 0; q < 4; ++q)
+            if (s_child[q][0] >= 0 || s_child[q][1] >= 0) s_q[nq++] = q;
+        *s_nq = nq;
+    }
+    __syncthreads();
+    return *s_nq;
+}
+
+// M2M last step, per parent P and tile of RT parent rows i' (the present xy-quadrants q are
+// transformed together):
 //   W_q[i'][m] = sum_{children c = (q, sz)} Sz[sz][i'] Y[mi][c][i']          (z part of the shift, per mode)
 //   F_P[i'][j'] = sum_q Sxy[q][i'][j'] sum_m W_q[i'][m] e^{+i m phi'_j'}     (inverse FFT, xy part of the shift)
+// dRT divides by RT, dn by n.
 template <typename C>
 __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict__ ce, const uint64_t* __restrict__ ckey,
                               int nbox_c, const C* __restrict__ Y, int Lc, int nthp, FftPlan fp, const C* __restrict__ tw,
-                              const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, C* __restrict__ Fp) {
+                              const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, FastDiv dRT, FastDiv dn,
+                              C* __restrict__ Fp) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_child[4][2];
+    __shared__ int s_q[4], s_nq;
     const int n = fp.n, nm = 2 * Lc + 1;
     const int64_t Kp = (int64_t)nthp * n;
     const int P = blockIdx.x;
@@ -554,40 +606,28 @@ __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict_
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     C* buf1 = buf0 + 4 * RT * n;
     C* stw = buf1 + 4 * RT * n;
-    __shared__ int s_q[4], s_nq;
-    if (threadIdx.x < 8) s_child[threadIdx.x >> 1][threadIdx.x & 1] = -1;
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int c = c0; c < c1; ++c) {
-            const int oct = (int)(ckey[c] & 7);
-            s_child[oct & 3][oct >> 2] = c;
-        }
-        int nq = 0;
-        for (int q = 0; q < 4; ++q)
-            if (s_child[q][0] >= 0 || s_child[q][1] >= 0) s_q[nq++] = q;
-        s_nq = nq;
-    }
-    __syncthreads();
-    const int nq = s_nq;
+    const int nq = parent_quadrants(c0, c1, ckey, s_child, s_q, &s_nq);
     for (int idx = threadIdx.x; idx < nq * nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
     __syncthreads();
     // rows of the qi-th present quadrant occupy buf0[(qi * nr + r) * n ...]
-    for (int idx = threadIdx.x; idx < nq * nr * nm; idx += blockDim.x) {
-        const int r = idx % nr, t = idx / nr;
-        const int qi = t % nq, mi = t / nq;
+    for (int qi = 0; qi < nq; ++qi) {
         const int q = s_q[qi];
         const int ca = s_child[q][0], cz = s_child[q][1];
-        const C* Ym = Y + (int64_t)mi * nbox_c * nthp;
-        C w = cmake<C>(0, 0);
-        if (ca >= 0) cfma(w, Sz[i0 + r], Ym[(int64_t)ca * nthp + i0 + r]);
-        if (cz >= 0) cfma(w, Sz[nthp + i0 + r], Ym[(int64_t)cz * nthp + i0 + r]);
-        buf0[(qi * nr + r) * n + wrap(mi - Lc, n)] = w;
+        for (int idx = threadIdx.x; idx < RT * nm; idx += blockDim.x) {
+            const int mi = (int)dRT.div((unsigned)idx), r = idx - mi * RT;
+            if (r >= nr) continue;
+            const C* Ym = Y + (int64_t)mi * nbox_c * nthp;
+            C w = cmake<C>(0, 0);
+            if (ca >= 0) cfma(w, Sz[i0 + r], Ym[(int64_t)ca * nthp + i0 + r]);
+            if (cz >= 0) cfma(w, Sz[nthp + i0 + r], Ym[(int64_t)cz * nthp + i0 + r]);
+            buf0[(qi * nr + r) * n + wrap(mi - Lc, n)] = w;
+        }
     }
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true);
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
-        const int r = idx / n, j = idx - r * n;
+        const int r = (int)dn.div((unsigned)idx), j = idx - r * n;
         C acc = cmake<C>(0, 0);
         for (int qi = 0; qi < nq; ++qi)
             cfma(acc, Sxy[(int64_t)s_q[qi] * Kp + (int64_t)(i0 + r) * n + j], res[(qi * nr + r) * n + j]);
@@ -595,15 +635,17 @@ __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict_
     }
 }
 
-// L2L first step, per parent P and tile of parent rows i' (four xy-quadrants in one FFT pass):
+// L2L first step, per parent P and tile of RT parent rows i' (present xy-quadrants in one FFT pass):
 //   V_q[i'][m] = (1/n) sum_j' conj(Sxy[q][i'][j']) G_P[i'][j'] e^{+i m phi'_j'},  |m| <= Lc
 //   Y[mi][c][i'] = conj(Sz[sz][i']) V_q[i'][m] for each child c = (q, sz)
 template <typename C, typename R>
 __global__ void k_l2l_fft_in(const int* __restrict__ cb, const int* __restrict__ ce, const uint64_t* __restrict__ ckey,
                              int nbox_c, const C* __restrict__ Gp, int Lc, int nthp, FftPlan fp, const C* __restrict__ tw,
-                             const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, R inv_n, C* __restrict__ Y) {
+                             const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, FastDiv dRT, FastDiv dn, R inv_n,
+                             C* __restrict__ Y) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_child[4][2];
+    __shared__ int s_q[4], s_nq;
     const int n = fp.n, nm = 2 * Lc + 1;
     const int64_t Kp = (int64_t)nthp * n;
     const int P = blockIdx.x;
@@ -614,48 +656,36 @@ __global__ void k_l2l_fft_in(const int* __restrict__ cb, const int* __restrict__
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     C* buf1 = buf0 + 4 * RT * n;
     C* stw = buf1 + 4 * RT * n;
-    __shared__ int s_q[4], s_nq;
-    if (threadIdx.x < 8) s_child[threadIdx.x >> 1][threadIdx.x & 1] = -1;
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int c = c0; c < c1; ++c) {
-            const int oct = (int)(ckey[c] & 7);
-            s_child[oct & 3][oct >> 2] = c;
-        }
-        int nq = 0;
-        for (int q = 0; q < 4; ++q)
-            if (s_child[q][0] >= 0 || s_child[q][1] >= 0) s_q[nq++] = q;
-        s_nq = nq;
-    }
-    __syncthreads();
-    const int nq = s_nq;
+    const int nq = parent_quadrants(c0, c1, ckey, s_child, s_q, &s_nq);
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
         const int64_t g = (int64_t)i0 * n + idx;
         const C gv = Gp[(int64_t)P * Kp + g];
-        const int r = idx / n, j = idx - r * n;
+        const int r = (int)dn.div((unsigned)idx), j = idx - r * n;
         for (int qi = 0; qi < nq; ++qi)
             buf0[(qi * nr + r) * n + j] = cmul(cconj(Sxy[(int64_t)s_q[qi] * Kp + g]), gv);
     }
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true);
-    for (int idx = threadIdx.x; idx < nq * nr * nm; idx += blockDim.x) {
-        const int r = idx % nr, t = idx / nr;
-        const int qi = t % nq, mi = t / nq;
+    for (int qi = 0; qi < nq; ++qi) {
         const int q = s_q[qi];
         const int ca = s_child[q][0], cz = s_child[q][1];
-        C v = res[(qi * nr + r) * n + wrap(mi - Lc, n)];
-        v.x *= inv_n; v.y *= inv_n;
-        C* Ym = Y + (int64_t)mi * nbox_c * nthp;
-        if (ca >= 0) Ym[(int64_t)ca * nthp + i0 + r] = cmul(cconj(Sz[i0 + r]), v);
-        if (cz >= 0) Ym[(int64_t)cz * nthp + i0 + r] = cmul(cconj(Sz[nthp + i0 + r]), v);
+        for (int idx = threadIdx.x; idx < RT * nm; idx += blockDim.x) {
+            const int mi = (int)dRT.div((unsigned)idx), r = idx - mi * RT;
+            if (r >= nr) continue;
+            C v = res[(qi * nr + r) * n + wrap(mi - Lc, n)];
+            v.x *= inv_n; v.y *= inv_n;
+            C* Ym = Y + (int64_t)mi * nbox_c * nthp;
+            if (ca >= 0) Ym[(int64_t)ca * nthp + i0 + r] = cmul(cconj(Sz[i0 + r]), v);
+            if (cz >= 0) Ym[(int64_t)cz * nthp + i0 + r] = cmul(cconj(Sz[nthp + i0 + r]), v);
+        }
     }
 }
 
 // L2L last step: G[c][i][j] += sum_m H[mi][c][i] e^{-i m phi_j} for the rows r = c nth + i of all children.
 template <typename C>
 __global__ void k_l2l_fft_out(int nrows_tot, const C* __restrict__ H, int Lc, FftPlan fp, const C* __restrict__ tw, int RB,
-                              C* __restrict__ G) {
+                              FastDiv dRB, C* __restrict__ G) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
     C* buf0 = reinterpret_cast<C*>(smem_raw);
@@ -666,14 +696,158 @@ __global__ void k_l2l_fft_out(int nrows_tot, const C* __restrict__ H, int Lc, Ff
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nr * nm; idx += blockDim.x) {
-        const int row = idx % nr, mi = idx / nr;
+    for (int idx = threadIdx.x; idx < RB * nm; idx += blockDim.x) {
+        const int mi = (int)dRB.div((unsigned)idx), row = idx - mi * RB;
+        if (row >= nr) continue;
         buf0[row * n + wrap(mi - Lc, n)] = H[(int64_t)mi * nrows_tot + r0 + row];
     }
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
     C* g0 = G + (int64_t)r0 * n;
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) g0[idx] = cadd(g0[idx], res[idx]);
+}
+
+// ============================================================== fused phi transform + theta map (fine levels)
+// For level pairs whose child rows fit in shared memory a CTA takes CPB (2 ... 16, a power
+// of two) consecutive child boxes and keeps the spectral rows on chip between the phi transform and
+// the theta map.  The theta map is register-blocked over the CTA's children: a thread owns
+// one (mode, output row) pair and one accumulator per child, so each map entry is loaded
+// once per CTA and the spectral samples are shared-memory broadcasts.
+constexpr int kMaxCPB = 16;
+
+// M2M first two steps:  Y[mi][c][i'] = scale sum_i At[|m|][i][i'] sum_j F[c][i][j] e^{-i m phi_j}.
+// dnthp divides by nthp.
+template <typename C, typename R, int CPB>
+__global__ void k_m2m_in(int nbox_c, const C* __restrict__ F, int Lc, int nthc, int nthp, FftPlan fp,
+                         const C* __restrict__ tw, R scale, const R* __restrict__ At, FastDiv dnthp, C* __restrict__ Y) {
+    extern __shared__ unsigned char smem_raw[];
+    const int n = fp.n, nm = 2 * Lc + 1;
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + CPB * nthc * n;
+    C* stw = buf1 + CPB * nthc * n;
+    const int c0 = blockIdx.x * CPB;
+    const int ncb = min(CPB, nbox_c - c0);
+    const int nr = ncb * nthc;
+    const C* src = F + (int64_t)c0 * nthc * n;
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) cp_async_zfill<sizeof(C)>(buf0 + idx, src + idx, true);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) cp_async_zfill<sizeof(C)>(stw + j, tw + j, true);
+    cp_async_wait_all();
+    __syncthreads();
+    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
+    const int rowc = nthc * n;                     // stride between children in res
+    for (int idx = threadIdx.x; idx < nm * nthp; idx += blockDim.x) {
+        const int mi = (int)dnthp.div((unsigned)idx), o = idx - mi * nthp;
+        const int m = abs(mi - Lc);
+        const R* Am = At + (int64_t)m * nthc * nthp + o;
+        const C* xr = res + wrap(mi - Lc, n);
+        C acc[CPB];
+#pragma unroll
+        for (int c = 0; c < CPB; ++c) acc[c] = cmake<C>(0, 0);
+        for (int i = 0; i < nthc; ++i) {
+            const R a = Am[i * nthp];
+            const C* xi = xr + i * n;
+#pragma unroll
+            for (int c = 0; c < CPB; ++c)
+                if (c < ncb) crfma(acc[c], a, xi[c * rowc]);
+        }
+        C* yo = Y + ((int64_t)mi * nbox_c + c0) * nthp + o;
+#pragma unroll
+        for (int c = 0; c < CPB; ++c)
+            if (c < ncb) yo[c * nthp] = cmake<C>(acc[c].x * scale, acc[c].y * scale);
+    }
+}
+
+// L2L last two steps:  G[c][i][j] += sum_m e^{-i m phi_j} sum_i' Bt[|m|][i'][i] H[mi][c][i'].
+// The CTA's slice of H is staged in shared memory first.  dnthc divides by nthc, dhrow by
+// ncb nthp (dhfull: CPB nthp, the value for every CTA but the last).
+template <typename C, typename R, int CPB>
+__global__ void k_l2l_out(int nbox_c, const C* __restrict__ H, int Lc, int nthc, int nthp, FftPlan fp,
+                          const C* __restrict__ tw, const R* __restrict__ Bt, FastDiv dnthc, FastDiv dhrow,
+                          FastDiv dhfull, C* __restrict__ G) {
+    extern __shared__ unsigned char smem_raw[];
+    const int n = fp.n, nm = 2 * Lc + 1;
+    C* buf0 = reinterpret_cast<C*>(smem_raw);
+    C* buf1 = buf0 + CPB * nthc * n;
+    C* stw = buf1 + CPB * nthc * n;
+    C* hs = stw + n;                               // [nm][CPB][nthp]
+    const int c0 = blockIdx.x * CPB;
+    const int ncb = min(CPB, nbox_c - c0);
+    const int nr = ncb * nthc;
+    const int hrow = ncb * nthp;                   // contiguous run of the CTA's children in one mode
+    for (int idx = threadIdx.x; idx < nm * hrow; idx += blockDim.x) {
+        const int mi = (int)(ncb == CPB ? dhfull : dhrow).div((unsigned)idx), t = idx - mi * hrow;
+        cp_async_zfill<sizeof(C)>(hs + mi * CPB * nthp + t, H + ((int64_t)mi * nbox_c + c0) * nthp + t, true);
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) cp_async_zfill<sizeof(C)>(stw + j, tw + j, true);
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nm * nthc; idx += blockDim.x) {
+        const int mi = (int)dnthc.div((unsigned)idx), i = idx - mi * nthc;
+        const int m = abs(mi - Lc);
+        const R* Bm = Bt + (int64_t)m * nthp * nthc + i;
+        const C* hm = hs + mi * CPB * nthp;
+        C acc[CPB];
+#pragma unroll
+        for (int c = 0; c < CPB; ++c) acc[c] = cmake<C>(0, 0);
+        for (int ip = 0; ip < nthp; ++ip) {
+            const R b = Bm[ip * nthc];
+#pragma unroll
+            for (int c = 0; c < CPB; ++c)
+                if (c < ncb) crfma(acc[c], b, hm[c * nthp + ip]);
+        }
+        const int col = wrap(mi - Lc, n);
+#pragma unroll
+        for (int c = 0; c < CPB; ++c)
+            if (c < ncb) buf0[(c * nthc + i) * n + col] = acc[c];
+    }
+    __syncthreads();
+    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
+    C* g0 = G + (int64_t)c0 * nthc * n;
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) g0[idx] = cadd(g0[idx], res[idx]);
+}
+
+// children per CTA of the fused kernels, a power of two in [2, kMaxCPB] (0: the level pair
+// takes the three-kernel path); extra = complex elements per child staged besides the two
+// FFT buffers
+constexpr size_t kFusedSmemBytes = 40 * 1024;
+static int fused_children(int nthc, int n, int extra, size_t csz) {
+    const size_t per = ((size_t)2 * nthc * n + extra) * csz;
+    const size_t avail = kFusedSmemBytes - (size_t)n * csz;
+    int c = 0;
+    for (int t = 2; t <= kMaxCPB; t *= 2)
+        if ((size_t)t * per <= avail) c = t;
+    return c;
+}
+
+template <typename C, typename R>
+static void launch_m2m_in(int CPB, int nbox_c, const C* F, int Lc, int nthc, int nthp, const FftPlan& fp, const C* tw,
+                          R scale, const R* At, C* Y, cudaStream_t s) {
+    const size_t sm = ((size_t)2 * CPB * nthc * fp.n + fp.n) * sizeof(C);
+    const FastDiv d = FastDiv::make(nthp);
+    switch (CPB) {
+#define M2M_IN(c) case c: k_m2m_in<C, R, c><<<nblk(nbox_c, c), 128, sm, s>>>(nbox_c, F, Lc, nthc, nthp, fp, tw, scale, At, d, Y); break;
+        M2M_IN(2) M2M_IN(4) M2M_IN(8) M2M_IN(16)
+#undef M2M_IN
+        default: fail(MLFMA_ERR_INVALID_ARG, "children per CTA %d", CPB);
+    }
+    MLFMA_LAUNCH_CHECK();
+}
+
+template <typename C, typename R>
+static void launch_l2l_out(int CPB, int nbox_c, const C* H, int Lc, int nthc, int nthp, const FftPlan& fp, const C* tw,
+                           const R* Bt, C* G, cudaStream_t s) {
+    const size_t sm = ((size_t)CPB * (2 * nthc * fp.n + (2 * Lc + 1) * nthp) + fp.n) * sizeof(C);
+    const FastDiv d = FastDiv::make(nthc);
+    const int tail = nbox_c % CPB ? nbox_c % CPB : CPB;      // children of the last CTA
+    const FastDiv dt = FastDiv::make(tail * nthp), df = FastDiv::make(CPB * nthp);
+    switch (CPB) {
+#define L2L_OUT(c) case c: k_l2l_out<C, R, c><<<nblk(nbox_c, c), 128, sm, s>>>(nbox_c, H, Lc, nthc, nthp, fp, tw, Bt, d, dt, df, G); break;
+        L2L_OUT(2) L2L_OUT(4) L2L_OUT(8) L2L_OUT(16)
+#undef L2L_OUT
+        default: fail(MLFMA_ERR_INVALID_ARG, "children per CTA %d", CPB);
+    }
+    MLFMA_LAUNCH_CHECK();
 }
 
 // ============================================================== theta maps
@@ -783,25 +957,32 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         FarLevel& Ch = p.far[l + 1];
         TreeLevel& TC = p.lev[l + 1];
         const int Lc = Ch.L;
-        StageTimer st(p, MLFMA_STAGE_M2M, l, 3);
         const int64_t rows_c = TC.nbox * (int64_t)Ch.nth;
         const int budget = (int)(kFftSmemBytes / sizeof(C));
-        // A: forward FFT of the children's rows, modes |m| <= Lc
-        int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - Ch.nph, 2 * Ch.nph);
-        size_t sm = ((size_t)2 * RB * Ch.nph + Ch.nph) * sizeof(C);
-        k_fft_fwd_rows<C, R><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, (const C*)Ch.F, Lc, Ch.fft, (const C*)Ch.tw,
-                                                                  (R)(1.0 / Ch.nph), RB, (C*)F.X);
-        MLFMA_LAUNCH_CHECK();
-        // B: theta maps per mode
-        launch_theta_map<R, C>(TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, (const C*)F.X, (C*)F.Y, s);
+        const int CPB = fused_children(Ch.nth, Ch.nph, 0, sizeof(C));
+        StageTimer st(p, MLFMA_STAGE_M2M, l, CPB ? 2 : 3);
+        size_t sm;
+        if (CPB) {
+            // A+B: forward FFT of the children's rows and theta maps, on chip
+            launch_m2m_in<C, R>(CPB, (int)TC.nbox, (const C*)Ch.F, Lc, Ch.nth, F.nth, Ch.fft, (const C*)Ch.tw,
+                                (R)(1.0 / Ch.nph), (const R*)F.At, (C*)F.Y, s);
+        } else {
+            // A: forward FFT of the children's rows, modes |m| <= Lc
+            int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - Ch.nph, 2 * Ch.nph);
+            sm = ((size_t)2 * RB * Ch.nph + Ch.nph) * sizeof(C);
+            k_fft_fwd_rows<C, R><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, (const C*)Ch.F, Lc, Ch.fft,
+                                                                      (const C*)Ch.tw, (R)(1.0 / Ch.nph), RB,
+                                                                      FastDiv::make(RB), (C*)F.X);
+            MLFMA_LAUNCH_CHECK();
+            // B: theta maps per mode
+            launch_theta_map<R, C>(TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, (const C*)F.X, (C*)F.Y, s);
+        }
         // C: z-shift per mode, inverse FFT, xy-shift, sum over children
-        int RT = tile_rows(F.nth, budget - F.nph, 8 * F.nph);
+        int RT = balanced_rows(F.nth, tile_rows(F.nth, budget - F.nph, 8 * F.nph));
         sm = ((size_t)8 * RT * F.nph + F.nph) * sizeof(C);
-        k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(T.child_begin, T.child_end, TC.key,
-                                                                                  (int)TC.nbox, (const C*)F.Y, Lc, F.nth,
-                                                                                  F.fft,
-                                                                                  (const C*)F.tw, (const C*)F.Sz,
-                                                                                  (const C*)F.Sxy, RT, (C*)F.F);
+        k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(
+            T.child_begin, T.child_end, TC.key, (int)TC.nbox, (const C*)F.Y, Lc, F.nth, F.fft, (const C*)F.tw,
+            (const C*)F.Sz, (const C*)F.Sxy, RT, FastDiv::make(RT), FastDiv::make(F.nph), (C*)F.F);
         MLFMA_LAUNCH_CHECK();
     }
     // ---- downward pass: M2L, L2L, L2O
@@ -816,21 +997,29 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         if (l > p.top) {
             FarLevel& Pf = p.far[l - 1];
             const int Lc = F.L;
-            StageTimer st(p, MLFMA_STAGE_L2L, l, 3);
+            const int CPB = fused_children(F.nth, F.nph, (2 * Lc + 1) * Pf.nth, sizeof(C));
+            StageTimer st(p, MLFMA_STAGE_L2L, l, CPB ? 2 : 3);
             const int budget = (int)(kFftSmemBytes / sizeof(C));
-            int RT = tile_rows(Pf.nth, budget - Pf.nph, 8 * Pf.nph);
+            int RT = balanced_rows(Pf.nth, tile_rows(Pf.nth, budget - Pf.nph, 8 * Pf.nph));
             size_t sm = ((size_t)8 * RT * Pf.nph + Pf.nph) * sizeof(C);
             k_l2l_fft_in<C, R><<<dim3((unsigned)TP.nbox, nblk(Pf.nth, RT)), 128, sm, s>>>(
                 TP.child_begin, TP.child_end, T.key, (int)T.nbox, (const C*)Pf.G, Lc, Pf.nth, Pf.fft, (const C*)Pf.tw,
-                (const C*)Pf.Sz, (const C*)Pf.Sxy, RT, (R)(1.0 / Pf.nph), (C*)Pf.Y);
+                (const C*)Pf.Sz, (const C*)Pf.Sxy, RT, FastDiv::make(RT), FastDiv::make(Pf.nph), (R)(1.0 / Pf.nph),
+                (C*)Pf.Y);
             MLFMA_LAUNCH_CHECK();
-            launch_theta_map<R, C>(T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, (const C*)Pf.Y, (C*)Pf.X, s);
-            const int64_t rows_c = T.nbox * (int64_t)F.nth;
-            int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * F.nph);
-            sm = ((size_t)2 * RB * F.nph + F.nph) * sizeof(C);
-            k_l2l_fft_out<C><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, (const C*)Pf.X, Lc, F.fft, (const C*)F.tw, RB,
-                                                                (C*)F.G);
-            MLFMA_LAUNCH_CHECK();
+            if (CPB) {
+                // theta maps and inverse FFT of the children's rows, on chip; added to G
+                launch_l2l_out<C, R>(CPB, (int)T.nbox, (const C*)Pf.Y, Lc, F.nth, Pf.nth, F.fft, (const C*)F.tw,
+                                     (const R*)Pf.Bt, (C*)F.G, s);
+            } else {
+                launch_theta_map<R, C>(T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, (const C*)Pf.Y, (C*)Pf.X, s);
+                const int64_t rows_c = T.nbox * (int64_t)F.nth;
+                int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * F.nph);
+                sm = ((size_t)2 * RB * F.nph + F.nph) * sizeof(C);
+                k_l2l_fft_out<C><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, (const C*)Pf.X, Lc, F.fft, (const C*)F.tw,
+                                                                    RB, FastDiv::make(RB), (C*)F.G);
+                MLFMA_LAUNCH_CHECK();
+            }
         }
         if (T.nleaf > 0) {
             StageTimer st(p, MLFMA_STAGE_L2O, l, (T.n_small_leaves > 0) + (T.n_big_tiles > 0));

@@ -41,6 +41,15 @@ FftPlan make_fft_plan(int n) {
             m /= r;
         }
     if (m != 1) fail(MLFMA_ERR_UNSUPPORTED, "FFT length %d is not 7-smooth", n);
+    int Ns = 1;
+    for (int st = 0; st < p.ns; ++st) {
+        p.Ns[st] = Ns;
+        p.nb[st] = n / p.r[st];
+        p.tstep[st] = n / (Ns * p.r[st]);
+        p.dNs[st] = FastDiv::make((unsigned)Ns);
+        p.dnb[st] = FastDiv::make((unsigned)p.nb[st]);
+        Ns *= p.r[st];
+    }
     return p;
 }
 
