@@ -31,6 +31,8 @@ import numpy as np  # noqa: E402
 WORKLOAD = "sphere1m"
 DIGITS = 3
 SAMPLE_TARGETS = 2000
+CPU_BASELINE_TARGETS = 6144          # about 10 s of FP64 direct sum on 16 host cores at N = 2^20
+METRIC = "MLFMA matvec points/s at stated rel. err vs FP64 direct; % HBM roofline"
 
 
 def _dist():
@@ -122,13 +124,45 @@ def work_model(info):
             "L2L": {"flops": interp_flops}}
 
 
+KERNEL_SOURCES = ("paper_2006_15367_gb300/csrc/far.cu", "paper_2006_15367_gb300/csrc/common.cuh")
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, precision, nrhs, mode):
+    """DRAM bytes (read + write) of k_m2l per step from a committed ncu summary, or None.
+
+    The summary records the hash of the kernel sources it was taken on; a different hash
+    (the kernel changed since) gives None.
+    """
+    if (workload, precision, nrhs, mode) != ("sphere1m", "fp32", 1, "apply"):
+        return None
+    p = os.path.join(ROOT, "profiles", "k_m2l_sphere1m.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for ln in open(p):
+        if ln.startswith("- ") and ":" in ln:
+            k, v = ln[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256_16") != source_hash() or "dram_bytes_per_step" not in vals:
+        return None
+    return {"bytes_per_step": float(vals["dram_bytes_per_step"]), "source": "profiles/k_m2l_sphere1m.md"}
+
+
 def run_reference(args, ws, rank):
     """CPU oracle: FP64 direct sum at a bounded sample of targets per step."""
     if rank != 0:
         return 0
     import synth
     from oracle import direct
-    pts, q, prm = synth.workload(WORKLOAD)
+    pts, q, prm, _ = load_case(args.workload)
     n = pts.shape[0]
     per_step = 256
     rng = np.random.default_rng(123)
@@ -140,10 +174,10 @@ def run_reference(args, ws, rank):
         direct.direct(pts, q[0], prm["k"], targets=np.sort(rng.choice(n, per_step, replace=False)))
     dt = (time.perf_counter() - t0) / args.steps
     v = per_step / dt
-    line = {"impl": "reference", "metric": "MLFMA matvec points/s (rel. err vs FP64 direct)", "value": v,
+    line = {"impl": "reference", "metric": METRIC, "value": v,
             "unit": "points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "sphere N=1048576 r=32 wavelengths, k=2pi, 3 digits", "n": n},
+            "config": config_dict(args, n, prm),
             "cpu_baseline": {"value": v, "unit": "points/s", "cores": cores, "kind": "oracle",
                              "sample": f"FP64 direct sum over all {n} sources at {per_step} random targets per step"},
             "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -161,6 +195,15 @@ WORKLOADS = {
     "batch256": "256 random ellipsoids (semi-axes U(2,16) wavelengths, N log-uniform 1000..65536) in one batched "
                 "plan, leaf 0.25 wavelength, 3 digits",
 }
+
+
+def config_dict(args, n, prm):
+    """The workload description shared by both arms of the benchmark."""
+    return {"workload": WORKLOADS[args.workload] + f", {args.precision.upper()} complex, nrhs={args.nrhs}"
+                        + (", forward+backward (charges and positions)" if args.mode == "grad" else ""),
+            "n": n, "digits": prm["digits"], "nrhs": args.nrhs, "mode": args.mode,
+            "parallelism": f"replicas x{_dist()[0]}",
+            "l2": "flushed between steps (256 MiB write outside the timed events)"}
 
 
 def load_case(name):
@@ -340,31 +383,38 @@ def main():
         dref, got = torch.cat(drefs), torch.cat(gots)
     rel_err = float(torch.linalg.norm(got - dref) / torch.linalg.norm(dref))
 
-    # ---- roofline of the dominant stage
+    # ---- roofline of the dominant kernel: k_m2l (one launch per far level, timed by the M2L stage events)
     pk, pk_kind = peaks()
-    dom = max((s for s in ("M2L", "M2M", "L2L", "P2P", "C2M", "L2O")), key=lambda s: stage_ms.get(s, 0.0))
     sm_max = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
-    roof = {"kernel": dom, "bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
+    roof = {"kernel": "k_m2l", "bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s", "achieved": None, "frac": None,
+            "traffic": None,
             "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (clock from MEASURED_PEAKS.json)"}
     m2l = None
+    stages = None
     if offsets is None and info["top"]:
         wm = work_model(info)
         reps = nrhs * (2 if args.mode == "grad" else 1)
-        if dom in wm:
-            ach = wm[dom]["flops"] * reps / (stage_ms[dom] / 1e3) / 1e12
-            roof.update({"achieved": ach, "frac": ach / fp32_peak})
+        nl = info["nlev"] - info["top"] + 1
+        ach = wm["M2L"]["flops"] * reps / (stage_ms["M2L"] / 1e3) / 1e12
+        roof.update({"achieved": ach, "frac": ach / fp32_peak, "launches_per_step": nl * reps,
+                     "work": "8 flops per complex MAC x sum over levels of nv_l K_l (per step, all launches)"})
+        tr = measured_traffic(args.workload, args.precision, nrhs, args.mode)
+        if tr is not None:
+            roof["traffic"] = tr["bytes_per_step"]
+            roof["traffic_source"] = tr["source"]
         m2l = {"ms": stage_ms["M2L"], "flops": wm["M2L"]["flops"] * reps, "unique_bytes": wm["M2L"]["bytes"] * reps,
-               "tflops": wm["M2L"]["flops"] * reps / (stage_ms["M2L"] / 1e3) / 1e12,
+               "tflops": ach,
                "hbm_frac_unique_bytes": wm["M2L"]["bytes"] * reps / (stage_ms["M2L"] / 1e3) / 1e9 / pk["hbm_gbs"]}
-    if "achieved" not in roof:
-        roof.update({"achieved": None, "frac": None})
+        stages = {s: {"ms": stage_ms[s], "dense_equiv_tflops": wm[s]["flops"] * reps / (stage_ms[s] / 1e3) / 1e12}
+                  for s in ("M2M", "L2L")}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import direct
         a, b, tgl = groups[0]
-        ct = tgl[:512]
+        ct = tgl if offsets is not None else np.sort(
+            np.random.default_rng(77).choice(b - a, min(CPU_BASELINE_TARGETS, b - a), replace=False))
         t0 = time.perf_counter()
         cref = direct.direct(pts[a:b], q0[a:b], prm["k"], targets=ct)
         cdt_s = time.perf_counter() - t0
@@ -374,19 +424,17 @@ def main():
                          f"sources of their geometry",
                "rel_err_gpu_vs_oracle_direct": float(np.linalg.norm(o0h[ct] - cref) / np.linalg.norm(cref))}
 
-    cfg = {"workload": WORKLOADS[args.workload] + f", {args.precision.upper()} complex, nrhs={nrhs}"
-                       + (", forward+backward (charges and positions)" if args.mode == "grad" else ""),
-           "n": n, "digits": prm["digits"], "nrhs": nrhs, "mode": args.mode, "levels": info["nlev"], "L": info["L"],
-           "n_geom": info["n_geom"], "parallelism": f"replicas x{ws}",
-           "l2": "flushed between steps (256 MiB write outside the timed events)"}
+    cfg = config_dict(args, n, prm)
     line = {
-        "metric": "MLFMA matvec points/s at stated rel. err vs FP64 direct; % HBM roofline",
+        "metric": METRIC,
         "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 (fp32)" if args.precision == "fp32" else "c128 (fp64)", "data": "synthetic", "config": cfg,
         "accuracy": {"rel_err_vs_fp64_direct": rel_err, "targets": int(sum(len(g[2]) for g in groups)),
                      "reference": "GPU FP64 direct sum"},
-        "stage_ms": stage_ms, "setup_ms": info["setup_ms"], "m2l": m2l,
+        "plan": {"levels": info["nlev"], "top": info["top"], "L": info["L"], "n_geom": info["n_geom"],
+                 "device_bytes": info["device_bytes"]},
+        "stage_ms": stage_ms, "setup_ms": info["setup_ms"], "m2l": m2l, "interp_rates": stages,
         "roofline": roof, "peaks_source": pk_kind, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
     }

@@ -153,8 +153,8 @@ void mlfma_options_init(mlfma_options* opt);
  *   opt      NULL = defaults.
  *   out      receives the plan (NULL on error).
  * Errors: INVALID_ARG (n < 1, k, digits, leaf_max < 0, null pointers, non-finite
- * coordinates), UNSUPPORTED (uniform tree deeper than max_depth, adaptive trees
- * in this build), OUT_OF_MEMORY, CUDA.  Synchronises the plan stream.
+ * coordinates), UNSUPPORTED (uniform tree deeper than max_depth; more than 2^32
+ * far-field samples on one level), OUT_OF_MEMORY, CUDA.  Synchronises the plan stream.
  */
 mlfma_status mlfma_plan_create(const double* points, int64_t n, double k, int digits, int leaf_max,
                                const mlfma_options* opt, mlfma_plan** out);
