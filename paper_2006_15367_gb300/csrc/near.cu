@@ -4,8 +4,8 @@
 //
 // P2P for a target leaf b sums q_j e^{ikR}/R over the points of its near sources
 // (U list; W and X lists of adaptive trees), skipping R = 0 (the point itself and
-// coincident points).  One warp per target leaf; the source points of each source
-// box are staged through shared memory relative to the target leaf centre (FP64
+// coincident points).  One warp per target leaf; the source points of its near boxes
+// are staged through shared memory relative to the target leaf centre (FP64
 // difference, then rounded), lanes split (target, source slice) and the slices are
 // combined with warp shuffles.
 #include <cstdio>
@@ -39,14 +39,22 @@ struct LevelRanges {
 };
 
 // GRAD: also grad phi_i = sum_j q_j e^{ikR} (ikR - 1) / R^3 (r_i - r_j), written to grads[3 i + a].
+// The near sources of the leaf are read as one stream over its near boxes: each round the
+// lanes take up to 32 boxes, scan their point counts and fill up to kP2PSlots staged
+// sources (a lane finds the box of its slot by a binary search over the scanned counts),
+// so the loads of many small boxes are in flight together.  (eb, oe) is the stream
+// cursor: box entry and points of it already consumed.
+constexpr int kP2PSlots = 128;
+
 template <typename R, typename C, bool GRAD>
 __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restrict__ leaves, const int* __restrict__ leaf_level,
                                              const int* __restrict__ leaf_box, const int* __restrict__ near_off,
                                              const int* __restrict__ near_lev, const int* __restrict__ near_box, LevelRanges LR,
                                              const double* __restrict__ pos, const C* __restrict__ qs, R kpi,
                                              C* __restrict__ phis, C* __restrict__ grads) {
-    __shared__ R sx[4][32], sy[4][32], sz[4][32];
-    __shared__ C sq[4][32];
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ R sx[4][kP2PSlots], sy[4][kP2PSlots], sz[4][kP2PSlots];
+    __shared__ C sq[4][kP2PSlots];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t wi = (int64_t)blockIdx.x * 4 + wl;
     if (wi >= nleaf) return;
@@ -72,45 +80,78 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
         C acc = cmake<C>(0, 0);
         C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
         const R kk = kpi * (R)M_PI;
-        for (int e = s_lo; e < s_hi; ++e) {
-            const int ls = near_lev[e], bs = near_box[e];
-            const int u0 = LR.begin[ls][bs], u1 = LR.end[ls][bs];
-            for (int k0 = u0; k0 < u1; k0 += 32) {
-                const int cnt = min(32, u1 - k0);
-                if (lane < cnt) {
-                    int64_t j = k0 + lane;
-                    sx[wl][lane] = (R)(pos[3 * j] - cx);
-                    sy[wl][lane] = (R)(pos[3 * j + 1] - cy);
-                    sz[wl][lane] = (R)(pos[3 * j + 2] - cz);
-                    sq[wl][lane] = qs[j];
+        int eb = s_lo, oe = 0;
+        while (eb < s_hi) {
+            const int e = eb + lane;
+            int u0 = 0, cnt = 0;
+            if (e < s_hi) {
+                const int ls = near_lev[e], bs = near_box[e];
+                u0 = LR.begin[ls][bs];
+                cnt = LR.end[ls][bs] - u0;
+            }
+            if (lane == 0) { u0 += oe; cnt -= oe; }
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const int exc = inc - cnt;
+            const int all = __shfl_sync(FULL, inc, 31);
+            const int total = min(all, kP2PSlots);
+            for (int s0 = 0; s0 < total; s0 += 32) {
+                const int sidx = s0 + lane;
+                int q = 0;                       // first lane whose inclusive count exceeds sidx
+#pragma unroll
+                for (int st = 16; st >= 1; st >>= 1) {
+                    const int v = __shfl_sync(FULL, inc, q + st - 1);
+                    if (v <= sidx) q += st;
                 }
-                __syncwarp();
-                if (tp < np) {
-                    for (int jj = sl; jj < cnt; jj += S) {
-                        R dx = x - sx[wl][jj], dy = y - sy[wl][jj], dz = z - sz[wl][jj];
-                        R r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 > (R)0) {
-                            R inv = rsq(r2);
-                            R r = r2 * inv;
-                            R s, c;
-                            scpi(kpi * r, s, c);
-                            if (!GRAD) {
-                                cfma(acc, sq[wl][jj], cmake<C>(c * inv, s * inv));
-                            } else {
-                                const C qe = cmul(sq[wl][jj], cmake<C>(c * inv, s * inv));   // q e^{ikR} / R
-                                acc = cadd(acc, qe);
-                                // q e^{ikR} (ikR - 1) / R^3 = qe (ikR - 1) / R^2
-                                const R i2 = inv * inv;
-                                const C g = cmul(qe, cmake<C>(-i2, kk * r * i2));
-                                ga[0] = cadd(ga[0], cmake<C>(g.x * dx, g.y * dx));
-                                ga[1] = cadd(ga[1], cmake<C>(g.x * dy, g.y * dy));
-                                ga[2] = cadd(ga[2], cmake<C>(g.x * dz, g.y * dz));
-                            }
+                const int uq = __shfl_sync(FULL, u0, q), xq = __shfl_sync(FULL, exc, q);
+                if (sidx < total) {
+                    const int64_t j = uq + (sidx - xq);
+                    sx[wl][sidx] = (R)(pos[3 * j] - cx);
+                    sy[wl][sidx] = (R)(pos[3 * j + 1] - cy);
+                    sz[wl][sidx] = (R)(pos[3 * j + 2] - cz);
+                    sq[wl][sidx] = qs[j];
+                }
+            }
+            // advance the cursor past the consumed points
+            const int qn = __popc(__ballot_sync(FULL, inc <= total));
+            if (total == all) {
+                eb += 32;
+                oe = 0;
+            } else {
+                const int xn = __shfl_sync(FULL, exc, qn);
+                oe = (qn == 0 ? oe : 0) + (total - xn);
+                eb += qn;
+            }
+            __syncwarp();
+            if (tp < np) {
+                for (int jj = sl; jj < total; jj += S) {
+                    R dx = x - sx[wl][jj], dy = y - sy[wl][jj], dz = z - sz[wl][jj];
+                    R r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 > (R)0) {
+                        R inv = rsq(r2);
+                        R r = r2 * inv;
+                        R s, c;
+                        scpi(kpi * r, s, c);
+                        if (!GRAD) {
+                            cfma(acc, sq[wl][jj], cmake<C>(c * inv, s * inv));
+                        } else {
+                            const C qe = cmul(sq[wl][jj], cmake<C>(c * inv, s * inv));   // q e^{ikR} / R
+                            acc = cadd(acc, qe);
+                            // q e^{ikR} (ikR - 1) / R^3 = qe (ikR - 1) / R^2
+                            const R i2 = inv * inv;
+                            const C g = cmul(qe, cmake<C>(-i2, kk * r * i2));
+                            ga[0] = cadd(ga[0], cmake<C>(g.x * dx, g.y * dx));
+                            ga[1] = cadd(ga[1], cmake<C>(g.x * dy, g.y * dy));
+                            ga[2] = cadd(ga[2], cmake<C>(g.x * dz, g.y * dz));
                         }
                     }
                 }
-                __syncwarp();
             }
+            __syncwarp();
         }
         for (int o = 16; o >= P; o >>= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
