@@ -229,7 +229,7 @@ def main():
     ap.add_argument("--ncu", action="store_true",
                     help="profile-region mode: warm up, then run one step between cudaProfilerStart/Stop and exit")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32x3"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--mode", default="apply", choices=["apply", "grad"],
                     help="apply: phi = A q; grad: forward + backward of sum |phi - t|^2 for q and the positions")
@@ -253,7 +253,7 @@ def main():
     n = pts.shape[0]
     nrhs = args.nrhs
     ptd = torch.as_tensor(pts, device=dev)
-    cdt = np.complex64 if args.precision == "fp32" else np.complex128
+    cdt = np.complex128 if args.precision == "fp64" else np.complex64
     Q = q[0] if nrhs == 1 else synth.complex_normal(2003, n, nrhs=nrhs)
     qd = torch.as_tensor(Q.astype(cdt), device=dev)
     out = torch.empty_like(qd)
@@ -429,7 +429,8 @@ def main():
         "metric": METRIC,
         "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64 (fp32)" if args.precision == "fp32" else "c128 (fp64)", "data": "synthetic", "config": cfg,
+        "dtype": {"fp32": "c64 (fp32)", "fp64": "c128 (fp64)", "tf32x3": "c64 (fp32; theta maps split-tf32 x3 on "
+                  "tensor cores)"}[args.precision], "data": "synthetic", "config": cfg,
         "accuracy": {"rel_err_vs_fp64_direct": rel_err, "targets": int(sum(len(g[2]) for g in groups)),
                      "reference": "GPU FP64 direct sum"},
         "plan": {"levels": info["nlev"], "top": info["top"], "L": info["L"], "n_geom": info["n_geom"],

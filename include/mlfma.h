@@ -52,7 +52,12 @@ typedef enum {
 
 typedef enum {
     MLFMA_PREC_FP64 = 0,          /* complex128 data, FP64 arithmetic on every stage */
-    MLFMA_PREC_FP32 = 1           /* complex64 data, FP32 arithmetic; operators built in FP64 */
+    MLFMA_PREC_FP32 = 1,          /* complex64 data, FP32 arithmetic; operators built in FP64 */
+    MLFMA_PREC_FP32_BF16X3 = 2,   /* reserved: split-BF16 tensor-core contractions (UNSUPPORTED in this build) */
+    MLFMA_PREC_FP32_TF32X3 = 3    /* as FP32, but the theta maps of the interpolation (Sec. 3.2.2) and
+                                     anterpolation (Sec. 3.2.4) on level pairs too large to fuse run on
+                                     the tensor cores as split-TF32 GEMMs (x = hi + lo, products hi*hi +
+                                     hi*lo + lo*hi accumulated in FP32): FP32-level accuracy */
 } mlfma_precision;
 
 /* Options of mlfma_plan_create.  Initialise with mlfma_options_init(). */

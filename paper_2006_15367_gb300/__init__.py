@@ -22,7 +22,9 @@ from . import _build
 
 PREC_FP64 = 0
 PREC_FP32 = 1
-_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32}
+PREC_FP32_BF16X3 = 2
+PREC_FP32_TF32X3 = 3
+_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "bf16x3": PREC_FP32_BF16X3, "tf32x3": PREC_FP32_TF32X3}
 MAX_LEVELS = 22
 
 EXPORT = dict(PERM=0, KEYS=1, BOX_KEY=2, BOX_BEGIN=3, BOX_END=4, BOX_PARENT=5, BOX_LEAF=6, V_OFFSETS=7,
@@ -249,7 +251,8 @@ class Plan:
 
     points    [n, 3] float64 (torch tensor on a CUDA device, or host array)
     k         wavenumber; digits: requested accuracy; leaf_max: 0 = level-uniform tree
-    precision "fp32" (complex64 data) or "fp64" (complex128 data)
+    precision "fp32" (complex64 data), "fp64" (complex128 data) or "tf32x3" (complex64 data, theta
+              maps of the large level pairs on the tensor cores as split-TF32 GEMMs)
     """
 
     def __init__(self, points, k, digits=3, leaf_max=0, precision="fp32", leaf_edge=0.0, max_depth=12,

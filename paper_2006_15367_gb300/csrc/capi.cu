@@ -293,7 +293,9 @@ static mlfma_options checked_options(const mlfma_options* opt, double k, int dig
         if (opt->struct_size < sizeof(mlfma_options)) fail(MLFMA_ERR_INVALID_ARG, "options.struct_size too small");
         o = *opt;
     }
-    if (o.precision != MLFMA_PREC_FP64 && o.precision != MLFMA_PREC_FP32)
+    if (o.precision == MLFMA_PREC_FP32_BF16X3)
+        fail(MLFMA_ERR_UNSUPPORTED, "precision FP32_BF16X3 is not built (use FP32_TF32X3)");
+    if (o.precision != MLFMA_PREC_FP64 && o.precision != MLFMA_PREC_FP32 && o.precision != MLFMA_PREC_FP32_TF32X3)
         fail(MLFMA_ERR_INVALID_ARG, "unknown precision %d", (int)o.precision);
     if (o.max_depth < 1 || o.max_depth > kMaxLev) fail(MLFMA_ERR_INVALID_ARG, "max_depth must be in [1, %d]", kMaxLev);
     if (o.digit_margin < -1 || o.digit_margin > 8) fail(MLFMA_ERR_INVALID_ARG, "digit_margin must be in [-1, 8]");
@@ -327,6 +329,8 @@ static void build_plan(Plan& p, const double* pts) {
     build_far_levels(p);
     build_m2l_lists(p);
     build_p2p_work(p);
+    p.dev_err = p.mem.make<int>(1);
+    MLFMA_CUDA(cudaMemsetAsync(p.dev_err, 0, sizeof(int), p.stream));
     prepare_kernels(p);
     p.near_dump = p.mem.get(p.n * csize(p));
     ensure_apply_buffers(p, 1);
@@ -428,10 +432,24 @@ mlfma_status mlfma_apply_grad(mlfma_plan* plan, const void* q, void* phi, void* 
     });
 }
 
+// error flags raised by kernels that gave up a bounded wait (this plan and its sub-plans)
+static void check_device_errors(const Plan& p) {
+    auto one = [](const Plan& q) {
+        if (!q.dev_err) return;
+        int e = 0;
+        MLFMA_CUDA(cudaStreamSynchronize(q.stream));
+        MLFMA_CUDA(cudaMemcpy(&e, q.dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) fail(MLFMA_ERR_TIMEOUT, "a tensor-core kernel timed out waiting for its MMAs (flag %d)", e);
+    };
+    one(p);
+    for (const Plan* sp : p.subs) one(*sp);
+}
+
 mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info) {
     return guarded([&] {
         if (!plan || !info) fail(MLFMA_ERR_INVALID_ARG, "null plan or info");
         const Plan& p = plan->p;
+        check_device_errors(p);
         memset(info, 0, sizeof(*info));
         info->n = p.n;
         info->nlev = p.nlev;

@@ -173,6 +173,7 @@ struct Plan {
     double k = 0;
     int digits = 0, leaf_max = 0, max_depth = 12, margin = 1;
     mlfma_precision prec = MLFMA_PREC_FP32;
+    int* dev_err = nullptr;        // raised by kernels whose bounded waits ran out
     double leaf_edge = 0, a1 = 0, D0 = 0;
     double x0[3] = {0, 0, 0}, scale = 0;
     int nlev = 0, top = 0;
@@ -262,6 +263,10 @@ void build_far_levels(Plan& p);
 void build_m2l_lists(Plan& p);
 void build_p2p_work(Plan& p);
 void prepare_kernels(Plan& p);
+// theta_tc.cu: split-TF32 tensor-core theta maps (complex64 data)
+void prepare_theta_tc();
+void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const float* M, const float2* in,
+                         float2* out, cudaStream_t s);
 // far.cu / near.cu
 // one right-hand side in sorted order; grads_r (nullable): [n][3] complex gradient of phi
 void apply_pipeline(Plan& p, const void* qs_r, void* phis_r, void* grads_r);

@@ -420,6 +420,7 @@ static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
 
 // raise the dynamic shared-memory limit of the M2L kernel once (before any capture)
 void prepare_kernels(Plan& p) {
+    if (p.prec == MLFMA_PREC_FP32_TF32X3) prepare_theta_tc();
     if (p.prec == MLFMA_PREC_FP64)
         MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<double, double2, M2LShape<double2>::U, M2LShape<double2>::NW>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_smem<double, double2>()));
@@ -916,7 +917,14 @@ __global__ void __launch_bounds__(256) k_theta_map(int nbox, int Lc, int nin, in
 }
 
 template <typename R, typename C>
-static void launch_theta_map(int64_t nbox, int Lc, int nin, int nout, const R* M, const C* in, C* out, cudaStream_t s) {
+static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const R* M, const C* in, C* out,
+                             cudaStream_t s) {
+    if constexpr (sizeof(C) == 8) {
+        if (p.prec == MLFMA_PREC_FP32_TF32X3) {
+            launch_theta_map_tc(p, nbox, Lc, nin, nout, (const float*)M, (const float2*)in, (float2*)out, s);
+            return;
+        }
+    }
     const int nm = 2 * Lc + 1;
     if (nout <= 16 && sizeof(C) == 8) {          // the 256-box tile of complex128 would exceed 48 KB
         k_theta_map<R, C, 16><<<dim3(nblk(nbox, 256), nblk(nout, 16), nm), 256, 0, s>>>((int)nbox, Lc, nin, nout, M, in, out);
@@ -975,7 +983,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
                                                                       FastDiv::make(RB), (C*)F.X);
             MLFMA_LAUNCH_CHECK();
             // B: theta maps per mode
-            launch_theta_map<R, C>(TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, (const C*)F.X, (C*)F.Y, s);
+            launch_theta_map<R, C>(p, TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, (const C*)F.X, (C*)F.Y, s);
         }
         // C: z-shift per mode, inverse FFT, xy-shift, sum over children
         int RT = balanced_rows(F.nth, tile_rows(F.nth, budget - F.nph, 8 * F.nph));
@@ -1012,7 +1020,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
                 launch_l2l_out<C, R>(CPB, (int)T.nbox, (const C*)Pf.Y, Lc, F.nth, Pf.nth, F.fft, (const C*)F.tw,
                                      (const R*)Pf.Bt, (C*)F.G, s);
             } else {
-                launch_theta_map<R, C>(T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, (const C*)Pf.Y, (C*)Pf.X, s);
+                launch_theta_map<R, C>(p, T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, (const C*)Pf.Y, (C*)Pf.X, s);
                 const int64_t rows_c = T.nbox * (int64_t)F.nth;
                 int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * F.nph);
                 sm = ((size_t)2 * RB * F.nph + F.nph) * sizeof(C);

@@ -1,0 +1,219 @@
+// Theta maps of the interpolation (Sec. 3.2.2) and anterpolation (Sec. 3.2.4) on the
+// 5th-generation tensor cores, split-TF32 form (MLFMA_PREC_FP32_TF32X3):
+//
+//   out[mi][c][o] = sum_i M[|m|][i][o] in[mi][c][i],   m = mi - Lc
+//
+// a real matrix applied to complex vectors, one GEMM per Fourier mode.  A CTA takes 64
+// boxes of one mode: the A operand has 128 rows (row 2b = Re in[c0+b][.], row 2b+1 = Im),
+// the B operand is the mode's map with N <= 256 output rows as K-major rows.  Both are
+// split into TF32 parts while staged in shared memory, x = hi + lo with hi = x truncated to
+// TF32 and lo = x - hi (exact), and the product is accumulated in FP32 in tensor memory
+// as hi*hi + hi*lo + lo*hi (the dropped lo*lo term is below 2^-22 relative), so the result
+// carries FP32-level accuracy.  The K dimension is staged in chunks of 32; one thread
+// issues tcgen05.mma (kind::tf32, M = 128) and tcgen05.commit signals an mbarrier; the
+// accumulator is read back with tcgen05.ld.  Every wait has an iteration limit after which
+// the kernel raises the plan's error flag, releases its tensor memory and returns.
+#include "common.cuh"
+
+namespace mlfma {
+
+namespace {
+
+constexpr int kTcBoxes = 64;                 // boxes per CTA (A rows 2b, 2b + 1)
+constexpr int kTcM = 128;                    // MMA M
+constexpr int kTcKC = 32;                    // K elements per staged chunk (4 MMA K-steps)
+constexpr int kTcMaxN = 256;                 // output rows per CTA (MMA N <= 256)
+constexpr int kTcThreads = 128;
+constexpr uint32_t kABytes = kTcM * kTcKC * 4;        // one TF32 part of the A chunk (16 KB)
+constexpr uint32_t kBBytes = kTcMaxN * kTcKC * 4;     // one TF32 part of the B chunk (32 KB)
+constexpr size_t kTcSmem = 2 * (size_t)kABytes + 2 * (size_t)kBBytes;   // 96 KB
+constexpr long long kWaitLimit = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Canonical K-major layout without swizzle: core matrices of 8 rows x 16 bytes (4 TF32),
+// core (row / 8, k / 4) at byte ((row / 8) (KC / 4) + k / 4) 128, row r % 8 at 16 (r % 8).
+// Leading-dimension offset (next core along K) 128 B, stride offset (next 8 rows) KC / 4 * 128 B.
+__device__ __forceinline__ uint32_t core_off(int row, int k) {
+    return (uint32_t)(((row >> 3) * (kTcKC / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);                    // start address
+    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;                       // leading-dimension byte offset
+    d |= (uint64_t)(((kTcKC / 4) * 128u >> 4) & 0x3FFFu) << 32;         // stride-dimension byte offset
+    d |= (uint64_t)1 << 46;                                             // descriptor version of tcgen05
+    return d;                                                           // base offset 0, no swizzle
+}
+
+// instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, N >> 3, M >> 4
+__device__ __forceinline__ uint32_t instr_desc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+    hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+    lo = x - hi;
+}
+
+__device__ __forceinline__ void st_f32(uint32_t addr, float v) {
+    asm volatile("st.shared.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc, int nin, int nout,
+                                                                const float* __restrict__ Mt, const float2* __restrict__ in,
+                                                                float2* __restrict__ out, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_taddr;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mi = blockIdx.z, m = abs(mi - Lc);
+    const int c0 = blockIdx.x * kTcBoxes;
+    const int n0 = blockIdx.y * kTcMaxN;
+    const int N = min(kTcMaxN, nout - n0);
+    const int Np = (N + 15) & ~15;                                      // MMA N: multiple of 16 for M = 128
+    const uint32_t ncols = Np <= 32 ? 32u : Np <= 64 ? 64u : Np <= 128 ? 128u : 256u;
+    const uint32_t sA[2] = {smem_u32(smem_raw), smem_u32(smem_raw + kABytes)};
+    const uint32_t sB[2] = {smem_u32(smem_raw + 2 * kABytes), smem_u32(smem_raw + 2 * kABytes + kBBytes)};
+    const uint32_t bar = smem_u32(&mbar);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_taddr)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_taddr;
+
+    const float* Mm = Mt + (int64_t)m * nin * nout;
+    const float2* inm = in + (int64_t)mi * nbox * nin;
+    const uint32_t idesc = instr_desc_tf32(kTcM, Np);
+    uint32_t phase = 0;
+    bool ok = true;
+    bool issued = false;                                                // MMAs committed but not yet waited for
+    const int nchunks = (nin + kTcKC - 1) / kTcKC;
+    for (int ch = 0; ch < nchunks && ok; ++ch) {
+        const int k0 = ch * kTcKC;
+        // A: box b, column k (k fastest: contiguous reads of in[c][k0 ..])
+        for (int idx = threadIdx.x; idx < kTcBoxes * kTcKC; idx += kTcThreads) {
+            const int b = idx / kTcKC, k = idx % kTcKC;
+            float2 v = make_float2(0.f, 0.f);
+            if (c0 + b < nbox && k0 + k < nin) v = inm[(int64_t)(c0 + b) * nin + k0 + k];
+            float h, l;
+            split_tf32(v.x, h, l);
+            st_f32(sA[0] + core_off(2 * b, k), h);
+            st_f32(sA[1] + core_off(2 * b, k), l);
+            split_tf32(v.y, h, l);
+            st_f32(sA[0] + core_off(2 * b + 1, k), h);
+            st_f32(sA[1] + core_off(2 * b + 1, k), l);
+        }
+        // B: output row n, column k, B[n][k] = M[|m|][k0 + k][n0 + n] (n fastest: contiguous reads)
+        for (int idx = threadIdx.x; idx < Np * kTcKC; idx += kTcThreads) {
+            const int k = idx / Np, n = idx - k * Np;
+            float v = 0.f;
+            if (n < N && k0 + k < nin) v = Mm[(int64_t)(k0 + k) * nout + n0 + n];
+            float h, l;
+            split_tf32(v, h, l);
+            st_f32(sB[0] + core_off(n, k), h);
+            st_f32(sB[1] + core_off(n, k), l);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+            for (int s = 0; s < kTcKC / 8; ++s) {
+                const uint32_t ko = (uint32_t)s * 256;                  // two 16-byte cores along K per step
+                mma_tf32(tmem, smem_desc(sA[0] + ko), smem_desc(sB[0] + ko), idesc, ch > 0 || s > 0);
+                mma_tf32(tmem, smem_desc(sA[0] + ko), smem_desc(sB[1] + ko), idesc, 1);
+                mma_tf32(tmem, smem_desc(sA[1] + ko), smem_desc(sB[0] + ko), idesc, 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                         : "memory");
+        }
+        issued = true;
+        // the MMAs read the staged chunk: wait before it is overwritten (and before the epilogue)
+        ok = __syncthreads_and(mbar_wait(bar, phase));       // one decision for the whole CTA
+        issued = !ok;
+        phase ^= 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+        const int row = 32 * warp + lane, b = row >> 1;
+        const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+        for (int col0 = 0; col0 < Np; col0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tl + (uint32_t)col0, r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float v = __uint_as_float(r[j]);
+                const float w = __shfl_xor_sync(0xffffffffu, v, 1);      // the other part of the same box
+                const int n = col0 + j;
+                if (!(row & 1) && c0 + b < nbox && n < N)
+                    out[((int64_t)mi * nbox + c0 + b) * nout + n0 + n] = make_float2(v, w);
+            }
+        }
+    } else {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        if (issued) mbar_wait(bar, phase ^ 1);                          // let the MMAs in flight finish (bounded)
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+}  // namespace
+
+void prepare_theta_tc() {
+    MLFMA_CUDA(cudaFuncSetAttribute(k_theta_map_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+}
+
+void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const float* M, const float2* in,
+                         float2* out, cudaStream_t s) {
+    const int nm = 2 * Lc + 1;
+    const dim3 grid((unsigned)((nbox + kTcBoxes - 1) / kTcBoxes), (unsigned)((nout + kTcMaxN - 1) / kTcMaxN), (unsigned)nm);
+    k_theta_map_tc<<<grid, kTcThreads, kTcSmem, s>>>((int)nbox, Lc, nin, nout, M, in, out, p.dev_err);
+    MLFMA_LAUNCH_CHECK();
+}
+
+}  // namespace mlfma

@@ -1,0 +1,69 @@
+"""Split-TF32 tensor-core theta maps (precision "tf32x3") against the oracle and the FP32 path.
+
+The tf32x3 plans run the theta maps of the level pairs that are too large for the fused
+FFT + theta-map kernels as tcgen05 GEMMs with operands split into two TF32 parts and
+three products accumulated in FP32, so every stage keeps the FP32 tolerances (1e-5 per
+stage against the FP64 oracle, 1e-3 end to end).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import direct
+from oracle import mlfma as om
+
+from gpu_common import apply_plan, make_plan, rel
+
+pytestmark = pytest.mark.gpu
+K = 2.0 * math.pi
+
+
+def test_tf32x3_stages_match_oracle_mid_sphere():
+    """16,377 points on a radius-4 sphere: the L2L pair of levels 3 -> 4 runs on the tensor cores."""
+    pts = synth.sphere(16384 - 7, 4.0, seed=81)
+    q = synth.complex_normal(82, pts.shape[0])[0]
+    o = om.OracleMLFMA(pts, K, 3, margin=0)
+    phio, dump = o.apply(q, dump=True)
+    plan = make_plan(pts, K, 3, "tf32x3")
+    phi = apply_plan(plan, q, "tf32x3")
+    for l in range(o.top, o.tree.nlev + 1):
+        nb = o.tree.levels[l].nbox
+        assert rel(plan.export("F", l).reshape(nb, -1), dump["F"][l]) < 1e-5, ("F", l)
+        assert rel(plan.export("G", l).reshape(nb, -1), dump["G"][l]) < 1e-5, ("G", l)
+    assert rel(phi, phio) < 1e-3
+    tg = np.arange(0, pts.shape[0], 7)
+    assert rel(phi[tg], direct.direct(pts, q, K, targets=tg)) < 1e-3
+    assert plan.info()["precision"] == 3          # no device error flag raised
+    plan.close()
+
+
+def test_tf32x3_matches_fp32_large_sphere():
+    """65,536 points on a radius-8 sphere: M2M and L2L theta maps of the upper levels on the
+    tensor cores (several K chunks); every level's F and G against the FP32 plan."""
+    pts = synth.sphere(65536, 8.0, seed=91)
+    q = synth.complex_normal(92, pts.shape[0])[0]
+    p32 = make_plan(pts, K, 3, "fp32")
+    ptc = make_plan(pts, K, 3, "tf32x3")
+    phi32 = apply_plan(p32, q, "fp32")
+    phitc = apply_plan(ptc, q, "tf32x3")
+    info = ptc.info()
+    assert info["L"] == p32.info()["L"]
+    for l in range(info["top"], info["nlev"] + 1):
+        assert rel(ptc.export("F", l), p32.export("F", l)) < 1e-5, ("F", l)
+        assert rel(ptc.export("G", l), p32.export("G", l)) < 1e-5, ("G", l)
+    assert rel(phitc, phi32) < 1e-5
+    tg = np.sort(np.random.default_rng(5).choice(pts.shape[0], 500, replace=False))
+    assert rel(phitc[tg], direct.direct(pts, q, K, targets=tg)) < 1e-3
+    # graph replay gives the same bits
+    assert np.array_equal(apply_plan(ptc, q, "tf32x3"), phitc)
+    ptc.close()
+    p32.close()
+
+
+def test_bf16x3_reports_unsupported():
+    import paper_2006_15367_gb300 as mf
+    with pytest.raises(mf.MLFMAError) as e:
+        make_plan(synth.sphere(100, 1.0, seed=1), K, 3, "bf16x3")
+    assert e.value.status == 5
