@@ -419,16 +419,6 @@ static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
 }
 
 // raise the dynamic shared-memory limit of the M2L kernel once (before any capture)
-void prepare_kernels(Plan& p) {
-    if (p.prec == MLFMA_PREC_FP32_TF32X3) prepare_theta_tc();
-    if (p.prec == MLFMA_PREC_FP64)
-        MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<double, double2, M2LShape<double2>::U, M2LShape<double2>::NW>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_smem<double, double2>()));
-    else
-        MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<float, float2, M2LShape<float2>::U, M2LShape<float2>::NW>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_smem<float, float2>()));
-}
-
 // ============================================================== phi transforms: mixed-radix FFTs in shared memory
 // Stockham autosort FFT of several rows at once (length n = prod of radices 2, 3, 4, 5, 7).
 // tw[k] = e^{-2 pi i k / n}; inv = true uses e^{+2 pi i k / n} (no 1/n scaling).
@@ -534,6 +524,9 @@ __device__ __forceinline__ int wrap(int m, int n) { return m < 0 ? m + n : m; }
 
 // shared-memory budget of one FFT CTA: small enough for several resident CTAs per SM
 constexpr size_t kFftSmemBytes = 20 * 1024;
+// the per-parent transforms (quadrant rows of one parent) take larger tiles: fewer row tiles
+// per parent, 5 CTAs of 128 threads per SM
+constexpr size_t kParentSmemBytes = 32 * 1024;
 
 // M2M first step: X[mi][c][i] = scale sum_j F[c][i][j] e^{-i m phi_j}, |m| <= Lc, for the rows
 // r = c nth + i of all children (rows are contiguous in F; X is mode-major).  dRB divides by RB.
@@ -986,7 +979,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
             launch_theta_map<R, C>(p, TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, (const C*)F.X, (C*)F.Y, s);
         }
         // C: z-shift per mode, inverse FFT, xy-shift, sum over children
-        int RT = balanced_rows(F.nth, tile_rows(F.nth, budget - F.nph, 8 * F.nph));
+        const int pbudget = (int)(kParentSmemBytes / sizeof(C));
+        int RT = balanced_rows(F.nth, tile_rows(F.nth, pbudget - F.nph, 8 * F.nph));
         sm = ((size_t)8 * RT * F.nph + F.nph) * sizeof(C);
         k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(
             T.child_begin, T.child_end, TC.key, (int)TC.nbox, (const C*)F.Y, Lc, F.nth, F.fft, (const C*)F.tw,
@@ -1008,7 +1002,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
             const int CPB = fused_children(F.nth, F.nph, (2 * Lc + 1) * Pf.nth, sizeof(C));
             StageTimer st(p, MLFMA_STAGE_L2L, l, CPB ? 2 : 3);
             const int budget = (int)(kFftSmemBytes / sizeof(C));
-            int RT = balanced_rows(Pf.nth, tile_rows(Pf.nth, budget - Pf.nph, 8 * Pf.nph));
+            const int pbudget = (int)(kParentSmemBytes / sizeof(C));
+            int RT = balanced_rows(Pf.nth, tile_rows(Pf.nth, pbudget - Pf.nph, 8 * Pf.nph));
             size_t sm = ((size_t)8 * RT * Pf.nph + Pf.nph) * sizeof(C);
             k_l2l_fft_in<C, R><<<dim3((unsigned)TP.nbox, nblk(Pf.nth, RT)), 128, sm, s>>>(
                 TP.child_begin, TP.child_end, T.key, (int)T.nbox, (const C*)Pf.G, Lc, Pf.nth, Pf.fft, (const C*)Pf.tw,
@@ -1055,6 +1050,38 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
             }
         }
     }
+}
+
+// allow a kernel the device's opt-in shared memory per block minus its static shared memory
+template <typename K>
+static void allow_max_smem(K kernel) {
+    int dev = 0, optin = 0;
+    MLFMA_CUDA(cudaGetDevice(&dev));
+    MLFMA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    MLFMA_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    MLFMA_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+}
+
+template <typename C, typename R>
+static void prepare_fft_kernels() {
+    // one row tile of a long transform (e.g. 9 n complex128 for n = 400) can exceed 48 KB
+    allow_max_smem(k_m2m_fft_out<C>);
+    allow_max_smem(k_l2l_fft_in<C, R>);
+    allow_max_smem(k_fft_fwd_rows<C, R>);
+    allow_max_smem(k_l2l_fft_out<C>);
+}
+
+void prepare_kernels(Plan& p) {
+    if (p.prec == MLFMA_PREC_FP64) prepare_fft_kernels<double2, double>();
+    else prepare_fft_kernels<float2, float>();
+    if (p.prec == MLFMA_PREC_FP32_TF32X3) prepare_theta_tc();
+    if (p.prec == MLFMA_PREC_FP64)
+        MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<double, double2, M2LShape<double2>::U, M2LShape<double2>::NW>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_smem<double, double2>()));
+    else
+        MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<float, float2, M2LShape<float2>::U, M2LShape<float2>::NW>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_smem<float, float2>()));
 }
 
 void far_apply(Plan& p, const void* qs, void* phis, void* grads) {

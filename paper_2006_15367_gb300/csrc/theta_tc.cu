@@ -13,6 +13,8 @@
 // issues tcgen05.mma (kind::tf32, M = 128) and tcgen05.commit signals an mbarrier; the
 // accumulator is read back with tcgen05.ld.  Every wait has an iteration limit after which
 // the kernel raises the plan's error flag, releases its tensor memory and returns.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace mlfma {
@@ -25,8 +27,8 @@ constexpr int kTcKC = 32;                    // K elements per staged chunk (4 M
 constexpr int kTcMaxN = 256;                 // output rows per CTA (MMA N <= 256)
 constexpr int kTcThreads = 128;
 constexpr uint32_t kABytes = kTcM * kTcKC * 4;        // one TF32 part of the A chunk (16 KB)
-constexpr uint32_t kBBytes = kTcMaxN * kTcKC * 4;     // one TF32 part of the B chunk (32 KB)
-constexpr size_t kTcSmem = 2 * (size_t)kABytes + 2 * (size_t)kBBytes;   // 96 KB
+constexpr uint32_t kBBytesMax = kTcMaxN * kTcKC * 4;  // one TF32 part of the widest B chunk (32 KB)
+constexpr size_t kTcSmemMax = 2 * (size_t)kABytes + 2 * (size_t)kBBytesMax;   // 96 KB
 constexpr long long kWaitLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -56,9 +58,6 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
     lo = x - hi;
 }
 
-__device__ __forceinline__ void st_f32(uint32_t addr, float v) {
-    asm volatile("st.shared.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
-}
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
     asm volatile(
@@ -92,7 +91,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc, int nin, int nout,
+// Npmax: the MMA N of the widest tile of the launch (sizes the B region of shared memory)
+__global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc, int nin, int nout, int Npmax,
                                                                 const float* __restrict__ Mt, const float2* __restrict__ in,
                                                                 float2* __restrict__ out, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -105,8 +105,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
     const int N = min(kTcMaxN, nout - n0);
     const int Np = (N + 15) & ~15;                                      // MMA N: multiple of 16 for M = 128
     const uint32_t ncols = Np <= 32 ? 32u : Np <= 64 ? 64u : Np <= 128 ? 128u : 256u;
-    const uint32_t sA[2] = {smem_u32(smem_raw), smem_u32(smem_raw + kABytes)};
-    const uint32_t sB[2] = {smem_u32(smem_raw + 2 * kABytes), smem_u32(smem_raw + 2 * kABytes + kBBytes)};
+    const uint32_t bbytes = (uint32_t)Npmax * kTcKC * 4;              // one TF32 part of the B chunk
+    // plain stores (no compiler barrier between them, so the global loads of the staging
+    // loops overlap); the async-proxy fence before the MMAs orders them
+    unsigned char* pA[2] = {smem_raw, smem_raw + kABytes};
+    unsigned char* pB[2] = {smem_raw + 2 * kABytes, smem_raw + 2 * kABytes + bbytes};
+    const uint32_t sA[2] = {smem_u32(pA[0]), smem_u32(pA[1])};
+    const uint32_t sB[2] = {smem_u32(pB[0]), smem_u32(pB[1])};
     const uint32_t bar = smem_u32(&mbar);
 
     if (warp == 0) {
@@ -133,28 +138,63 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
     const int nchunks = (nin + kTcKC - 1) / kTcKC;
     for (int ch = 0; ch < nchunks && ok; ++ch) {
         const int k0 = ch * kTcKC;
-        // A: box b, column k (k fastest: contiguous reads of in[c][k0 ..])
-        for (int idx = threadIdx.x; idx < kTcBoxes * kTcKC; idx += kTcThreads) {
-            const int b = idx / kTcKC, k = idx % kTcKC;
-            float2 v = make_float2(0.f, 0.f);
-            if (c0 + b < nbox && k0 + k < nin) v = inm[(int64_t)(c0 + b) * nin + k0 + k];
-            float h, l;
-            split_tf32(v.x, h, l);
-            st_f32(sA[0] + core_off(2 * b, k), h);
-            st_f32(sA[1] + core_off(2 * b, k), l);
-            split_tf32(v.y, h, l);
-            st_f32(sA[0] + core_off(2 * b + 1, k), h);
-            st_f32(sA[1] + core_off(2 * b + 1, k), l);
+        // A: a warp stores 4 boxes x 8 columns, so its 32 stores of one part cover the banks
+        // (row mod 8, k mod 4) at most twice; reads are 4 runs of 8 contiguous samples.  Each
+        // thread issues its kAPer loads before any store.
+        {
+            constexpr int kAPer = kTcBoxes * kTcKC / kTcThreads;
+            float2 va[kAPer];
+#pragma unroll
+            for (int it = 0; it < kAPer; ++it) {
+                const int idx = threadIdx.x + it * kTcThreads;
+                const int w = idx >> 5, l = idx & 31;
+                const int b = (w & 15) * 4 + (l >> 3), k = (w >> 4) * 8 + (l & 7);
+                va[it] = (c0 + b < nbox && k0 + k < nin) ? inm[(int64_t)(c0 + b) * nin + k0 + k] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int it = 0; it < kAPer; ++it) {
+                const int idx = threadIdx.x + it * kTcThreads;
+                const int w = idx >> 5, l = idx & 31;
+                const int b = (w & 15) * 4 + (l >> 3), k = (w >> 4) * 8 + (l & 7);
+                float h, lo;
+                split_tf32(va[it].x, h, lo);
+                *reinterpret_cast<float*>(pA[0] + core_off(2 * b, k)) = h;
+                *reinterpret_cast<float*>(pA[1] + core_off(2 * b, k)) = lo;
+                split_tf32(va[it].y, h, lo);
+                *reinterpret_cast<float*>(pA[0] + core_off(2 * b + 1, k)) = h;
+                *reinterpret_cast<float*>(pA[1] + core_off(2 * b + 1, k)) = lo;
+            }
         }
-        // B: output row n, column k, B[n][k] = M[|m|][k0 + k][n0 + n] (n fastest: contiguous reads)
-        for (int idx = threadIdx.x; idx < Np * kTcKC; idx += kTcThreads) {
-            const int k = idx / Np, n = idx - k * Np;
-            float v = 0.f;
-            if (n < N && k0 + k < nin) v = Mm[(int64_t)(k0 + k) * nout + n0 + n];
-            float h, l;
-            split_tf32(v, h, l);
-            st_f32(sB[0] + core_off(n, k), h);
-            st_f32(sB[1] + core_off(n, k), l);
+        // B: output row n, column k, B[n][k] = M[|m|][k0 + k][n0 + n]; a warp stores 8 rows x 4
+        // columns (all 32 banks once); reads are 4 runs of 8 contiguous entries, issued in
+        // batches of kBBatch per thread
+        {
+            constexpr int kBBatch = 8;
+            const int ng = Np >> 3;
+            const int tot = Np * kTcKC;                      // a multiple of kTcThreads * kBBatch / 2
+            for (int base = 0; base < tot; base += kTcThreads * kBBatch) {
+                float vb[kBBatch];
+#pragma unroll
+                for (int it = 0; it < kBBatch; ++it) {
+                    const int idx = base + threadIdx.x + it * kTcThreads;
+                    const int w = idx >> 5, l = idx & 31;
+                    const int kq = w / ng, nq = w - kq * ng;
+                    const int n = nq * 8 + (l >> 2), k = kq * 4 + (l & 3);
+                    vb[it] = (idx < tot && n < N && k0 + k < nin) ? Mm[(int64_t)(k0 + k) * nout + n0 + n] : 0.f;
+                }
+#pragma unroll
+                for (int it = 0; it < kBBatch; ++it) {
+                    const int idx = base + threadIdx.x + it * kTcThreads;
+                    if (idx >= tot) break;
+                    const int w = idx >> 5, l = idx & 31;
+                    const int kq = w / ng, nq = w - kq * ng;
+                    const int n = nq * 8 + (l >> 2), k = kq * 4 + (l & 3);
+                    float h, lo;
+                    split_tf32(vb[it], h, lo);
+                    *reinterpret_cast<float*>(pB[0] + core_off(n, k)) = h;
+                    *reinterpret_cast<float*>(pB[1] + core_off(n, k)) = lo;
+                }
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
@@ -205,14 +245,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
 }  // namespace
 
 void prepare_theta_tc() {
-    MLFMA_CUDA(cudaFuncSetAttribute(k_theta_map_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+    MLFMA_CUDA(cudaFuncSetAttribute(k_theta_map_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax));
 }
 
 void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const float* M, const float2* in,
                          float2* out, cudaStream_t s) {
     const int nm = 2 * Lc + 1;
     const dim3 grid((unsigned)((nbox + kTcBoxes - 1) / kTcBoxes), (unsigned)((nout + kTcMaxN - 1) / kTcMaxN), (unsigned)nm);
-    k_theta_map_tc<<<grid, kTcThreads, kTcSmem, s>>>((int)nbox, Lc, nin, nout, M, in, out, p.dev_err);
+    const int Npmax = ((std::min(nout, kTcMaxN) + 15) / 16) * 16;
+    const size_t smem = 2 * (size_t)kABytes + 2 * (size_t)Npmax * kTcKC * 4;
+    k_theta_map_tc<<<grid, kTcThreads, smem, s>>>((int)nbox, Lc, nin, nout, Npmax, M, in, out, p.dev_err);
     MLFMA_LAUNCH_CHECK();
 }
 

@@ -209,3 +209,16 @@ def test_full_size_sphere_fp32_three_digits():
     ref = direct.direct(pts, q[0], prm["k"], targets=tg)
     assert rel(phi[tg], ref) < 1e-3
     plan.close()
+
+
+@pytest.mark.slow
+def test_full_size_sphere_fp64_three_digits():
+    """The FP64 path at 2^20 points: the top level's transforms (length 400) take row tiles of
+    more than 48 KB of shared memory."""
+    pts, q, prm = synth.workload("sphere1m")
+    plan = make_plan(pts, prm["k"], 3, "fp64")
+    phi = apply_plan(plan, q[0], "fp64")
+    tg = np.sort(np.random.default_rng(2001).choice(pts.shape[0], 2000, replace=False))
+    ref = direct.direct(pts, q[0], prm["k"], targets=tg)
+    assert rel(phi[tg], ref) < 1e-3
+    plan.close()
