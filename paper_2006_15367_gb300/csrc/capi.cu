@@ -51,6 +51,19 @@ void* Allocator::get(size_t n) {
     return ptr;
 }
 
+void Allocator::drop(void* ptr) {
+    if (!ptr) return;
+    for (size_t i = 0; i < live.size(); ++i)
+        if (live[i].first == ptr) {
+            if (free) free(ptr, (void*)stream, ctx);
+            else cudaFree(ptr);
+            bytes -= live[i].second;
+            live[i] = live.back();
+            live.pop_back();
+            return;
+        }
+}
+
 void Allocator::release_all() {
     for (auto& a : live) {
         if (free) free(a.first, (void*)stream, ctx);
@@ -77,8 +90,28 @@ static void drop_graphs(Plan& p) {
     p.graphs.clear();
 }
 
+// Signatures F and G of every far level with room for nr right-hand sides (layout
+// [r][nbox][K], slice 0 first).  The old buffers are released, so the plan is marked: run()
+// drops every captured graph (a batched plan's graphs belong to its parent) before it
+// captures again.
+static void ensure_far_rhs(Plan& p, int nr) {
+    if (nr <= p.far_nr || !p.top) return;
+    MLFMA_CUDA(cudaDeviceSynchronize());           // no graph in flight still uses the old buffers
+    for (int l = p.top; l <= p.nlev; ++l) {
+        FarLevel& F = p.far[l];
+        const size_t bytes = (size_t)nr * p.lev[l].nbox * F.K * csize(p);
+        p.mem.drop(F.F);
+        p.mem.drop(F.G);
+        F.F = p.mem.get(bytes);
+        F.G = p.mem.get(bytes);
+    }
+    p.far_nr = nr;
+    p.graphs_stale = true;
+}
+
 // Morton-order work buffers of one plan (grown only; growth invalidates captured graphs)
 static void ensure_apply_buffers(Plan& p, int nrhs) {
+    if (nrhs >= kMaxNR) ensure_far_rhs(p, kMaxNR);
     if (nrhs <= p.nrhs_cap) return;
     p.qs = p.mem.get((size_t)nrhs * p.n * csize(p));
     p.phis = p.mem.get((size_t)nrhs * p.n * csize(p));
@@ -118,9 +151,13 @@ static void sweep(Plan& p, const void* qin, void* phiout, void* gout, int64_t ld
         StageTimer st(p, MLFMA_STAGE_PERMUTE, 0, 1);
         permute_in(p, qin, p.qs, nrhs, adjoint, ld);
     }
-    for (int r = 0; r < nrhs; ++r)
+    // passes of kMaxNR right-hand sides while that many remain (not for gradients), then single ones
+    for (int r = 0; r < nrhs;) {
+        const int nr = (!grad && nrhs - r >= kMaxNR) ? kMaxNR : 1;
         apply_pipeline(p, (const char*)p.qs + (size_t)r * p.n * cs, (char*)p.phis + (size_t)r * p.n * cs,
-                       grad ? (char*)p.grads + (size_t)3 * r * p.n * cs : nullptr);
+                       grad ? (char*)p.grads + (size_t)3 * r * p.n * cs : nullptr, nr);
+        r += nr;
+    }
     {
         StageTimer st(p, MLFMA_STAGE_PERMUTE, 0, 1);
         permute_out(p, p.phis, phiout, nrhs, adjoint, ld);
@@ -170,6 +207,13 @@ static void run(Plan& P, int nrhs, bool adjoint, bool grad) {
     if (it == P.graphs.end()) {
         // first call with this shape: run eagerly (this also sizes every buffer), then capture
         sweep_all(P, P.stream, nrhs, adjoint, grad);
+        bool stale = P.graphs_stale;
+        for (Plan* sp : P.subs) stale = stale || sp->graphs_stale;
+        if (stale) {                                   // buffers the other graphs captured were replaced
+            drop_graphs(P);
+            P.graphs_stale = false;
+            for (Plan* sp : P.subs) sp->graphs_stale = false;
+        }
         MLFMA_CUDA(cudaEventRecord(P.ev_fork, P.stream));
         MLFMA_CUDA(cudaStreamWaitEvent(P.gstream, P.ev_fork, 0));
         MLFMA_CUDA(cudaStreamBeginCapture(P.gstream, cudaStreamCaptureModeThreadLocal));

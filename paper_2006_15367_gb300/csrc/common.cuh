@@ -20,6 +20,7 @@ constexpr int kBits = 21;
 constexpr int kNumOffsets = 316;            // [-3,3]^3 minus [-1,1]^3: far offsets of one level
 constexpr int kSmallLeaf = 64;              // P2P: leaves up to this size take one warp
 constexpr int kP2PTile = 128;               // P2P: targets per CTA for larger leaves
+constexpr int kMaxNR = 4;                   // right-hand sides per pass of the sweep
 
 // ---------------------------------------------------------------- errors
 void set_error(const char* fmt, ...);
@@ -77,6 +78,7 @@ struct Allocator {
     std::vector<std::pair<void*, size_t>> live;
     size_t bytes = 0;
     void* get(size_t n);
+    void drop(void* ptr);          // releases one allocation made by get (no-op for nullptr)
     template <typename T> T* make(size_t count) { return static_cast<T*>(get(count * sizeof(T))); }
     void release_all();
 };
@@ -174,6 +176,8 @@ struct Plan {
     int digits = 0, leaf_max = 0, max_depth = 12, margin = 1;
     mlfma_precision prec = MLFMA_PREC_FP32;
     int* dev_err = nullptr;        // raised by kernels whose bounded waits ran out
+    int far_nr = 1;                // right-hand sides the far-level signatures F, G have room for
+    bool graphs_stale = false;     // buffers captured by earlier graphs were replaced
     double leaf_edge = 0, a1 = 0, D0 = 0;
     double x0[3] = {0, 0, 0}, scale = 0;
     int nlev = 0, top = 0;
@@ -269,8 +273,9 @@ void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout,
                          float2* out, cudaStream_t s);
 // far.cu / near.cu
 // one right-hand side in sorted order; grads_r (nullable): [n][3] complex gradient of phi
-void apply_pipeline(Plan& p, const void* qs_r, void* phis_r, void* grads_r);
-void far_apply(Plan& p, const void* qs, void* phis, void* grads);
+// nr right-hand sides per pass (1, or kMaxNR without gradients): q and phi r n apart
+void apply_pipeline(Plan& p, const void* qs_r, void* phis_r, void* grads_r, int nr);
+void far_apply(Plan& p, const void* qs, void* phis, void* grads, int nr);
 // ld: row stride of the caller-order vectors (default n)
 void permute_out3(Plan& p, const void* gs, void* g, int nrhs, int64_t ld = -1);
 void permute_in(Plan& p, const void* q, void* qs, int nrhs, bool conj, int64_t ld = -1);

@@ -38,13 +38,14 @@ static inline int balanced_rows(int nrows, int rmax) {
 // ============================================================== C2M (warp per leaf)
 constexpr int kC2MPass = 4;   // samples per lane per pass
 
-template <typename R, typename C>
+// NR right-hand sides share each exponential: charges qs[r sn + j], signatures F[r sF + b K + p].
+template <typename R, typename C, int NR>
 __global__ void __launch_bounds__(128) k_c2m(int64_t nleaf, const int* __restrict__ leaf_box, const int* __restrict__ begin,
                                              const int* __restrict__ end, const double* __restrict__ center,
-                                             const double* __restrict__ pos, const C* __restrict__ qs,
-                                             const R* __restrict__ dirs, int64_t K, R k, C* __restrict__ F) {
+                                             const double* __restrict__ pos, const C* __restrict__ qs, int64_t sn,
+                                             const R* __restrict__ dirs, int64_t K, R k, C* __restrict__ F, int64_t sF) {
     __shared__ R sp[4][32][3];
-    __shared__ C sq[4][32];
+    __shared__ C sq[4][NR][32];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t w = (int64_t)blockIdx.x * 4 + wl;
     if (w >= nleaf) return;
@@ -53,11 +54,12 @@ __global__ void __launch_bounds__(128) k_c2m(int64_t nleaf, const int* __restric
     const double cx = center[3 * b], cy = center[3 * b + 1], cz = center[3 * b + 2];
     C* Fb = F + (int64_t)b * K;
     for (int64_t p0 = 0; p0 < K; p0 += 32 * kC2MPass) {
-        C acc[kC2MPass];
+        C acc[kC2MPass][NR];
         R d[kC2MPass][3];
 #pragma unroll
         for (int u = 0; u < kC2MPass; ++u) {
-            acc[u] = cmake<C>(0, 0);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[u][r] = cmake<C>(0, 0);
             int64_t p = p0 + lane + 32 * u;
             int64_t pp = p < K ? p : K - 1;
             d[u][0] = -k * dirs[4 * pp]; d[u][1] = -k * dirs[4 * pp + 1]; d[u][2] = -k * dirs[4 * pp + 2];
@@ -68,19 +70,21 @@ __global__ void __launch_bounds__(128) k_c2m(int64_t nleaf, const int* __restric
                 sp[wl][lane][0] = (R)(pos[3 * (int64_t)j] - cx);
                 sp[wl][lane][1] = (R)(pos[3 * (int64_t)j + 1] - cy);
                 sp[wl][lane][2] = (R)(pos[3 * (int64_t)j + 2] - cz);
-                sq[wl][lane] = qs[j];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) sq[wl][r][lane] = qs[r * sn + j];
             }
             __syncwarp();
             int cnt = min(32, b1 - j0);
             for (int t = 0; t < cnt; ++t) {
                 R x = sp[wl][t][0], y = sp[wl][t][1], z = sp[wl][t][2];
-                C q = sq[wl][t];
 #pragma unroll
                 for (int u = 0; u < kC2MPass; ++u) {
                     R ph = d[u][0] * x + d[u][1] * y + d[u][2] * z;
                     R s, c;
                     sc(ph, s, c);
-                    cfma(acc[u], q, cmake<C>(c, s));
+                    const C e = cmake<C>(c, s);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) cfma(acc[u][r], sq[wl][r][t], e);
                 }
             }
             __syncwarp();
@@ -88,18 +92,24 @@ __global__ void __launch_bounds__(128) k_c2m(int64_t nleaf, const int* __restric
 #pragma unroll
         for (int u = 0; u < kC2MPass; ++u) {
             int64_t p = p0 + lane + 32 * u;
-            if (p < K) Fb[p] = acc[u];
+            if (p < K)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) Fb[r * sF + p] = acc[u][r];
         }
     }
 }
 
 // ============================================================== L2O (warp per leaf, lanes = point x slice)
 // GRAD: also grad phi_i += (ik/4pi) sum_p w_p (ik khat_p) e^{ik khat_p.(r_i - c_b)} G_b(p).
-template <typename R, typename C, bool GRAD>
+// NR right-hand sides share each exponential (GRAD only with NR = 1): G[r sF + b K + p],
+// phis[r sn + j].
+template <typename R, typename C, bool GRAD, int NR>
 __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restrict__ leaf_box, const int* __restrict__ begin,
                                              const int* __restrict__ end, const double* __restrict__ center,
                                              const double* __restrict__ pos, const R* __restrict__ dirs, int64_t K, R k,
-                                             const C* __restrict__ G, C* __restrict__ phis, C* __restrict__ grads) {
+                                             const C* __restrict__ G, int64_t sF, C* __restrict__ phis, int64_t sn,
+                                             C* __restrict__ grads) {
+    static_assert(!GRAD || NR == 1, "gradients take one right-hand side per pass");
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t w = (int64_t)blockIdx.x * 4 + wl;
     if (w >= nleaf) return;
@@ -121,7 +131,9 @@ __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restric
             y = (R)(pos[3 * (int64_t)j + 1] - cy);
             z = (R)(pos[3 * (int64_t)j + 2] - cz);
         }
-        C acc = cmake<C>(0, 0);
+        C acc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = cmake<C>(0, 0);
         C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
         for (int64_t p = sl; p < K; p += S) {
             R ph = k * (dirs[4 * p] * x + dirs[4 * p + 1] * y + dirs[4 * p + 2] * z);
@@ -129,10 +141,12 @@ __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restric
             sc(ph, s, c);
             R wp = dirs[4 * p + 3];
             if (!GRAD) {
-                cfma(acc, cmake<C>(wp * c, wp * s), Gb[p]);
+                const C e = cmake<C>(wp * c, wp * s);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) cfma(acc[r], e, Gb[r * sF + p]);
             } else {
                 const C term = cmul(cmake<C>(wp * c, wp * s), Gb[p]);
-                acc = cadd(acc, term);
+                acc[0] = cadd(acc[0], term);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     const R d = dirs[4 * p + a];
@@ -141,8 +155,11 @@ __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restric
             }
         }
         for (int o = 16; o >= P; o >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
+                acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
+            }
             if (GRAD) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
@@ -154,10 +171,13 @@ __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restric
         if (sl == 0 && tp < np) {
             // (ik / 4 pi) * acc
             const R f = k / (R)(4.0 * M_PI);
-            C v = phis[j];
-            v.x += -f * acc.y;
-            v.y += f * acc.x;
-            phis[j] = v;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                C v = phis[r * sn + j];
+                v.x += -f * acc[r].y;
+                v.y += f * acc[r].x;
+                phis[r * sn + j] = v;
+            }
             if (GRAD) {
                 // (ik / 4 pi) (ik) = -k^2 / (4 pi)
                 const R f2 = -k * k / (R)(4.0 * M_PI);
@@ -177,20 +197,22 @@ __global__ void __launch_bounds__(128) k_l2o(int64_t nleaf, const int* __restric
 // ============================================================== C2M / L2O for leaves with many points
 // C2M: one CTA per (leaf, chunk of 128 samples), one sample per thread, the leaf's points
 // staged through shared memory.
-template <typename R, typename C>
+template <typename R, typename C, int NR>
 __global__ void __launch_bounds__(128) k_c2m_big(const int* __restrict__ leaves, const int* __restrict__ begin,
                                                  const int* __restrict__ end, const double* __restrict__ center,
-                                                 const double* __restrict__ pos, const C* __restrict__ qs,
-                                                 const R* __restrict__ dirs, int64_t K, R k, C* __restrict__ F) {
+                                                 const double* __restrict__ pos, const C* __restrict__ qs, int64_t sn,
+                                                 const R* __restrict__ dirs, int64_t K, R k, C* __restrict__ F, int64_t sF) {
     __shared__ R sx[256], sy[256], sz[256];
-    __shared__ C sq[256];
+    __shared__ C sq[NR][256];
     const int b = leaves[blockIdx.x];
     const int b0 = begin[b], b1 = end[b];
     const double cx = center[3 * b], cy = center[3 * b + 1], cz = center[3 * b + 2];
     const int64_t p = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     const int64_t pp = p < K ? p : K - 1;
     const R dx = -k * dirs[4 * pp], dy = -k * dirs[4 * pp + 1], dz = -k * dirs[4 * pp + 2];
-    C acc = cmake<C>(0, 0);
+    C acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = cmake<C>(0, 0);
     for (int j0 = b0; j0 < b1; j0 += 256) {
         const int cnt = min(256, b1 - j0);
         __syncthreads();
@@ -199,28 +221,35 @@ __global__ void __launch_bounds__(128) k_c2m_big(const int* __restrict__ leaves,
             sx[m] = (R)(pos[3 * j] - cx);
             sy[m] = (R)(pos[3 * j + 1] - cy);
             sz[m] = (R)(pos[3 * j + 2] - cz);
-            sq[m] = qs[j];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) sq[r][m] = qs[r * sn + j];
         }
         __syncthreads();
 #pragma unroll 4
         for (int m = 0; m < cnt; ++m) {
             R s, c;
             sc(dx * sx[m] + dy * sy[m] + dz * sz[m], s, c);
-            cfma(acc, sq[m], cmake<C>(c, s));
+            const C e = cmake<C>(c, s);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) cfma(acc[r], sq[r][m], e);
         }
     }
-    if (p < K) F[(int64_t)b * K + p] = acc;
+    if (p < K)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) F[r * sF + (int64_t)b * K + p] = acc[r];
 }
 
 // L2O: one CTA per tile of kP2PTile points of a leaf, one point per thread, the leaf's
 // samples (direction, weight, G) staged through shared memory.
-template <typename R, typename C, bool GRAD>
+template <typename R, typename C, bool GRAD, int NR>
 __global__ void __launch_bounds__(128) k_l2o_big(const int2* __restrict__ tiles, const int* __restrict__ begin,
                                                  const int* __restrict__ end, const double* __restrict__ center,
                                                  const double* __restrict__ pos, const R* __restrict__ dirs, int64_t K, R k,
-                                                 const C* __restrict__ G, C* __restrict__ phis, C* __restrict__ grads) {
+                                                 const C* __restrict__ G, int64_t sF, C* __restrict__ phis, int64_t sn,
+                                                 C* __restrict__ grads) {
+    static_assert(!GRAD || NR == 1, "gradients take one right-hand side per pass");
     __shared__ R sd[256][4];
-    __shared__ C sg[256];
+    __shared__ C sg[NR][256];
     const int2 tile = tiles[blockIdx.x];
     const int b = tile.x;
     const int i = begin[b] + tile.y + threadIdx.x;
@@ -233,7 +262,9 @@ __global__ void __launch_bounds__(128) k_l2o_big(const int2* __restrict__ tiles,
         z = (R)(pos[3 * (int64_t)i + 2] - cz);
     }
     const C* Gb = G + (int64_t)b * K;
-    C acc = cmake<C>(0, 0);
+    C acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = cmake<C>(0, 0);
     C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
     for (int64_t p0 = 0; p0 < K; p0 += 256) {
         const int cnt = (int)min((int64_t)256, K - p0);
@@ -241,7 +272,8 @@ __global__ void __launch_bounds__(128) k_l2o_big(const int2* __restrict__ tiles,
         for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
 #pragma unroll
             for (int a = 0; a < 4; ++a) sd[m][a] = dirs[4 * (p0 + m) + a];
-            sg[m] = Gb[p0 + m];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) sg[r][m] = Gb[r * sF + p0 + m];
         }
         __syncthreads();
         for (int m = 0; m < cnt; ++m) {
@@ -249,10 +281,12 @@ __global__ void __launch_bounds__(128) k_l2o_big(const int2* __restrict__ tiles,
             sc(k * (sd[m][0] * x + sd[m][1] * y + sd[m][2] * z), s, c);
             const R wp = sd[m][3];
             if (!GRAD) {
-                cfma(acc, cmake<C>(wp * c, wp * s), sg[m]);
+                const C e = cmake<C>(wp * c, wp * s);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) cfma(acc[r], e, sg[r][m]);
             } else {
-                const C term = cmul(cmake<C>(wp * c, wp * s), sg[m]);
-                acc = cadd(acc, term);
+                const C term = cmul(cmake<C>(wp * c, wp * s), sg[0][m]);
+                acc[0] = cadd(acc[0], term);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) ga[a] = cadd(ga[a], cmake<C>(sd[m][a] * term.x, sd[m][a] * term.y));
             }
@@ -260,10 +294,13 @@ __global__ void __launch_bounds__(128) k_l2o_big(const int2* __restrict__ tiles,
     }
     if (valid) {
         const R f = k / (R)(4.0 * M_PI);
-        C v = phis[i];
-        v.x += -f * acc.y;
-        v.y += f * acc.x;
-        phis[i] = v;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            C v = phis[r * sn + i];
+            v.x += -f * acc[r].y;
+            v.y += f * acc[r].x;
+            phis[r * sn + i] = v;
+        }
         if (GRAD) {
             const R f2 = -k * k / (R)(4.0 * M_PI);
 #pragma unroll
@@ -279,13 +316,14 @@ __global__ void __launch_bounds__(128) k_l2o_big(const int2* __restrict__ tiles,
 
 // ============================================================== M2L (Eq. 9)
 // G_t = sum over s in V(t) of T_{t-s} F_s, organised per parent P: a warp takes P and a
-// 32U-sample slice of the grid (p = tile * 32U + lane + 32u), walks the list of P's
-// colleagues' children that are far from some child of P (entries (src * K) << 32 |
-// far-children mask << 16 | base), loads each source's samples once and adds them to every
-// child of P it is far from.  The operators of the slice are staged in shared memory as the
-// full 7^3 offset cube Ts[343][32U] (the 27 near rows zero), so the row of a (child, source)
-// pair is base(source) + c(child).  The child count NT is a template argument, so each entry
-// costs NT predicated child slots.
+// 32-sample slice of the grid (p = tile * 32 + lane), walks the list of P's colleagues'
+// children that are far from some child of P (entries (src * K) << 32 | far-children mask
+// << 16 | base), loads each source's samples once and adds them to every child of P it is
+// far from.  The operators of the slice are staged in shared memory as the full 7^3 offset
+// cube Ts[343][32] (the 27 near rows zero), so the row of a (child, source) pair is
+// base(source) + c(child).  The child count NT is a template argument, so each entry costs
+// NT predicated child slots.  NR right-hand sides (signatures r sF apart) share every
+// operator load.
 constexpr int kM2LParentsPerWarp = 4;
 
 // cp.async of B bytes global -> shared; v = false fills the B bytes with zeros (nothing is read)
@@ -300,22 +338,21 @@ __device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, bool 
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <typename C, int U, int NT>
+template <typename C, int NR, int NT>
 __device__ __forceinline__ void m2l_parent(int lane, int t0, const uint64_t* __restrict__ ckey,
-                                           const unsigned long long* __restrict__ le, int ne, const C* const (&Fp)[U],
-                                           const C* Tl, const bool (&ok)[U], int64_t K, int64_t p0, C* __restrict__ G) {
-    constexpr int TS = 32 * U;
-    int cr[NT];     // child part of the row index, times TS
+                                           const unsigned long long* __restrict__ le, int ne, const C* Fp, int64_t sF,
+                                           const C* Tl, bool ok, int64_t K, int64_t p0, C* __restrict__ G) {
+    int cr[NT];     // child part of the row index, times 32
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
         const int ct = (int)(ckey[t0 + t] & 7);
-        cr[t] = ((ct & 1) + 7 * ((ct >> 1) & 1) + 49 * (ct >> 2)) * TS;
+        cr[t] = ((ct & 1) + 7 * ((ct >> 1) & 1) + 49 * (ct >> 2)) * 32;
     }
-    C acc[NT][U];
+    C acc[NT][NR];
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
-        for (int u = 0; u < U; ++u) acc[t][u] = cmake<C>(0, 0);
+        for (int r = 0; r < NR; ++r) acc[t][r] = cmake<C>(0, 0);
     // the lanes fetch 32 list entries at once and broadcast them one by one
     for (int eb = 0; eb < ne; eb += 32) {
         const unsigned long long mine = eb + lane < ne ? __ldg(le + eb + lane) : 0ull;
@@ -323,65 +360,57 @@ __device__ __forceinline__ void m2l_parent(int lane, int t0, const uint64_t* __r
         for (int j = 0; j < cnt; ++j) {
             const unsigned long long w = __shfl_sync(0xffffffffu, mine, j);
             const unsigned lo = (unsigned)w;
-            C f[U];
+            const C* fs = Fp + (unsigned)(w >> 32);
+            C f[NR];
 #pragma unroll
-            for (int u = 0; u < U; ++u) f[u] = Fp[u][(unsigned)(w >> 32)];
-            const C* Tb = Tl + (lo & 511u) * TS;
+            for (int r = 0; r < NR; ++r) f[r] = fs[r * sF];
+            const C* Tb = Tl + (lo & 511u) * 32;
 #pragma unroll
             for (int t = 0; t < NT; ++t)
                 if (lo & (0x10000u << t)) {
-                    const C* Tr = Tb + cr[t];
+                    const C tv = Tb[cr[t]];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) cfma(acc[t][u], Tr[32 * u], f[u]);
+                    for (int r = 0; r < NR; ++r) cfma(acc[t][r], tv, f[r]);
                 }
         }
     }
+    if (ok)
 #pragma unroll
-    for (int t = 0; t < NT; ++t)
+        for (int t = 0; t < NT; ++t)
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (ok[u]) G[(int64_t)(t0 + t) * K + p0 + lane + 32 * u] = acc[t][u];
+            for (int r = 0; r < NR; ++r) G[r * sF + (int64_t)(t0 + t) * K + p0 + lane] = acc[t][r];
 }
 
-template <typename R, typename C, int U, int NW>
+template <typename R, typename C, int NR, int NW>
 __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __restrict__ pcb, const int* __restrict__ pce,
                                                    const int* __restrict__ loff, const unsigned long long* __restrict__ lsrc,
                                                    const uint64_t* __restrict__ ckey, const int* __restrict__ off343,
-                                                   const C* __restrict__ F, const C* __restrict__ T, int64_t K,
+                                                   const C* __restrict__ F, const C* __restrict__ T, int64_t K, int64_t sF,
                                                    C* __restrict__ G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int TS = 32 * U;
-    C* Ts = reinterpret_cast<C*>(smem_raw);                               // [343][TS]
+    C* Ts = reinterpret_cast<C*>(smem_raw);                               // [343][32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t p0 = (int64_t)blockIdx.y * TS;
+    const int64_t p0 = (int64_t)blockIdx.y * 32;
     const int64_t P0 = (int64_t)blockIdx.x * (NW * kM2LParentsPerWarp);
     // stage the slice with asynchronous copies: warp w takes rows w, w + NW, ...; the far-offset
     // index of each row is fetched once per warp; near rows and samples past K are zero-filled
-    static_assert(343 <= 32 * NW, "one far-offset index per lane");
     {
         const int nrw = (343 - warp + NW - 1) / NW;
-        const int myo = lane < nrw ? off343[warp + NW * lane] : -1;
-        for (int j = 0; j < nrw; ++j) {
-            const int r = warp + NW * j;
-            const int o = __shfl_sync(0xffffffffu, myo, j);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int l = lane + 32 * u;
-                const bool v = o >= 0 && p0 + l < K;
-                cp_async_zfill<sizeof(C)>(Ts + r * TS + l, v ? T + (int64_t)o * K + p0 + l : T, v);
+        for (int jb = 0; jb < nrw; jb += 32) {         // batches of 32 rows: one offset index per lane
+            const int myo = jb + lane < nrw ? off343[warp + NW * (jb + lane)] : -1;
+            const int nb = nrw - jb < 32 ? nrw - jb : 32;
+            for (int j = 0; j < nb; ++j) {
+                const int r = warp + NW * (jb + j);
+                const int o = __shfl_sync(0xffffffffu, myo, j);
+                const bool v = o >= 0 && p0 + lane < K;
+                cp_async_zfill<sizeof(C)>(Ts + r * 32 + lane, v ? T + (int64_t)o * K + p0 + lane : T, v);
             }
         }
         cp_async_wait_all();
     }
     __syncthreads();
-    const C* Fp[U];
-    bool ok[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int64_t p = p0 + lane + 32 * u;
-        ok[u] = p < K;
-        Fp[u] = F + (ok[u] ? p : K - 1);       // lane's sample; + (src * K) per source
-    }
+    const bool ok = p0 + lane < K;
+    const C* Fp = F + (ok ? p0 + lane : K - 1);       // lane's sample; + (src * K) per source
     const C* Tl = Ts + lane;
     for (int pw = 0; pw < kM2LParentsPerWarp; ++pw) {
         const int64_t P = P0 + (int64_t)pw * NW + warp;
@@ -390,7 +419,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __r
         const unsigned long long* le = lsrc + loff[P];
         const int ne = loff[P + 1] - loff[P];
         switch (nt) {
-#define M2L_NT(n) case n: m2l_parent<C, U, n>(lane, t0, ckey, le, ne, Fp, Tl, ok, K, p0, G); break;
+#define M2L_NT(n) case n: m2l_parent<C, NR, n>(lane, t0, ckey, le, ne, Fp, sF, Tl, ok, K, p0, G); break;
             M2L_NT(1) M2L_NT(2) M2L_NT(3) M2L_NT(4) M2L_NT(5) M2L_NT(6) M2L_NT(7) M2L_NT(8)
 #undef M2L_NT
             default: break;
@@ -398,23 +427,25 @@ __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __r
     }
 }
 
-// one sample per lane; 32 warps share the 88 KB complex64 operator slice, 16 the 176 KB
-// complex128 one
-template <typename C> struct M2LShape { static constexpr int U = 1, NW = sizeof(C) == 8 ? 32 : 16; };
+// warps per CTA sharing the operator slice (88 KB complex64, 176 KB complex128): as many as
+// the registers of the accumulators (8 children x NR right-hand sides) allow
+template <typename C, int NR> struct M2LShape {
+    static constexpr int NW = sizeof(C) == 8 ? (NR == 1 ? 32 : 16) : (NR == 1 ? 16 : 8);
+};
 
 template <typename R, typename C>
-static size_t m2l_smem() { return (size_t)343 * 32 * M2LShape<C>::U * sizeof(C); }
+static size_t m2l_smem() { return (size_t)343 * 32 * sizeof(C); }
 
-template <typename R, typename C>
+template <typename R, typename C, int NR>
 static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
-    constexpr int U = M2LShape<C>::U, NW = M2LShape<C>::NW;
+    constexpr int NW = M2LShape<C, NR>::NW;
     const FarLevel& F = p.far[l];
     const TreeLevel& T = p.lev[l];
     const TreeLevel& TP = p.lev[l - 1];
-    const dim3 grid(nblk(TP.nbox, NW * kM2LParentsPerWarp), nblk(F.K, 32 * U));
-    k_m2l<R, C, U, NW><<<grid, 32 * NW, m2l_smem<R, C>(), s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off,
-                                                               TP.m2l_src, T.key, p.off343, (const C*)F.F, (const C*)F.T,
-                                                               F.K, (C*)F.G);
+    const dim3 grid(nblk(TP.nbox, NW * kM2LParentsPerWarp), nblk(F.K, 32));
+    k_m2l<R, C, NR, NW><<<grid, 32 * NW, m2l_smem<R, C>(), s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off,
+                                                                TP.m2l_src, T.key, p.off343, (const C*)F.F, (const C*)F.T,
+                                                                F.K, T.nbox * F.K, (C*)F.G);
     MLFMA_LAUNCH_CHECK();
 }
 
@@ -930,13 +961,18 @@ static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int n
 }
 
 // ============================================================== pipeline
-template <typename R>
+// One pass of the far field for NR right-hand sides (charges qs[r n + j], potentials
+// phis[r n + j]; signatures of level l r nbox_l K_l apart).  C2M, M2L and L2O take all NR
+// at once; the interpolation steps run per right-hand side on the shared spectral scratch.
+template <typename R, int NR>
 static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v) {
     using C = typename Cx<R>::T;
     cudaStream_t s = p.stream;
     const C* qs = (const C*)qs_v;
     C* phis = (C*)phis_v;
     const R k = (R)p.k;
+    const int64_t sn = p.n;
+    auto sF = [&](int l) { return p.lev[l].nbox * p.far[l].K; };
     // ---- upward pass: C2M at every far level's leaves, M2M from the deepest level up
     for (int l = p.nlev; l >= p.top; --l) {
         FarLevel& F = p.far[l];
@@ -944,13 +980,14 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         if (T.nleaf > 0) {
             StageTimer st(p, MLFMA_STAGE_C2M, l, (T.n_small_leaves > 0) + (T.n_big_leaves > 0));
             if (T.n_small_leaves > 0) {
-                k_c2m<R, C><<<nblk(T.n_small_leaves, 4), 128, 0, s>>>(T.n_small_leaves, T.small_leaves, T.begin, T.end,
-                                                                    T.center, p.pos, qs, (const R*)F.dirs, F.K, k, (C*)F.F);
+                k_c2m<R, C, NR><<<nblk(T.n_small_leaves, 4), 128, 0, s>>>(T.n_small_leaves, T.small_leaves, T.begin,
+                                                                        T.end, T.center, p.pos, qs, sn, (const R*)F.dirs,
+                                                                        F.K, k, (C*)F.F, sF(l));
                 MLFMA_LAUNCH_CHECK();
             }
             if (T.n_big_leaves > 0) {
-                k_c2m_big<R, C><<<dim3((unsigned)T.n_big_leaves, nblk(F.K, 128)), 128, 0, s>>>(
-                    T.big_leaves, T.begin, T.end, T.center, p.pos, qs, (const R*)F.dirs, F.K, k, (C*)F.F);
+                k_c2m_big<R, C, NR><<<dim3((unsigned)T.n_big_leaves, nblk(F.K, 128)), 128, 0, s>>>(
+                    T.big_leaves, T.begin, T.end, T.center, p.pos, qs, sn, (const R*)F.dirs, F.K, k, (C*)F.F, sF(l));
                 MLFMA_LAUNCH_CHECK();
             }
         }
@@ -961,31 +998,35 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         const int64_t rows_c = TC.nbox * (int64_t)Ch.nth;
         const int budget = (int)(kFftSmemBytes / sizeof(C));
         const int CPB = fused_children(Ch.nth, Ch.nph, 0, sizeof(C));
-        StageTimer st(p, MLFMA_STAGE_M2M, l, CPB ? 2 : 3);
-        size_t sm;
-        if (CPB) {
-            // A+B: forward FFT of the children's rows and theta maps, on chip
-            launch_m2m_in<C, R>(CPB, (int)TC.nbox, (const C*)Ch.F, Lc, Ch.nth, F.nth, Ch.fft, (const C*)Ch.tw,
-                                (R)(1.0 / Ch.nph), (const R*)F.At, (C*)F.Y, s);
-        } else {
-            // A: forward FFT of the children's rows, modes |m| <= Lc
-            int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - Ch.nph, 2 * Ch.nph);
-            sm = ((size_t)2 * RB * Ch.nph + Ch.nph) * sizeof(C);
-            k_fft_fwd_rows<C, R><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, (const C*)Ch.F, Lc, Ch.fft,
-                                                                      (const C*)Ch.tw, (R)(1.0 / Ch.nph), RB,
-                                                                      FastDiv::make(RB), (C*)F.X);
+        StageTimer st(p, MLFMA_STAGE_M2M, l, NR * (CPB ? 2 : 3));
+        for (int r = 0; r < NR; ++r) {
+            const C* Fc = (const C*)Ch.F + r * sF(l + 1);
+            C* Fp = (C*)F.F + r * sF(l);
+            size_t sm;
+            if (CPB) {
+                // A+B: forward FFT of the children's rows and theta maps, on chip
+                launch_m2m_in<C, R>(CPB, (int)TC.nbox, Fc, Lc, Ch.nth, F.nth, Ch.fft, (const C*)Ch.tw,
+                                    (R)(1.0 / Ch.nph), (const R*)F.At, (C*)F.Y, s);
+            } else {
+                // A: forward FFT of the children's rows, modes |m| <= Lc
+                int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - Ch.nph, 2 * Ch.nph);
+                sm = ((size_t)2 * RB * Ch.nph + Ch.nph) * sizeof(C);
+                k_fft_fwd_rows<C, R><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, Fc, Lc, Ch.fft, (const C*)Ch.tw,
+                                                                          (R)(1.0 / Ch.nph), RB, FastDiv::make(RB),
+                                                                          (C*)F.X);
+                MLFMA_LAUNCH_CHECK();
+                // B: theta maps per mode
+                launch_theta_map<R, C>(p, TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, (const C*)F.X, (C*)F.Y, s);
+            }
+            // C: z-shift per mode, inverse FFT, xy-shift, sum over children
+            const int pbudget = (int)(kParentSmemBytes / sizeof(C));
+            const int RT = balanced_rows(F.nth, tile_rows(F.nth, pbudget - F.nph, 8 * F.nph));
+            sm = ((size_t)8 * RT * F.nph + F.nph) * sizeof(C);
+            k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(
+                T.child_begin, T.child_end, TC.key, (int)TC.nbox, (const C*)F.Y, Lc, F.nth, F.fft, (const C*)F.tw,
+                (const C*)F.Sz, (const C*)F.Sxy, RT, FastDiv::make(RT), FastDiv::make(F.nph), Fp);
             MLFMA_LAUNCH_CHECK();
-            // B: theta maps per mode
-            launch_theta_map<R, C>(p, TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, (const C*)F.X, (C*)F.Y, s);
         }
-        // C: z-shift per mode, inverse FFT, xy-shift, sum over children
-        const int pbudget = (int)(kParentSmemBytes / sizeof(C));
-        int RT = balanced_rows(F.nth, tile_rows(F.nth, pbudget - F.nph, 8 * F.nph));
-        sm = ((size_t)8 * RT * F.nph + F.nph) * sizeof(C);
-        k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(
-            T.child_begin, T.child_end, TC.key, (int)TC.nbox, (const C*)F.Y, Lc, F.nth, F.fft, (const C*)F.tw,
-            (const C*)F.Sz, (const C*)F.Sxy, RT, FastDiv::make(RT), FastDiv::make(F.nph), (C*)F.F);
-        MLFMA_LAUNCH_CHECK();
     }
     // ---- downward pass: M2L, L2L, L2O
     for (int l = p.top; l <= p.nlev; ++l) {
@@ -994,58 +1035,62 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         TreeLevel& TP = p.lev[l - 1];
         {
             StageTimer st(p, MLFMA_STAGE_M2L, l, 1);
-            launch_m2l<R, C>(p, l, s);
+            launch_m2l<R, C, NR>(p, l, s);
         }
         if (l > p.top) {
             FarLevel& Pf = p.far[l - 1];
             const int Lc = F.L;
             const int CPB = fused_children(F.nth, F.nph, (2 * Lc + 1) * Pf.nth, sizeof(C));
-            StageTimer st(p, MLFMA_STAGE_L2L, l, CPB ? 2 : 3);
+            StageTimer st(p, MLFMA_STAGE_L2L, l, NR * (CPB ? 2 : 3));
             const int budget = (int)(kFftSmemBytes / sizeof(C));
             const int pbudget = (int)(kParentSmemBytes / sizeof(C));
-            int RT = balanced_rows(Pf.nth, tile_rows(Pf.nth, pbudget - Pf.nph, 8 * Pf.nph));
-            size_t sm = ((size_t)8 * RT * Pf.nph + Pf.nph) * sizeof(C);
-            k_l2l_fft_in<C, R><<<dim3((unsigned)TP.nbox, nblk(Pf.nth, RT)), 128, sm, s>>>(
-                TP.child_begin, TP.child_end, T.key, (int)T.nbox, (const C*)Pf.G, Lc, Pf.nth, Pf.fft, (const C*)Pf.tw,
-                (const C*)Pf.Sz, (const C*)Pf.Sxy, RT, FastDiv::make(RT), FastDiv::make(Pf.nph), (R)(1.0 / Pf.nph),
-                (C*)Pf.Y);
-            MLFMA_LAUNCH_CHECK();
-            if (CPB) {
-                // theta maps and inverse FFT of the children's rows, on chip; added to G
-                launch_l2l_out<C, R>(CPB, (int)T.nbox, (const C*)Pf.Y, Lc, F.nth, Pf.nth, F.fft, (const C*)F.tw,
-                                     (const R*)Pf.Bt, (C*)F.G, s);
-            } else {
-                launch_theta_map<R, C>(p, T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, (const C*)Pf.Y, (C*)Pf.X, s);
-                const int64_t rows_c = T.nbox * (int64_t)F.nth;
-                int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * F.nph);
-                sm = ((size_t)2 * RB * F.nph + F.nph) * sizeof(C);
-                k_l2l_fft_out<C><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, (const C*)Pf.X, Lc, F.fft, (const C*)F.tw,
-                                                                    RB, FastDiv::make(RB), (C*)F.G);
+            const int RT = balanced_rows(Pf.nth, tile_rows(Pf.nth, pbudget - Pf.nph, 8 * Pf.nph));
+            for (int r = 0; r < NR; ++r) {
+                const C* Gp = (const C*)Pf.G + r * sF(l - 1);
+                C* Gc = (C*)F.G + r * sF(l);
+                size_t sm = ((size_t)8 * RT * Pf.nph + Pf.nph) * sizeof(C);
+                k_l2l_fft_in<C, R><<<dim3((unsigned)TP.nbox, nblk(Pf.nth, RT)), 128, sm, s>>>(
+                    TP.child_begin, TP.child_end, T.key, (int)T.nbox, Gp, Lc, Pf.nth, Pf.fft, (const C*)Pf.tw,
+                    (const C*)Pf.Sz, (const C*)Pf.Sxy, RT, FastDiv::make(RT), FastDiv::make(Pf.nph), (R)(1.0 / Pf.nph),
+                    (C*)Pf.Y);
                 MLFMA_LAUNCH_CHECK();
+                if (CPB) {
+                    // theta maps and inverse FFT of the children's rows, on chip; added to G
+                    launch_l2l_out<C, R>(CPB, (int)T.nbox, (const C*)Pf.Y, Lc, F.nth, Pf.nth, F.fft, (const C*)F.tw,
+                                         (const R*)Pf.Bt, Gc, s);
+                } else {
+                    launch_theta_map<R, C>(p, T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, (const C*)Pf.Y, (C*)Pf.X, s);
+                    const int64_t rows_c = T.nbox * (int64_t)F.nth;
+                    int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * F.nph);
+                    sm = ((size_t)2 * RB * F.nph + F.nph) * sizeof(C);
+                    k_l2l_fft_out<C><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, (const C*)Pf.X, Lc, F.fft,
+                                                                        (const C*)F.tw, RB, FastDiv::make(RB), Gc);
+                    MLFMA_LAUNCH_CHECK();
+                }
             }
         }
         if (T.nleaf > 0) {
             StageTimer st(p, MLFMA_STAGE_L2O, l, (T.n_small_leaves > 0) + (T.n_big_tiles > 0));
             if (T.n_small_leaves > 0) {
                 if (grads_v)
-                    k_l2o<R, C, true><<<nblk(T.n_small_leaves, 4), 128, 0, s>>>(T.n_small_leaves, T.small_leaves, T.begin,
-                                                                              T.end, T.center, p.pos, (const R*)F.dirs, F.K,
-                                                                              k, (const C*)F.G, phis, (C*)grads_v);
+                    k_l2o<R, C, true, 1><<<nblk(T.n_small_leaves, 4), 128, 0, s>>>(
+                        T.n_small_leaves, T.small_leaves, T.begin, T.end, T.center, p.pos, (const R*)F.dirs, F.K, k,
+                        (const C*)F.G, sF(l), phis, sn, (C*)grads_v);
                 else
-                    k_l2o<R, C, false><<<nblk(T.n_small_leaves, 4), 128, 0, s>>>(T.n_small_leaves, T.small_leaves, T.begin,
-                                                                               T.end, T.center, p.pos, (const R*)F.dirs, F.K,
-                                                                               k, (const C*)F.G, phis, nullptr);
+                    k_l2o<R, C, false, NR><<<nblk(T.n_small_leaves, 4), 128, 0, s>>>(
+                        T.n_small_leaves, T.small_leaves, T.begin, T.end, T.center, p.pos, (const R*)F.dirs, F.K, k,
+                        (const C*)F.G, sF(l), phis, sn, nullptr);
                 MLFMA_LAUNCH_CHECK();
             }
             if (T.n_big_tiles > 0) {
                 if (grads_v)
-                    k_l2o_big<R, C, true><<<(unsigned)T.n_big_tiles, 128, 0, s>>>(T.big_tiles, T.begin, T.end, T.center, p.pos,
-                                                                               (const R*)F.dirs, F.K, k, (const C*)F.G, phis,
-                                                                               (C*)grads_v);
+                    k_l2o_big<R, C, true, 1><<<(unsigned)T.n_big_tiles, 128, 0, s>>>(
+                        T.big_tiles, T.begin, T.end, T.center, p.pos, (const R*)F.dirs, F.K, k, (const C*)F.G, sF(l), phis,
+                        sn, (C*)grads_v);
                 else
-                    k_l2o_big<R, C, false><<<(unsigned)T.n_big_tiles, 128, 0, s>>>(T.big_tiles, T.begin, T.end, T.center,
-                                                                                p.pos, (const R*)F.dirs, F.K, k,
-                                                                                (const C*)F.G, phis, nullptr);
+                    k_l2o_big<R, C, false, NR><<<(unsigned)T.n_big_tiles, 128, 0, s>>>(
+                        T.big_tiles, T.begin, T.end, T.center, p.pos, (const R*)F.dirs, F.K, k, (const C*)F.G, sF(l), phis,
+                        sn, nullptr);
                 MLFMA_LAUNCH_CHECK();
             }
         }
@@ -1076,18 +1121,25 @@ void prepare_kernels(Plan& p) {
     if (p.prec == MLFMA_PREC_FP64) prepare_fft_kernels<double2, double>();
     else prepare_fft_kernels<float2, float>();
     if (p.prec == MLFMA_PREC_FP32_TF32X3) prepare_theta_tc();
-    if (p.prec == MLFMA_PREC_FP64)
-        MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<double, double2, M2LShape<double2>::U, M2LShape<double2>::NW>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_smem<double, double2>()));
-    else
-        MLFMA_CUDA(cudaFuncSetAttribute(k_m2l<float, float2, M2LShape<float2>::U, M2LShape<float2>::NW>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_smem<float, float2>()));
+    if (p.prec == MLFMA_PREC_FP64) {
+        allow_max_smem(k_m2l<double, double2, 1, M2LShape<double2, 1>::NW>);
+        allow_max_smem(k_m2l<double, double2, kMaxNR, M2LShape<double2, kMaxNR>::NW>);
+    } else {
+        allow_max_smem(k_m2l<float, float2, 1, M2LShape<float2, 1>::NW>);
+        allow_max_smem(k_m2l<float, float2, kMaxNR, M2LShape<float2, kMaxNR>::NW>);
+    }
 }
 
-void far_apply(Plan& p, const void* qs, void* phis, void* grads) {
+void far_apply(Plan& p, const void* qs, void* phis, void* grads, int nr) {
     if (!p.top) return;
-    if (p.prec == MLFMA_PREC_FP64) far_pipeline<double>(p, qs, phis, grads);
-    else far_pipeline<float>(p, qs, phis, grads);
+    if (nr != 1 && nr != kMaxNR) fail(MLFMA_ERR_INVALID_ARG, "right-hand sides per pass %d", nr);
+    if (p.prec == MLFMA_PREC_FP64) {
+        if (nr == 1) far_pipeline<double, 1>(p, qs, phis, grads);
+        else far_pipeline<double, kMaxNR>(p, qs, phis, nullptr);
+    } else {
+        if (nr == 1) far_pipeline<float, 1>(p, qs, phis, grads);
+        else far_pipeline<float, kMaxNR>(p, qs, phis, nullptr);
+    }
 }
 
 }  // namespace mlfma

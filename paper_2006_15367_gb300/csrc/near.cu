@@ -14,8 +14,6 @@
 
 namespace mlfma {
 
-void far_apply(Plan& p, const void* qs, void* phis);
-
 static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 __device__ __forceinline__ void scpi(float x, float& s, float& c) { sincospif(x, &s, &c); }
@@ -46,15 +44,18 @@ struct LevelRanges {
 // cursor: box entry and points of it already consumed.
 constexpr int kP2PSlots = 128;
 
-template <typename R, typename C, bool GRAD>
+// NR right-hand sides (charges and potentials sn apart) share each kernel value; GRAD only
+// with NR = 1.
+template <typename R, typename C, bool GRAD, int NR>
 __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restrict__ leaves, const int* __restrict__ leaf_level,
                                              const int* __restrict__ leaf_box, const int* __restrict__ near_off,
                                              const int* __restrict__ near_lev, const int* __restrict__ near_box, LevelRanges LR,
-                                             const double* __restrict__ pos, const C* __restrict__ qs, R kpi,
+                                             const double* __restrict__ pos, const C* __restrict__ qs, int64_t sn, R kpi,
                                              C* __restrict__ phis, C* __restrict__ grads) {
+    static_assert(!GRAD || NR == 1, "gradients take one right-hand side per pass");
     constexpr unsigned FULL = 0xffffffffu;
     __shared__ R sx[4][kP2PSlots], sy[4][kP2PSlots], sz[4][kP2PSlots];
-    __shared__ C sq[4][kP2PSlots];
+    __shared__ C sq[4][NR][kP2PSlots];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t wi = (int64_t)blockIdx.x * 4 + wl;
     if (wi >= nleaf) return;
@@ -77,7 +78,9 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
             y = (R)(pos[3 * (int64_t)i + 1] - cy);
             z = (R)(pos[3 * (int64_t)i + 2] - cz);
         }
-        C acc = cmake<C>(0, 0);
+        C acc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = cmake<C>(0, 0);
         C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
         const R kk = kpi * (R)M_PI;
         int eb = s_lo, oe = 0;
@@ -113,7 +116,8 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
                     sx[wl][sidx] = (R)(pos[3 * j] - cx);
                     sy[wl][sidx] = (R)(pos[3 * j + 1] - cy);
                     sz[wl][sidx] = (R)(pos[3 * j + 2] - cz);
-                    sq[wl][sidx] = qs[j];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) sq[wl][r][sidx] = qs[r * sn + j];
                 }
             }
             // advance the cursor past the consumed points
@@ -137,10 +141,12 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
                         R s, c;
                         scpi(kpi * r, s, c);
                         if (!GRAD) {
-                            cfma(acc, sq[wl][jj], cmake<C>(c * inv, s * inv));
+                            const C g = cmake<C>(c * inv, s * inv);
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) cfma(acc[r], sq[wl][r][jj], g);
                         } else {
-                            const C qe = cmul(sq[wl][jj], cmake<C>(c * inv, s * inv));   // q e^{ikR} / R
-                            acc = cadd(acc, qe);
+                            const C qe = cmul(sq[wl][0][jj], cmake<C>(c * inv, s * inv));   // q e^{ikR} / R
+                            acc[0] = cadd(acc[0], qe);
                             // q e^{ikR} (ikR - 1) / R^3 = qe (ikR - 1) / R^2
                             const R i2 = inv * inv;
                             const C g = cmul(qe, cmake<C>(-i2, kk * r * i2));
@@ -154,8 +160,11 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
             __syncwarp();
         }
         for (int o = 16; o >= P; o >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
+                acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
+            }
             if (GRAD) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
@@ -165,7 +174,8 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
             }
         }
         if (sl == 0 && tp < np) {
-            phis[i] = acc;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) phis[r * sn + i] = acc[r];
             if (GRAD)
 #pragma unroll
                 for (int a = 0; a < 3; ++a) grads[3 * (int64_t)i + a] = ga[a];
@@ -177,16 +187,17 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
 // Larger leaves: one CTA per tile of kP2PTile targets, one target per thread; the source
 // points of every near box are staged through shared memory (positions relative to the
 // target leaf centre, FP64 difference then rounded) in tiles of 2 * kP2PTile.
-template <typename R, typename C, bool GRAD>
+template <typename R, typename C, bool GRAD, int NR>
 __global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ tiles, const int* __restrict__ leaf_level,
                                                        const int* __restrict__ leaf_box, const int* __restrict__ near_off,
                                                        const int* __restrict__ near_lev, const int* __restrict__ near_box,
                                                        LevelRanges LR, const double* __restrict__ pos,
-                                                       const C* __restrict__ qs, R kpi, C* __restrict__ phis,
+                                                       const C* __restrict__ qs, int64_t sn, R kpi, C* __restrict__ phis,
                                                        C* __restrict__ grads) {
+    static_assert(!GRAD || NR == 1, "gradients take one right-hand side per pass");
     constexpr int SRC = 2 * kP2PTile;
     __shared__ R sx[SRC], sy[SRC], sz[SRC];
-    __shared__ C sq[SRC];
+    __shared__ C sq[NR][SRC];
     const int2 tile = tiles[blockIdx.x];
     const int w = tile.x;
     const int l = leaf_level[w], b = leaf_box[w];
@@ -202,7 +213,9 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ 
         z = (R)(pos[3 * (int64_t)i + 2] - cz);
     }
     const R kk = kpi * (R)M_PI;
-    C acc = cmake<C>(0, 0);
+    C acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = cmake<C>(0, 0);
     C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
     for (int e = near_off[w]; e < near_off[w + 1]; ++e) {
         const int ls = near_lev[e], bs = near_box[e];
@@ -215,7 +228,8 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ 
                 sx[m] = (R)(pos[3 * j] - cx);
                 sy[m] = (R)(pos[3 * j + 1] - cy);
                 sz[m] = (R)(pos[3 * j + 2] - cz);
-                sq[m] = qs[j];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) sq[r][m] = qs[r * sn + j];
             }
             __syncthreads();
             if (valid) {
@@ -228,15 +242,17 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ 
                         const R inv = r2 > (R)0 ? rsq(r2) : (R)0;
                         R s, c;
                         scpi_fast(kpi * (r2 * inv), s, c);
-                        cfma(acc, sq[m], cmake<C>(c * inv, s * inv));
+                        const C g = cmake<C>(c * inv, s * inv);
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) cfma(acc[r], sq[r][m], g);
                     } else if (r2 > (R)0) {
                         const R inv = rsq(r2);
                         const R r = r2 * inv;
                         R s, c;
                         scpi(kpi * r, s, c);
                         {
-                            const C qe = cmul(sq[m], cmake<C>(c * inv, s * inv));
-                            acc = cadd(acc, qe);
+                            const C qe = cmul(sq[0][m], cmake<C>(c * inv, s * inv));
+                            acc[0] = cadd(acc[0], qe);
                             const R i2 = inv * inv;
                             const C g = cmul(qe, cmake<C>(-i2, kk * r * i2));
                             ga[0] = cadd(ga[0], cmake<C>(g.x * dx, g.y * dx));
@@ -249,7 +265,8 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ 
         }
     }
     if (valid) {
-        phis[i] = acc;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) phis[r * sn + i] = acc[r];
         if (GRAD)
 #pragma unroll
             for (int a = 0; a < 3; ++a) grads[3 * (int64_t)i + a] = ga[a];
@@ -301,7 +318,7 @@ void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj, int6
     MLFMA_LAUNCH_CHECK();
 }
 
-template <typename R>
+template <typename R, int NR>
 static void near_apply(Plan& p, const void* qs, void* phis, void* grads) {
     using C = typename Cx<R>::T;
     LevelRanges LR;
@@ -310,43 +327,50 @@ static void near_apply(Plan& p, const void* qs, void* phis, void* grads) {
         LR.end[l] = l <= p.nlev ? p.lev[l].end : nullptr;
         LR.center[l] = l <= p.nlev ? p.lev[l].center : nullptr;
     }
-    const int64_t nl = p.n_small;
+    const int64_t nl = p.n_small, sn = p.n;
     const R kpi = (R)(p.k / M_PI);
     StageTimer st(p, MLFMA_STAGE_P2P, 0, (nl > 0) + (p.n_tiles > 0));
     if (nl > 0) {
         if (grads)
-            k_p2p<R, C, true><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off,
-                                                                 p.near_lev, p.near_box, LR, p.pos, (const C*)qs, kpi,
-                                                                 (C*)phis, (C*)grads);
+            k_p2p<R, C, true, 1><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off,
+                                                                    p.near_lev, p.near_box, LR, p.pos, (const C*)qs, sn,
+                                                                    kpi, (C*)phis, (C*)grads);
         else
-            k_p2p<R, C, false><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off,
-                                                                  p.near_lev, p.near_box, LR, p.pos, (const C*)qs, kpi,
-                                                                  (C*)phis, nullptr);
+            k_p2p<R, C, false, NR><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.p2p_small, p.leaf_level, p.leaf_box,
+                                                                      p.near_off, p.near_lev, p.near_box, LR, p.pos,
+                                                                      (const C*)qs, sn, kpi, (C*)phis, nullptr);
         MLFMA_LAUNCH_CHECK();
     }
     if (p.n_tiles > 0) {
         if (grads)
-            k_p2p_tile<R, C, true><<<(unsigned)p.n_tiles, kP2PTile, 0, p.stream>>>(
-                p.p2p_tiles, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, kpi,
+            k_p2p_tile<R, C, true, 1><<<(unsigned)p.n_tiles, kP2PTile, 0, p.stream>>>(
+                p.p2p_tiles, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, sn, kpi,
                 (C*)phis, (C*)grads);
         else
-            k_p2p_tile<R, C, false><<<(unsigned)p.n_tiles, kP2PTile, 0, p.stream>>>(
-                p.p2p_tiles, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, kpi,
+            k_p2p_tile<R, C, false, NR><<<(unsigned)p.n_tiles, kP2PTile, 0, p.stream>>>(
+                p.p2p_tiles, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, sn, kpi,
                 (C*)phis, nullptr);
         MLFMA_LAUNCH_CHECK();
     }
 }
 
 void near_only(Plan& p, const void* qs, void* phis) {
-    if (p.prec == MLFMA_PREC_FP64) near_apply<double>(p, qs, phis, nullptr);
-    else near_apply<float>(p, qs, phis, nullptr);
+    if (p.prec == MLFMA_PREC_FP64) near_apply<double, 1>(p, qs, phis, nullptr);
+    else near_apply<float, 1>(p, qs, phis, nullptr);
 }
 
-void apply_pipeline(Plan& p, const void* qs, void* phis, void* grads) {
-    if (p.prec == MLFMA_PREC_FP64) near_apply<double>(p, qs, phis, grads);
-    else near_apply<float>(p, qs, phis, grads);
+// nr right-hand sides (q and phi n apart): 1, or kMaxNR without gradients
+void apply_pipeline(Plan& p, const void* qs, void* phis, void* grads, int nr) {
+    if (nr == kMaxNR && !grads) {
+        if (p.prec == MLFMA_PREC_FP64) near_apply<double, kMaxNR>(p, qs, phis, nullptr);
+        else near_apply<float, kMaxNR>(p, qs, phis, nullptr);
+    } else {
+        if (nr != 1) fail(MLFMA_ERR_INVALID_ARG, "right-hand sides per pass %d", nr);
+        if (p.prec == MLFMA_PREC_FP64) near_apply<double, 1>(p, qs, phis, grads);
+        else near_apply<float, 1>(p, qs, phis, grads);
+    }
     if (p.near_dump) MLFMA_CUDA(cudaMemcpyAsync(p.near_dump, phis, p.n * csize(p), cudaMemcpyDeviceToDevice, p.stream));
-    far_apply(p, qs, phis, grads);
+    far_apply(p, qs, phis, grads, nr);
 }
 
 template <typename C>

@@ -222,3 +222,47 @@ def test_full_size_sphere_fp64_three_digits():
     ref = direct.direct(pts, q[0], prm["k"], targets=tg)
     assert rel(phi[tg], ref) < 1e-3
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_rhs_passes_match_single_applies(sphere4k, prec):
+    """9 right-hand sides run as two passes of 4 (kernels sharing exponentials and operator
+    loads) and one single pass; each matches its own single apply.  Graphs captured before and
+    after the signature buffers grow give the same results."""
+    import torch
+    pts, _, prm = sphere4k
+    Q = synth.complex_normal(98, pts.shape[0], nrhs=9).astype(cdtype(prec))
+    plan = make_plan(pts, prm["k"], 3, prec)
+    dev = torch.device("cuda", 0)
+    before = [plan.apply(torch.as_tensor(Q[r], device=dev)).cpu().numpy() for r in range(2)]
+    batch = plan.apply(torch.as_tensor(Q, device=dev)).cpu().numpy()
+    tol = 1e-6 if prec == "fp32" else 1e-13
+    for r in range(9):
+        single = plan.apply(torch.as_tensor(Q[r], device=dev)).cpu().numpy()
+        assert rel(batch[r], single) < tol, r
+        if r < 2:
+            assert np.array_equal(single, before[r])
+    plan.close()
+
+
+def test_rhs_passes_batched_geometries():
+    """A plan over 3 geometries with 5 right-hand sides (one pass of 4, one single)."""
+    import torch
+
+    import paper_2006_15367_gb300 as mf
+    geoms = [synth.sphere(1500, 1.2, seed=101), synth.sphere(900, 0.8, seed=102), synth.sphere(2100, 1.5, seed=103)]
+    pts = np.concatenate(geoms)
+    off = np.concatenate([[0], np.cumsum([g.shape[0] for g in geoms])]).astype(np.int64)
+    dev = torch.device("cuda", 0)
+    plan = mf.Plan(torch.as_tensor(pts, device=dev), K, 3, offsets=off)
+    Q = synth.complex_normal(99, pts.shape[0], nrhs=5).astype(np.complex64)
+    one = plan.apply(torch.as_tensor(Q[0], device=dev)).cpu().numpy()
+    batch = plan.apply(torch.as_tensor(Q, device=dev)).cpu().numpy()
+    again = plan.apply(torch.as_tensor(Q[0], device=dev)).cpu().numpy()
+    assert np.array_equal(one, again)
+    assert rel(batch[0], one) < 1e-6
+    for g in range(3):
+        a, b = int(off[g]), int(off[g + 1])
+        ref = direct.direct(pts[a:b], Q[4][a:b].astype(np.complex128), K)
+        assert rel(batch[4][a:b], ref) < 1e-3
+    plan.close()
