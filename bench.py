@@ -197,6 +197,131 @@ WORKLOADS = {
 }
 
 
+def _time_ms(fn, stream, steps, warmup=2):
+    """Mean CUDA-event time of fn() on stream (after warm-up)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def _rel_err(mf, torch, ptd, q0, k, out, n, ntg=500, seed=7):
+    rng = np.random.default_rng(seed)
+    tg = np.sort(rng.choice(n, min(ntg, n), replace=False))
+    dev = ptd.device
+    dref = mf.direct_fp64(ptd, torch.as_tensor(q0, device=dev), k, torch.as_tensor(tg, device=dev))
+    got = out.to(torch.complex128)[torch.as_tensor(tg, device=dev)]
+    return float(torch.linalg.norm(got - dref) / torch.linalg.norm(dref))
+
+
+def measure_forms(dev, pts, q, prm, fp32_ms):
+    """The precision, batching and adjoint forms against the plain paths, same geometry and digits.
+
+    precision: the plain FP64 path vs the FP32 (and split-TF32 tensor-core) paths at the same
+    digits; batching: 64 right-hand sides per apply vs one, and one plan over 64 ellipsoids vs
+    64 separate plans; adjoint: forward + backward (charges and positions) vs one apply.
+    """
+    import torch
+    import paper_2006_15367_gb300 as mf
+    import synth
+    out = {}
+    n = pts.shape[0]
+    ptd = torch.as_tensor(pts, device=dev)
+
+    def guarded(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as e:                    # a form that fails is reported, not fatal
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        torch.cuda.empty_cache()
+
+    def precision(prec):
+        cdt = np.complex128 if prec == "fp64" else np.complex64
+        qd = torch.as_tensor(q[0].astype(cdt), device=dev)
+        res = torch.empty_like(qd)
+        plan = mf.Plan(ptd, prm["k"], prm["digits"], precision=prec)
+        t = _time_ms(lambda: plan.apply(qd, res), plan.stream, 3)
+        err = _rel_err(mf, torch, ptd, q[0], prm["k"], res, n)
+        plan.close()
+        return {"ms": t, "rel_err_vs_fp64_direct": err}
+
+    guarded("fp64", lambda: precision("fp64"))
+    guarded("tf32x3", lambda: precision("tf32x3"))
+    if "ms" in out.get("fp64", {}):
+        out["fp64"]["note"] = "plain FP64 path, same digits"
+        out["fp32_speedup_vs_fp64"] = out["fp64"]["ms"] / fp32_ms
+        if "ms" in out.get("tf32x3", {}):
+            out["tf32x3_speedup_vs_fp64"] = out["fp64"]["ms"] / out["tf32x3"]["ms"]
+            out["tf32x3_speedup_vs_fp32"] = fp32_ms / out["tf32x3"]["ms"]
+
+    def nrhs64():
+        Q = synth.complex_normal(2003, n, nrhs=64).astype(np.complex64)
+        qd = torch.as_tensor(Q, device=dev)
+        res = torch.empty_like(qd)
+        plan = mf.Plan(ptd, prm["k"], prm["digits"], precision="fp32")
+        t = _time_ms(lambda: plan.apply(qd, res), plan.stream, 2, warmup=1)
+        err = _rel_err(mf, torch, ptd, Q[5], prm["k"], res[5], n)
+        plan.close()
+        return {"ms": t, "ms_per_rhs": t / 64, "speedup_per_rhs_vs_single": fp32_ms / (t / 64),
+                "rel_err_rhs5": err}
+
+    guarded("nrhs64", nrhs64)
+
+    def geometries():
+        geoms, sizes, _ = synth.ellipsoid_batch(64, seed=4001)
+        allp = np.concatenate(geoms)
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        Q = synth.complex_normal(4002, allp.shape[0])[0].astype(np.complex64)
+        ap = torch.as_tensor(allp, device=dev)
+        qd = torch.as_tensor(Q, device=dev)
+        res = torch.empty_like(qd)
+        plan = mf.Plan(ap, prm["k"], prm["digits"], precision="fp32", offsets=off)
+        tb = _time_ms(lambda: plan.apply(qd, res), plan.stream, 3)
+        plan.close()
+        ts = 0.0
+        for g in range(64):
+            a, b = int(off[g]), int(off[g + 1])
+            pg = mf.Plan(ap[a:b].contiguous(), prm["k"], prm["digits"], precision="fp32")
+            qg = qd[a:b].contiguous()
+            rg = torch.empty_like(qg)
+            ts += _time_ms(lambda: pg.apply(qg, rg), pg.stream, 3)
+            pg.close()
+        return {"geometries": 64, "points": int(allp.shape[0]), "batched_ms": tb, "separate_plans_ms": ts,
+                "speedup": ts / tb}
+
+    guarded("geometries64", geometries)
+
+    def adjoint():
+        pe, qe, pre = synth.workload("ellipsoid256k")
+        pdev = torch.as_tensor(pe, device=dev)
+        qd = torch.as_tensor(qe[0].astype(np.complex64), device=dev)
+        tgt = torch.as_tensor(synth.complex_normal(5003, pe.shape[0])[0].astype(np.complex64), device=dev)
+        plan = mf.Plan(pdev, pre["k"], pre["digits"], precision="fp32")
+        res = torch.empty_like(qd)
+        ta = _time_ms(lambda: plan.apply(qd, res), plan.stream, 3)
+        rt = pdev.clone().requires_grad_(True)
+
+        def fb():
+            qv = qd.detach().requires_grad_(True)
+            phi = mf.mlfma(qv, rt, plan)
+            torch.sum(torch.abs(phi - tgt) ** 2).backward()
+        tg = _time_ms(fb, plan.stream, 3)
+        plan.close()
+        return {"workload": "ellipsoid (8,4,2) N=262144", "apply_ms": ta, "forward_backward_ms": tg,
+                "ratio": tg / ta}
+
+    guarded("adjoint", adjoint)
+    return out
+
+
 def config_dict(args, n, prm):
     """The workload description shared by both arms of the benchmark."""
     return {"workload": WORKLOADS[args.workload] + f", {args.precision.upper()} complex, nrhs={args.nrhs}"
@@ -231,6 +356,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32x3"])
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the precision / batching / adjoint form comparisons added to the JSON line")
     ap.add_argument("--mode", default="apply", choices=["apply", "grad"],
                     help="apply: phi = A q; grad: forward + backward of sum |phi - t|^2 for q and the positions")
     args = ap.parse_args()
@@ -440,9 +567,12 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
     }
     line["clocks"] = clk.summary()
+    plan.close()
+    if rank == 0 and not args.no_forms and args.workload == WORKLOAD and args.precision == "fp32" and nrhs == 1 \
+            and args.mode == "apply":
+        line["forms"] = measure_forms(dev, pts, q, prm, ms)
     if rank == 0:
         print(json.dumps(line))
-    plan.close()
     if dist:
         dist.destroy_process_group()
     return 0
