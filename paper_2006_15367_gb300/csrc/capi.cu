@@ -104,6 +104,7 @@ static void ensure_far_rhs(Plan& p, int nr) {
         p.mem.drop(F.G);
         F.F = p.mem.get(bytes);
         F.G = p.mem.get(bytes);
+        MLFMA_CUDA(cudaMemsetAsync(F.G, 0, bytes, p.stream));    // boxes M2L never writes stay zero
     }
     p.far_nr = nr;
     p.graphs_stale = true;
@@ -168,7 +169,7 @@ static void sweep(Plan& p, const void* qin, void* phiout, void* gout, int64_t ld
 // The whole apply of P from P.qin to P.phiout on stream s (batched plans fork their
 // geometries over the sub-streams and join back).
 static void sweep_all(Plan& P, cudaStream_t s, int nrhs, bool adjoint, bool grad) {
-    if (P.subs.empty()) {
+    if (P.subs.empty() || P.forest) {
         cudaStream_t keep = P.stream;
         P.stream = s;
         try {
@@ -443,6 +444,10 @@ mlfma_status mlfma_plan_create_batched(const double* points, const int64_t* offs
             configure(*sp, offsets[g + 1] - offsets[g], k, digits, leaf_max, o);
             build_plan(*sp, pts + 3 * offsets[g]);
         }
+        if (forest_possible(P.subs)) {
+            build_forest(P);
+            P.forest = true;
+        }
         MLFMA_CUDA(cudaStreamSynchronize(P.stream));
         P.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         *out = h;
@@ -516,7 +521,9 @@ mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info) {
         info->device_bytes = (int64_t)p.mem.bytes;
         info->setup_ms = p.setup_ms;
         info->n_geom = p.subs.empty() ? 1 : (int)p.subs.size();
-        if (!p.subs.empty()) {
+        if (p.forest) {                                // the merged levels (height above the leaves)
+            for (const Plan* sp : p.subs) info->device_bytes += (int64_t)sp->mem.bytes;
+        } else if (!p.subs.empty()) {
             const Plan& s0 = *p.subs[0];
             info->nlev = s0.nlev;
             info->top = s0.top;

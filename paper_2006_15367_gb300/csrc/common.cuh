@@ -229,7 +229,10 @@ struct Plan {
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::map<int64_t, cudaGraphExec_t> graphs;
-    // batched plans: independent geometries, run concurrently on sub_streams
+    // batched plans: independent geometries; level-uniform ones are merged into this plan as a
+    // forest (the sub-plans then only hold the shared operators), others run concurrently on
+    // sub_streams
+    bool forest = false;
     std::vector<Plan*> subs;
     std::vector<int64_t> sub_off;  // [n_geom + 1] offsets into the caller's point order
     std::vector<cudaStream_t> sub_streams;
@@ -267,6 +270,9 @@ void build_far_levels(Plan& p);
 void build_m2l_lists(Plan& p);
 void build_p2p_work(Plan& p);
 void prepare_kernels(Plan& p);
+// forest.cu
+bool forest_possible(const std::vector<Plan*>& subs);
+void build_forest(Plan& P);
 // theta_tc.cu: split-TF32 tensor-core theta maps (complex64 data)
 void prepare_theta_tc();
 void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const float* M, const float2* in,
