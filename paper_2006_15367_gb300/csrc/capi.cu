@@ -579,7 +579,17 @@ mlfma_status mlfma_plan_export(const mlfma_plan* plan, int item, int level, void
             case MLFMA_EXPORT_F: parts.push_back({p.far[level].F, L->nbox * p.far[level].K * csize(p)}); break;
             case MLFMA_EXPORT_G: parts.push_back({p.far[level].G, L->nbox * p.far[level].K * csize(p)}); break;
             case MLFMA_EXPORT_NEAR_PHI: parts.push_back({p.near_dump, p.n * csize(p)}); break;
-            case MLFMA_EXPORT_TRANSLATION: parts.push_back({p.far[level].T, kNumOffsets * p.far[level].K * csize(p)}); break;
+            case MLFMA_EXPORT_TRANSLATION: {   // the 316 far rows of the 7^3 cube in raster order
+                const size_t row = p.far[level].K * csize(p);
+                for (int dz = -3; dz <= 3; ++dz)
+                    for (int dy = -3; dy <= 3; ++dy)
+                        for (int dx = -3; dx <= 3; ++dx) {
+                            if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) <= 1) continue;
+                            const int r = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
+                            parts.push_back({(const char*)p.far[level].T + r * row, row});
+                        }
+                break;
+            }
             default: fail(MLFMA_ERR_INVALID_ARG, "unknown export item %d", item);
         }
         size_t tot = 0;

@@ -1,6 +1,7 @@
 // Internal declarations of the MLFMA library (plan layout, helpers, kernels' launchers).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -150,6 +151,8 @@ struct FftPlan {                   // mixed-radix factorisation of an FFT length
 FftPlan make_fft_plan(int n);
 int smooth_even(int m);
 
+constexpr int kTBoxRows = 172;     // rows of one TMA box of T (two boxes cover the 343 rows)
+
 struct FarLevel {                  // sampling grid, operators and signatures of one far-field level
     int L = 0, nth = 0, nph = 0;
     FftPlan fft;                   // plan for length nph
@@ -158,7 +161,9 @@ struct FarLevel {                  // sampling grid, operators and signatures of
     double* wgl = nullptr;         // [nth] weights, FP64
     void* dirs = nullptr;          // [K][4] real: khat_p (x, y, z) and quadrature weight w_p
     void* tw = nullptr;            // [nph] complex: e^{-2 pi i j / nph}
-    void* T = nullptr;             // [316][K] complex translation operators
+    void* T = nullptr;             // [343][K] complex translation operators by offset raster index
+                                   // (dx+3) + 7 (dy+3) + 49 (dz+3); the 27 near rows are zero
+    CUtensorMap tmT;               // TMA descriptor of T (boxes of 32 samples x kTBoxRows rows)
     void* F = nullptr;             // [nbox][K] complex multipole signatures
     void* G = nullptr;             // [nbox][K] complex local signatures
     // interpolation from level l+1 (child) to this level (parent); set when l+1 is far-field
@@ -266,6 +271,7 @@ void build_tree(Plan& p, const double* pts_dev);
 void build_lists(Plan& p);
 // setup.cu
 int truncation_L(double edge, double k, int digits, int margin);
+void encode_translation_map(FarLevel& F, size_t csz);
 void build_far_levels(Plan& p);
 void build_m2l_lists(Plan& p);
 void build_p2p_work(Plan& p);

@@ -381,34 +381,60 @@ __device__ __forceinline__ void m2l_parent(int lane, int t0, const uint64_t* __r
             for (int r = 0; r < NR; ++r) G[r * sF + (int64_t)(t0 + t) * K + p0 + lane] = acc[t][r];
 }
 
+__device__ __forceinline__ bool m2l_bar_wait(uint32_t bar, uint32_t phase) {
+    for (long long i = 0; i < (1ll << 22); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 template <typename R, typename C, int NR, int NW>
 __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __restrict__ pcb, const int* __restrict__ pce,
                                                    const int* __restrict__ loff, const unsigned long long* __restrict__ lsrc,
-                                                   const uint64_t* __restrict__ ckey, const int* __restrict__ off343,
-                                                   const C* __restrict__ F, const C* __restrict__ T, int64_t K, int64_t sF,
-                                                   C* __restrict__ G) {
+                                                   const uint64_t* __restrict__ ckey, const __grid_constant__ CUtensorMap tmT,
+                                                   const C* __restrict__ F, int64_t K, int64_t sF, C* __restrict__ G,
+                                                   int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* Ts = reinterpret_cast<C*>(smem_raw);                               // [343][32]
+    __shared__ __align__(8) uint64_t tbar;
+    // operator slice Ts[344][32] at a 128-byte boundary (TMA destination)
+    C* Ts = reinterpret_cast<C*>(smem_raw + ((128 - ((uintptr_t)smem_raw & 127)) & 127));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p0 = (int64_t)blockIdx.y * 32;
     const int64_t P0 = (int64_t)blockIdx.x * (NW * kM2LParentsPerWarp);
-    // stage the slice with asynchronous copies: warp w takes rows w, w + NW, ...; the far-offset
-    // index of each row is fetched once per warp; near rows and samples past K are zero-filled
-    {
-        const int nrw = (343 - warp + NW - 1) / NW;
-        for (int jb = 0; jb < nrw; jb += 32) {         // batches of 32 rows: one offset index per lane
-            const int myo = jb + lane < nrw ? off343[warp + NW * (jb + lane)] : -1;
-            const int nb = nrw - jb < 32 ? nrw - jb : 32;
-            for (int j = 0; j < nb; ++j) {
-                const int r = warp + NW * (jb + j);
-                const int o = __shfl_sync(0xffffffffu, myo, j);
-                const bool v = o >= 0 && p0 + lane < K;
-                cp_async_zfill<sizeof(C)>(Ts + r * 32 + lane, v ? T + (int64_t)o * K + p0 + lane : T, v);
-            }
-        }
-        cp_async_wait_all();
+    // stage the slice with two TMA boxes of kTBoxRows rows (rows 343 and samples past K read as
+    // zero) completing on one mbarrier
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&tbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        constexpr uint32_t box = kTBoxRows * 32 * sizeof(C);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(2 * box) : "memory");
+        const int x = (int)(p0 * (int64_t)(sizeof(C) / 8));
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Ts + b * kTBoxRows * 32);
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];\n" ::"r"(dst),
+                "l"(reinterpret_cast<uint64_t>(&tmT)), "r"(x), "r"(b * kTBoxRows), "r"(bar)
+                : "memory");
+        }
+    }
+    if (!__syncthreads_and(m2l_bar_wait(bar, 0))) {
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        m2l_bar_wait(bar, 0);                     // bounded: let the copies in flight land
+        return;
+    }
     const bool ok = p0 + lane < K;
     const C* Fp = F + (ok ? p0 + lane : K - 1);       // lane's sample; + (src * K) per source
     const C* Tl = Ts + lane;
@@ -434,7 +460,7 @@ template <typename C, int NR> struct M2LShape {
 };
 
 template <typename R, typename C>
-static size_t m2l_smem() { return (size_t)343 * 32 * sizeof(C); }
+static size_t m2l_smem() { return (size_t)2 * kTBoxRows * 32 * sizeof(C) + 128; }
 
 template <typename R, typename C, int NR>
 static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
@@ -444,8 +470,8 @@ static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
     const TreeLevel& TP = p.lev[l - 1];
     const dim3 grid(nblk(TP.nbox, NW * kM2LParentsPerWarp), nblk(F.K, 32));
     k_m2l<R, C, NR, NW><<<grid, 32 * NW, m2l_smem<R, C>(), s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off,
-                                                                TP.m2l_src, T.key, p.off343, (const C*)F.F, (const C*)F.T,
-                                                                F.K, T.nbox * F.K, (C*)F.G);
+                                                                TP.m2l_src, T.key, F.tmT, (const C*)F.F, F.K,
+                                                                T.nbox * F.K, (C*)F.G, p.dev_err);
     MLFMA_LAUNCH_CHECK();
 }
 

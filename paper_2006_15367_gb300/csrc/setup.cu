@@ -53,6 +53,31 @@ FftPlan make_fft_plan(int n) {
     return p;
 }
 
+// TMA descriptor of a level's operators T[343][K] (complex as 8-byte elements: K or 2 K per
+// row), box of 32 complex samples x kTBoxRows rows; out-of-range samples and rows read as zero
+void encode_translation_map(FarLevel& F, size_t csz) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        MLFMA_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) fail(MLFMA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        encode = (Encode)fn;
+    }
+    const cuuint64_t per = csz / 8;                      // 8-byte elements per complex sample
+    const cuuint64_t dims[2] = {(cuuint64_t)F.K * per, 343};
+    const cuuint64_t strides[1] = {(cuuint64_t)F.K * csz};
+    const cuuint32_t box[2] = {(cuuint32_t)(32 * per), (cuuint32_t)kTBoxRows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(&F.tmT, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, F.T, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(MLFMA_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for K = %lld", (int)r, (long long)F.K);
+}
+
 int truncation_L(double edge, double k, int digits, int margin) {
     double kD = k * std::sqrt(3.0) * edge;
     double d0 = (double)(digits + margin);
@@ -217,7 +242,9 @@ __global__ void k_translation(int L, int nth, int nph, double edge, const double
         re += a * cr; im += a * ci;
     }
     (void)edge;
-    T[idx] = cmake<C>(re, im);
+    // row of the offset in the 7^3 cube (the 27 near rows stay zero)
+    const int row = (dxyz[3 * o] + 3) + 7 * (dxyz[3 * o + 1] + 3) + 49 * (dxyz[3 * o + 2] + 3);
+    T[(int64_t)row * K + p] = cmake<C>(re, im);
 }
 
 // ---------------------------------------------------------------- interpolation matrices
@@ -329,10 +356,12 @@ static void build_far_levels_t(Plan& p) {
         MLFMA_LAUNCH_CHECK();
         k_hankel<<<nblk(kNumOffsets, 32), 32, 0, s>>>(F.L, p.k, p.lev[l].edge, d_dxyz, hn, work);
         MLFMA_LAUNCH_CHECK();
-        F.T = p.mem.make<C>((size_t)kNumOffsets * F.K);
+        F.T = p.mem.make<C>((size_t)343 * F.K);
+        MLFMA_CUDA(cudaMemsetAsync(F.T, 0, (size_t)343 * F.K * sizeof(C), s));
         k_translation<C><<<nblk(F.K * kNumOffsets, 128), 128, 0, s>>>(F.L, F.nth, F.nph, p.lev[l].edge, F.x, d_dxyz, hn,
                                                                       (C*)F.T);
         MLFMA_LAUNCH_CHECK();
+        encode_translation_map(F, sizeof(C));
         F.F = p.mem.make<C>((size_t)p.lev[l].nbox * F.K);
         F.G = p.mem.make<C>((size_t)p.lev[l].nbox * F.K);
     }
