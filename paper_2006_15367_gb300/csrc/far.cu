@@ -515,10 +515,58 @@ __device__ __forceinline__ void root(int k, T& c, T& s) {
 
 // one radix-R butterfly of a Stockham stage: inputs a[j + r nb], outputs b[q Ns R + k + kk Ns]
 // with q = j / Ns, k = j mod Ns, twiddles tw[k r tstep]
+// R-point DFT X_k = sum_r v_r e^{-+2 pi i r k / R} (- forward, + inverse).  Radix 2 and 4 by
+// additions (the roots 0, +-1, +-i cost no multiplies); odd radices from the pairs
+// a_r = v_r + v_{R-r}, d_r = v_r - v_{R-r}:  A_k = v_0 + sum_r a_r cos(2 pi r k / R),
+// B_k = sum_r d_r sin(2 pi r k / R),  X_k = A_k -+ i B_k,  X_{R-k} = A_k +- i B_k.
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void small_dft(const C (&v)[R], C (&X)[R]) {
+    using T = decltype(C::x);
+    auto sub = [](C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); };
+    auto mi = [](C a) { return cmake<C>(a.y, -a.x); };          // -i a
+    if constexpr (R == 2) {
+        X[0] = cadd(v[0], v[1]);
+        X[1] = sub(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        const C s02 = cadd(v[0], v[2]), d02 = sub(v[0], v[2]);
+        const C s13 = cadd(v[1], v[3]), d13 = mi(sub(v[1], v[3]));
+        X[0] = cadd(s02, s13);
+        X[2] = sub(s02, s13);
+        X[INV ? 3 : 1] = cadd(d02, d13);
+        X[INV ? 1 : 3] = sub(d02, d13);
+    } else {
+        constexpr int H = (R - 1) / 2;
+        C a[H], d[H];
+        C x0 = v[0];
+#pragma unroll
+        for (int r = 1; r <= H; ++r) {
+            a[r - 1] = cadd(v[r], v[R - r]);
+            d[r - 1] = sub(v[r], v[R - r]);
+            x0 = cadd(x0, a[r - 1]);
+        }
+        X[0] = x0;
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            C A = v[0], B = cmake<C>(0, 0);
+#pragma unroll
+            for (int r = 1; r <= H; ++r) {
+                T c, s;
+                root<R, T>((r * k) % R, c, s);         // c = cos, s = -sin of 2 pi r k / R
+                crfma(A, c, a[r - 1]);
+                crfma(B, -s, d[r - 1]);
+            }
+            const C miB = mi(B);
+            X[INV ? R - k : k] = cadd(A, miB);
+            X[INV ? k : R - k] = sub(A, miB);
+        }
+    }
+}
+
+// one radix-R butterfly of a Stockham stage: inputs a[j + r nb], outputs b[q Ns R + k + kk Ns]
+// with q = j / Ns, k = j mod Ns, twiddles tw[k r tstep]
 template <int R, bool INV, typename C>
 __device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict__ b, int j, int nb, int Ns, int q, int tstep,
                                          const C* __restrict__ tw) {
-    using T = decltype(C::x);
     const int k = j - q * Ns;
     C v[R];
 #pragma unroll
@@ -527,19 +575,11 @@ __device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict_
         if (r > 0) x = cmul(x, twid(tw, k * r * tstep, INV));
         v[r] = x;
     }
+    C X[R];
+    small_dft<R, INV>(v, X);
     const int idxD = q * Ns * R + k;
 #pragma unroll
-    for (int kk = 0; kk < R; ++kk) {
-        C acc = v[0];
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-            T c, s;
-            root<R, T>((r * kk) % R, c, s);
-            if (INV) s = -s;
-            cfma(acc, v[r], cmake<C>(c, s));
-        }
-        b[idxD + kk * Ns] = acc;
-    }
+    for (int kk = 0; kk < R; ++kk) b[idxD + kk * Ns] = X[kk];
 }
 
 template <bool INV, typename C>
