@@ -163,6 +163,8 @@ def run_reference(args, ws, rank):
     import synth
     from oracle import direct
     pts, q, prm, _ = load_case(args.workload)
+    if args.digits:
+        prm = dict(prm, digits=args.digits)
     n = pts.shape[0]
     per_step = 256
     rng = np.random.default_rng(123)
@@ -324,7 +326,11 @@ def measure_forms(dev, pts, q, prm, fp32_ms):
 
 def config_dict(args, n, prm):
     """The workload description shared by both arms of the benchmark."""
-    return {"workload": WORKLOADS[args.workload] + f", {args.precision.upper()} complex, nrhs={args.nrhs}"
+    import re
+    wl = re.sub(r"\d+ digits", f"{prm['digits']} digits", WORKLOADS[args.workload])
+    if args.digits:
+        wl += " (digits set on the command line; leaf edge and level count as in the plan object)"
+    return {"workload": wl + f", {args.precision.upper()} complex, nrhs={args.nrhs}"
                         + (", forward+backward (charges and positions)" if args.mode == "grad" else ""),
             "n": n, "digits": prm["digits"], "nrhs": args.nrhs, "mode": args.mode,
             "parallelism": f"replicas x{_dist()[0]}",
@@ -356,6 +362,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32x3"])
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--digits", type=int, default=0, help="override the workload's digits (0: keep)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision / batching / adjoint form comparisons added to the JSON line")
     ap.add_argument("--mode", default="apply", choices=["apply", "grad"],
@@ -377,6 +384,8 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     pts, q, prm, offsets = load_case(args.workload)
+    if args.digits:
+        prm = dict(prm, digits=args.digits)
     n = pts.shape[0]
     nrhs = args.nrhs
     ptd = torch.as_tensor(pts, device=dev)

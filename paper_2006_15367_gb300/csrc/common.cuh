@@ -111,6 +111,11 @@ struct TreeLevel {                 // one octree level (root = 1)
     int64_t n_big_leaves = 0;
     int2* big_tiles = nullptr;     // [n_big_tiles] (box, first point offset)
     int64_t n_big_tiles = 0;
+    // forest plans: boxes of this level without a parent (a geometry's first level in the
+    // forest), as (first box, count) ranges; L2L into this level zeroes their spectral rows
+    int2* orphans = nullptr;
+    int n_orphan_ranges = 0;
+    int64_t n_orphans = 0;
     // M2L work of the children of each box (this level acting as parent level):
     // per box, the candidate sources with at least one far child, packed
     // (src * K) << 32 | far-children mask << 8 | code, code = colleague slot (0..26) * 8 + source octant

@@ -898,6 +898,26 @@ __global__ void k_l2l_out(int nbox_c, const C* __restrict__ H, int Lc, int nthc,
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) g0[idx] = cadd(g0[idx], res[idx]);
 }
 
+// Y[mi][c][i'] = 0 for the boxes c of the given ranges (forest boxes without a parent: the
+// L2L out-stage then adds nothing to them); one thread per (range, box, mode, row) in turn
+template <typename C>
+__global__ void k_zero_orphans(const int2* __restrict__ ranges, int nranges, int64_t total, int nbox_c, int nm, int nthp,
+                               C* __restrict__ Y) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= total * nm * nthp) return;
+    const int ip = (int)(idx % nthp);
+    const int64_t t = idx / nthp;
+    const int mi = (int)(t % nm);
+    int64_t b = t / nm;                       // orphan ordinal
+    int g = 0;
+    while (g < nranges && b >= ranges[g].y) {
+        b -= ranges[g].y;
+        ++g;
+    }
+    if (g >= nranges) return;
+    Y[((int64_t)mi * nbox_c + ranges[g].x + b) * nthp + ip] = cmake<C>(0, 0);
+}
+
 // children per CTA of the fused kernels, a power of two in [2, kMaxCPB] (0: the level pair
 // takes the three-kernel path); extra = complex elements per child staged besides the two
 // FFT buffers
@@ -1107,7 +1127,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
             FarLevel& Pf = p.far[l - 1];
             const int Lc = F.L;
             const int CPB = fused_children(F.nth, F.nph, (2 * Lc + 1) * Pf.nth, sizeof(C));
-            StageTimer st(p, MLFMA_STAGE_L2L, l, NR * (CPB ? 2 : 3));
+            StageTimer st(p, MLFMA_STAGE_L2L, l, NR * ((CPB ? 2 : 3) + (T.n_orphans > 0)));
             const int budget = (int)(kFftSmemBytes / sizeof(C));
             const int pbudget = (int)(kParentSmemBytes / sizeof(C));
             const int RT = balanced_rows(Pf.nth, tile_rows(Pf.nth, pbudget - Pf.nph, 8 * Pf.nph));
@@ -1120,6 +1140,12 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
                     (const C*)Pf.Sz, (const C*)Pf.Sxy, RT, FastDiv::make(RT), FastDiv::make(Pf.nph), (R)(1.0 / Pf.nph),
                     (C*)Pf.Y);
                 MLFMA_LAUNCH_CHECK();
+                if (T.n_orphans > 0) {
+                    const int64_t tot = T.n_orphans * (2 * Lc + 1) * Pf.nth;
+                    k_zero_orphans<C><<<nblk(tot, 256), 256, 0, s>>>(T.orphans, T.n_orphan_ranges, T.n_orphans,
+                                                                     (int)T.nbox, 2 * Lc + 1, Pf.nth, (C*)Pf.Y);
+                    MLFMA_LAUNCH_CHECK();
+                }
                 if (CPB) {
                     // theta maps and inverse FFT of the children's rows, on chip; added to G
                     launch_l2l_out<C, R>(CPB, (int)T.nbox, (const C*)Pf.Y, Lc, F.nth, Pf.nth, F.fft, (const C*)F.tw,

@@ -206,6 +206,29 @@ void build_forest(Plan& P) {
         MLFMA_LAUNCH_CHECK();
     }
 
+    // ---- parentless boxes per level (L2L adds nothing into them)
+    for (int l = 2; l <= Lmax; ++l) {
+        std::vector<int2> rg;
+        int64_t cnt = 0;
+        for (int g = 0; g < G; ++g) {
+            const int lg = l - shift[g];
+            if (!inc(g, l) || inc(g, l - 1)) continue;
+            const int64_t nbs = P.subs[g]->lev[lg].nbox;
+            if (nbs > 0) {
+                rg.push_back(make_int2((int)boff[g][l], (int)nbs));
+                cnt += nbs;
+            }
+        }
+        TreeLevel& T = P.lev[l];
+        T.n_orphan_ranges = (int)rg.size();
+        T.n_orphans = cnt;
+        if (!rg.empty()) {
+            T.orphans = P.mem.make<int2>(rg.size());
+            MLFMA_CUDA(cudaMemcpyAsync(T.orphans, rg.data(), rg.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+            MLFMA_CUDA(cudaStreamSynchronize(s));            // rg is a host temporary
+        }
+    }
+
     // ---- leaf table, near lists, P2P work
     int64_t nleaf = 0, nnear = 0, n_small = 0, n_tiles = 0;
     for (const Plan* sp : P.subs) {

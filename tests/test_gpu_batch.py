@@ -59,3 +59,28 @@ def test_batched_geometries(prec):
             assert rel(out[r, sl], direct.direct(geoms[gi], Q[r, sl], K)) < 1e-3
         single.close()
     plan.close()
+
+
+def test_forest_mixes_tiny_and_large_geometries():
+    """Geometries without a far field (a few points), small ones and a 20k-point sphere in one
+    forest plan: every geometry matches its own plan bit for bit and the direct sum."""
+    import torch
+    geoms = [np.array([[0.0, 0.0, 0.0], [0.3, 0.1, -0.2], [0.05, 0.0, 0.1]]),
+             synth.sphere(20000, 3.0, seed=111),
+             synth.sphere(40, 0.1, seed=112),
+             synth.sphere(1500, 1.0, seed=113),
+             np.array([[1.0, 2.0, 3.0]])]
+    pts = np.concatenate(geoms)
+    off = np.concatenate([[0], np.cumsum([g.shape[0] for g in geoms])])
+    Q = synth.complex_normal(4012, pts.shape[0], nrhs=1)
+    dev = torch.device("cuda", 0)
+    plan = make_plan(pts, K, 3, "fp32", offsets=off)
+    out = plan.apply(torch.as_tensor(Q[0].astype(np.complex64), device=dev)).cpu().numpy()
+    for gi, g in enumerate(geoms):
+        sl = slice(off[gi], off[gi + 1])
+        single = make_plan(g, K, 3, "fp32", graphs=False)
+        ref = single.apply(torch.as_tensor(Q[0, sl].astype(np.complex64), device=dev)).cpu().numpy()
+        assert np.array_equal(out[sl], ref), gi
+        assert rel(out[sl], direct.direct(g, Q[0, sl], K)) < 1e-3, gi
+        single.close()
+    plan.close()
