@@ -964,64 +964,105 @@ static void launch_l2l_out(int CPB, int nbox_c, const C* H, int Lc, int nthc, in
 // ============================================================== theta maps
 // Per Fourier mode, a batched GEMM (complex x real):
 //   out[mi][c][o] = sum_i M[|m|][i][o] in[mi][c][i],   m = mi - Lc
-// Tile BM boxes x BN outputs per CTA (BM * BN = 4096), 256 threads, 4 x 4 per thread,
-// reduction in chunks of 16 staged through shared memory.
-constexpr int kMapBK = 16;
+// Tile BM boxes x BN outputs per CTA (BM * BN = 4096), 256 threads, 4 x 4 per thread; the
+// reduction runs in chunks of BK (16 complex64, 8 complex128) staged in shared memory by
+// cp.async, double-buffered so that the next chunk loads while this one is multiplied.
+template <typename C> __device__ __forceinline__ void ld4c(const C* p, C (&v)[4]) {
+    if constexpr (sizeof(C) == 8) {            // two 16-byte loads
+        const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 2);
+        v[0] = cmake<C>(a.x, a.y); v[1] = cmake<C>(a.z, a.w); v[2] = cmake<C>(b.x, b.y); v[3] = cmake<C>(b.z, b.w);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = p[q];
+    }
+}
+template <typename R> __device__ __forceinline__ void ld4r(const R* p, R (&v)[4]) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else {
+        const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+}
+
+template <typename R, typename C, int BN>
+struct MapShape {
+    static constexpr int BM = 4096 / BN, BK = sizeof(C) == 8 ? 16 : 8, AP = BM + 2;   // AP: padded row of As
+    static constexpr size_t smem = 2 * ((size_t)BK * AP * sizeof(C) + (size_t)BK * BN * sizeof(R));
+};
 
 template <typename R, typename C, int BN>
 __global__ void __launch_bounds__(256) k_theta_map(int nbox, int Lc, int nin, int nout, const R* __restrict__ M,
                                                    const C* __restrict__ in, C* __restrict__ out) {
-    constexpr int BM = 4096 / BN;
+    using S = MapShape<R, C, BN>;
+    constexpr int BM = S::BM, BK = S::BK, AP = S::AP;
     constexpr int TX = BN / 4;            // threads along outputs
-    __shared__ C As[kMapBK][BM + 1];
-    __shared__ R Bs[kMapBK][BN];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* As = reinterpret_cast<C*>(smem_raw);                    // [2][BK][AP]
+    R* Bs = reinterpret_cast<R*>(As + 2 * BK * AP);            // [2][BK][BN]
     const int mi = blockIdx.z;
     const int m = abs(mi - Lc);
     const int c0 = blockIdx.x * BM, o0 = blockIdx.y * BN;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const C* inm = in + (int64_t)mi * nbox * nin;
     const R* Mm = M + (int64_t)m * nin * nout;
+    auto stage = [&](int buf, int k0) {
+        C* a = As + buf * BK * AP;
+        R* bb = Bs + buf * BK * BN;
+        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
+            const int cl = idx / BK, kk = idx % BK;
+            const int c = c0 + cl, i = k0 + kk;
+            const bool v = c < nbox && i < nin;
+            cp_async_zfill<sizeof(C)>(a + kk * AP + cl, v ? inm + (int64_t)c * nin + i : inm, v);
+        }
+        for (int idx = threadIdx.x; idx < BK * BN; idx += 256) {
+            const int kk = idx / BN, ol = idx % BN;
+            const int i = k0 + kk, o = o0 + ol;
+            const bool v = i < nin && o < nout;
+            cp_async_zfill<sizeof(R)>(bb + kk * BN + ol, v ? Mm + (int64_t)i * nout + o : Mm, v);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
     C acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = cmake<C>(0, 0);
-    for (int k0 = 0; k0 < nin; k0 += kMapBK) {
-        for (int idx = threadIdx.x; idx < BM * kMapBK; idx += 256) {
-            const int cl = idx / kMapBK, kk = idx % kMapBK;
-            const int c = c0 + cl, i = k0 + kk;
-            As[kk][cl] = (c < nbox && i < nin) ? inm[(int64_t)c * nin + i] : cmake<C>(0, 0);
-        }
-        for (int idx = threadIdx.x; idx < kMapBK * BN; idx += 256) {
-            const int kk = idx / BN, ol = idx % BN;
-            const int i = k0 + kk, o = o0 + ol;
-            Bs[kk][ol] = (i < nin && o < nout) ? Mm[(int64_t)i * nout + o] : (R)0;
+    const int nch = (nin + BK - 1) / BK;
+    stage(0, 0);
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) {
+            stage((ch + 1) & 1, (ch + 1) * BK);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncthreads();
+        const C* a = As + (ch & 1) * BK * AP;
+        const R* bb = Bs + (ch & 1) * BK * BN;
 #pragma unroll
-        for (int kk = 0; kk < kMapBK; ++kk) {
+        for (int kk = 0; kk < BK; ++kk) {
             C av[4];
             R bv[4];
+            ld4c(a + kk * AP + ty * 4, av);
+            ld4r(bb + kk * BN + tx * 4, bv);
 #pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) crfma(acc[a][b], bv[b], av[a]);
+                for (int j = 0; j < 4; ++j) crfma(acc[i][j], bv[j], av[i]);
         }
-        __syncthreads();
+        __syncthreads();                          // the buffer is restaged two chunks later
     }
     C* outm = out + (int64_t)mi * nbox * nout;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int c = c0 + ty * 4 + a;
+    for (int i = 0; i < 4; ++i) {
+        const int c = c0 + ty * 4 + i;
         if (c >= nbox) continue;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int o = o0 + tx * 4 + b;
-            if (o < nout) outm[(int64_t)c * nout + o] = acc[a][b];
+        for (int j = 0; j < 4; ++j) {
+            const int o = o0 + tx * 4 + j;
+            if (o < nout) outm[(int64_t)c * nout + o] = acc[i][j];
         }
     }
 }
@@ -1036,12 +1077,15 @@ static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int n
         }
     }
     const int nm = 2 * Lc + 1;
-    if (nout <= 16 && sizeof(C) == 8) {          // the 256-box tile of complex128 would exceed 48 KB
-        k_theta_map<R, C, 16><<<dim3(nblk(nbox, 256), nblk(nout, 16), nm), 256, 0, s>>>((int)nbox, Lc, nin, nout, M, in, out);
+    if (nout <= 16) {
+        k_theta_map<R, C, 16><<<dim3(nblk(nbox, 256), nblk(nout, 16), nm), 256, MapShape<R, C, 16>::smem, s>>>(
+            (int)nbox, Lc, nin, nout, M, in, out);
     } else if (nout <= 32) {
-        k_theta_map<R, C, 32><<<dim3(nblk(nbox, 128), nblk(nout, 32), nm), 256, 0, s>>>((int)nbox, Lc, nin, nout, M, in, out);
+        k_theta_map<R, C, 32><<<dim3(nblk(nbox, 128), nblk(nout, 32), nm), 256, MapShape<R, C, 32>::smem, s>>>(
+            (int)nbox, Lc, nin, nout, M, in, out);
     } else {
-        k_theta_map<R, C, 64><<<dim3(nblk(nbox, 64), nblk(nout, 64), nm), 256, 0, s>>>((int)nbox, Lc, nin, nout, M, in, out);
+        k_theta_map<R, C, 64><<<dim3(nblk(nbox, 64), nblk(nout, 64), nm), 256, MapShape<R, C, 64>::smem, s>>>(
+            (int)nbox, Lc, nin, nout, M, in, out);
     }
     MLFMA_LAUNCH_CHECK();
 }
@@ -1207,6 +1251,9 @@ static void prepare_fft_kernels() {
     allow_max_smem(k_l2l_fft_in<C, R>);
     allow_max_smem(k_fft_fwd_rows<C, R>);
     allow_max_smem(k_l2l_fft_out<C>);
+    allow_max_smem(k_theta_map<R, C, 16>);
+    allow_max_smem(k_theta_map<R, C, 32>);
+    allow_max_smem(k_theta_map<R, C, 64>);
 }
 
 void prepare_kernels(Plan& p) {
