@@ -152,6 +152,7 @@ struct FftPlan {                   // mixed-radix factorisation of an FFT length
     // tstep = n / (Ns r[st]) twiddle stride
     int Ns[16] = {0}, nb[16] = {0}, tstep[16] = {0};
     FastDiv dNs[16], dnb[16];
+    FastDiv dn;                    // divides by n
 };
 FftPlan make_fft_plan(int n);
 int smooth_even(int m);

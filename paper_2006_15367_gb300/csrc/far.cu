@@ -584,14 +584,14 @@ __device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict_
 
 template <bool INV, typename C>
 __device__ __forceinline__ void fft_stage(const C* __restrict__ in, C* __restrict__ out, int nrows, const FftPlan& fp, int st,
-                                          const C* __restrict__ tw) {
-    const int n = fp.n, R = fp.r[st], nb = fp.nb[st], Ns = fp.Ns[st], tstep = fp.tstep[st];
+                                          const C* __restrict__ tw, int pitch) {
+    const int R = fp.r[st], nb = fp.nb[st], Ns = fp.Ns[st], tstep = fp.tstep[st];
     const FastDiv dnb = fp.dnb[st], dNs = fp.dNs[st];
     for (int idx = threadIdx.x; idx < nrows * nb; idx += blockDim.x) {
         const int row = (int)dnb.div((unsigned)idx), j = idx - row * nb;
         const int q = (int)dNs.div((unsigned)j);
-        const C* a = in + row * n;
-        C* b = out + row * n;
+        const C* a = in + row * pitch;
+        C* b = out + row * pitch;
         switch (R) {
             case 2: fft_bfly<2, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
             case 3: fft_bfly<3, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
@@ -602,15 +602,17 @@ __device__ __forceinline__ void fft_stage(const C* __restrict__ in, C* __restric
     }
 }
 
-// Transforms nrows rows of length fp.n stored contiguously in buf0; returns the buffer
-// holding the result (buf0 or buf1).  All threads of the block take part.
+// Transforms nrows rows of length fp.n, pitch elements apart, in buf0; returns the buffer
+// holding the result (buf0 or buf1).  All threads of the block take part.  Kernels whose
+// gathers or scatters give consecutive threads consecutive rows use the odd pitch n + 1, so
+// that those rows start in different shared-memory banks.
 template <typename C>
-__device__ C* fft_rows(C* buf0, C* buf1, int nrows, const FftPlan& fp, const C* __restrict__ tw, bool inv) {
+__device__ C* fft_rows(C* buf0, C* buf1, int nrows, const FftPlan& fp, const C* __restrict__ tw, bool inv, int pitch) {
     C* in = buf0;
     C* out = buf1;
     for (int st = 0; st < fp.ns; ++st) {
-        if (inv) fft_stage<true>(in, out, nrows, fp, st, tw);
-        else fft_stage<false>(in, out, nrows, fp, st, tw);
+        if (inv) fft_stage<true>(in, out, nrows, fp, st, tw, pitch);
+        else fft_stage<false>(in, out, nrows, fp, st, tw, pitch);
         __syncthreads();
         C* t = in; in = out; out = t;
     }
@@ -631,22 +633,25 @@ template <typename C, typename R>
 __global__ void k_fft_fwd_rows(int nrows_tot, const C* __restrict__ F, int Lc, FftPlan fp, const C* __restrict__ tw,
                                R scale, int RB, FastDiv dRB, C* __restrict__ X) {
     extern __shared__ unsigned char smem_raw[];
-    const int n = fp.n, nm = 2 * Lc + 1;
+    const int n = fp.n, pn = n + 1, nm = 2 * Lc + 1;
     C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + RB * n;
-    C* stw = buf1 + RB * n;
+    C* buf1 = buf0 + RB * pn;
+    C* stw = buf1 + RB * pn;
     const int r0 = blockIdx.x * RB;
     const int nr = min(RB, nrows_tot - r0);
     const C* src = F + (int64_t)r0 * n;
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) cp_async_zfill<sizeof(C)>(buf0 + idx, src + idx, true);
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
+        const int row = (int)fp.dn.div((unsigned)idx), col = idx - row * n;
+        cp_async_zfill<sizeof(C)>(buf0 + row * pn + col, src + idx, true);
+    }
     for (int j = threadIdx.x; j < n; j += blockDim.x) cp_async_zfill<sizeof(C)>(stw + j, tw + j, true);
     cp_async_wait_all();
     __syncthreads();
-    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
+    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false, pn);
     for (int idx = threadIdx.x; idx < RB * nm; idx += blockDim.x) {
         const int mi = (int)dRB.div((unsigned)idx), row = idx - mi * RB;
         if (row >= nr) continue;
-        C v = res[row * n + wrap(mi - Lc, n)];
+        C v = res[row * pn + wrap(mi - Lc, n)];
         v.x *= scale; v.y *= scale;
         X[(int64_t)mi * nrows_tot + r0 + row] = v;
     }
@@ -694,14 +699,15 @@ __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict_
     if (c0 >= c1) return;
     const int i0 = blockIdx.y * RT;
     const int nr = min(RT, nthp - i0);
+    const int pn = n + 1;
     C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + 4 * RT * n;
-    C* stw = buf1 + 4 * RT * n;
+    C* buf1 = buf0 + 4 * RT * pn;
+    C* stw = buf1 + 4 * RT * pn;
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
     const int nq = parent_quadrants(c0, c1, ckey, s_child, s_q, &s_nq);
-    for (int idx = threadIdx.x; idx < nq * nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
+    for (int idx = threadIdx.x; idx < nq * nr * pn; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
     __syncthreads();
-    // rows of the qi-th present quadrant occupy buf0[(qi * nr + r) * n ...]
+    // rows of the qi-th present quadrant occupy buf0[(qi * nr + r) * pn ...]
     for (int qi = 0; qi < nq; ++qi) {
         const int q = s_q[qi];
         const int ca = s_child[q][0], cz = s_child[q][1];
@@ -712,16 +718,16 @@ __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict_
             C w = cmake<C>(0, 0);
             if (ca >= 0) cfma(w, Sz[i0 + r], Ym[(int64_t)ca * nthp + i0 + r]);
             if (cz >= 0) cfma(w, Sz[nthp + i0 + r], Ym[(int64_t)cz * nthp + i0 + r]);
-            buf0[(qi * nr + r) * n + wrap(mi - Lc, n)] = w;
+            buf0[(qi * nr + r) * pn + wrap(mi - Lc, n)] = w;
         }
     }
     __syncthreads();
-    const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true);
+    const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true, pn);
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
         const int r = (int)dn.div((unsigned)idx), j = idx - r * n;
         C acc = cmake<C>(0, 0);
         for (int qi = 0; qi < nq; ++qi)
-            cfma(acc, Sxy[(int64_t)s_q[qi] * Kp + (int64_t)(i0 + r) * n + j], res[(qi * nr + r) * n + j]);
+            cfma(acc, Sxy[(int64_t)s_q[qi] * Kp + (int64_t)(i0 + r) * n + j], res[(qi * nr + r) * pn + j]);
         Fp[(int64_t)P * Kp + (int64_t)i0 * n + idx] = acc;
     }
 }
@@ -744,9 +750,10 @@ __global__ void k_l2l_fft_in(const int* __restrict__ cb, const int* __restrict__
     if (c0 >= c1) return;
     const int i0 = blockIdx.y * RT;
     const int nr = min(RT, nthp - i0);
+    const int pn = n + 1;
     C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + 4 * RT * n;
-    C* stw = buf1 + 4 * RT * n;
+    C* buf1 = buf0 + 4 * RT * pn;
+    C* stw = buf1 + 4 * RT * pn;
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
     const int nq = parent_quadrants(c0, c1, ckey, s_child, s_q, &s_nq);
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
@@ -754,17 +761,17 @@ __global__ void k_l2l_fft_in(const int* __restrict__ cb, const int* __restrict__
         const C gv = Gp[(int64_t)P * Kp + g];
         const int r = (int)dn.div((unsigned)idx), j = idx - r * n;
         for (int qi = 0; qi < nq; ++qi)
-            buf0[(qi * nr + r) * n + j] = cmul(cconj(Sxy[(int64_t)s_q[qi] * Kp + g]), gv);
+            buf0[(qi * nr + r) * pn + j] = cmul(cconj(Sxy[(int64_t)s_q[qi] * Kp + g]), gv);
     }
     __syncthreads();
-    const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true);
+    const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true, pn);
     for (int qi = 0; qi < nq; ++qi) {
         const int q = s_q[qi];
         const int ca = s_child[q][0], cz = s_child[q][1];
         for (int idx = threadIdx.x; idx < RT * nm; idx += blockDim.x) {
             const int mi = (int)dRT.div((unsigned)idx), r = idx - mi * RT;
             if (r >= nr) continue;
-            C v = res[(qi * nr + r) * n + wrap(mi - Lc, n)];
+            C v = res[(qi * nr + r) * pn + wrap(mi - Lc, n)];
             v.x *= inv_n; v.y *= inv_n;
             C* Ym = Y + (int64_t)mi * nbox_c * nthp;
             if (ca >= 0) Ym[(int64_t)ca * nthp + i0 + r] = cmul(cconj(Sz[i0 + r]), v);
@@ -779,23 +786,27 @@ __global__ void k_l2l_fft_out(int nrows_tot, const C* __restrict__ H, int Lc, Ff
                               FastDiv dRB, C* __restrict__ G) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
+    const int pn = n + 1;
     C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + RB * n;
-    C* stw = buf1 + RB * n;
+    C* buf1 = buf0 + RB * pn;
+    C* stw = buf1 + RB * pn;
     const int r0 = blockIdx.x * RB;
     const int nr = min(RB, nrows_tot - r0);
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
+    for (int idx = threadIdx.x; idx < nr * pn; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
     __syncthreads();
     for (int idx = threadIdx.x; idx < RB * nm; idx += blockDim.x) {
         const int mi = (int)dRB.div((unsigned)idx), row = idx - mi * RB;
         if (row >= nr) continue;
-        buf0[row * n + wrap(mi - Lc, n)] = H[(int64_t)mi * nrows_tot + r0 + row];
+        buf0[row * pn + wrap(mi - Lc, n)] = H[(int64_t)mi * nrows_tot + r0 + row];
     }
     __syncthreads();
-    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
+    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false, pn);
     C* g0 = G + (int64_t)r0 * n;
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) g0[idx] = cadd(g0[idx], res[idx]);
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
+        const int row = (int)fp.dn.div((unsigned)idx), col = idx - row * n;
+        g0[idx] = cadd(g0[idx], res[row * pn + col]);
+    }
 }
 
 // ============================================================== fused phi transform + theta map (fine levels)
@@ -813,6 +824,7 @@ __global__ void k_m2m_in(int nbox_c, const C* __restrict__ F, int Lc, int nthc, 
                          const C* __restrict__ tw, R scale, const R* __restrict__ At, FastDiv dnthp, C* __restrict__ Y) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
+    // unpadded rows: no loop here walks across rows with consecutive threads
     C* buf0 = reinterpret_cast<C*>(smem_raw);
     C* buf1 = buf0 + CPB * nthc * n;
     C* stw = buf1 + CPB * nthc * n;
@@ -824,7 +836,7 @@ __global__ void k_m2m_in(int nbox_c, const C* __restrict__ F, int Lc, int nthc, 
     for (int j = threadIdx.x; j < n; j += blockDim.x) cp_async_zfill<sizeof(C)>(stw + j, tw + j, true);
     cp_async_wait_all();
     __syncthreads();
-    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
+    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false, n);
     const int rowc = nthc * n;                     // stride between children in res
     for (int idx = threadIdx.x; idx < nm * nthp; idx += blockDim.x) {
         const int mi = (int)dnthp.div((unsigned)idx), o = idx - mi * nthp;
@@ -857,27 +869,28 @@ __global__ void k_l2l_out(int nbox_c, const C* __restrict__ H, int Lc, int nthc,
                           FastDiv dhfull, C* __restrict__ G) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
+    const int pn = n + 1, hp = CPB * nthp + 1;     // padded pitches of the FFT rows and of hs
     C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + CPB * nthc * n;
-    C* stw = buf1 + CPB * nthc * n;
-    C* hs = stw + n;                               // [nm][CPB][nthp]
+    C* buf1 = buf0 + CPB * nthc * pn;
+    C* stw = buf1 + CPB * nthc * pn;
+    C* hs = stw + n;                               // [nm][hp]: the CPB children's rows of one mode
     const int c0 = blockIdx.x * CPB;
     const int ncb = min(CPB, nbox_c - c0);
     const int nr = ncb * nthc;
     const int hrow = ncb * nthp;                   // contiguous run of the CTA's children in one mode
     for (int idx = threadIdx.x; idx < nm * hrow; idx += blockDim.x) {
         const int mi = (int)(ncb == CPB ? dhfull : dhrow).div((unsigned)idx), t = idx - mi * hrow;
-        cp_async_zfill<sizeof(C)>(hs + mi * CPB * nthp + t, H + ((int64_t)mi * nbox_c + c0) * nthp + t, true);
+        cp_async_zfill<sizeof(C)>(hs + mi * hp + t, H + ((int64_t)mi * nbox_c + c0) * nthp + t, true);
     }
     for (int j = threadIdx.x; j < n; j += blockDim.x) cp_async_zfill<sizeof(C)>(stw + j, tw + j, true);
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
+    for (int idx = threadIdx.x; idx < nr * pn; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
     cp_async_wait_all();
     __syncthreads();
     for (int idx = threadIdx.x; idx < nm * nthc; idx += blockDim.x) {
         const int mi = (int)dnthc.div((unsigned)idx), i = idx - mi * nthc;
         const int m = abs(mi - Lc);
         const R* Bm = Bt + (int64_t)m * nthp * nthc + i;
-        const C* hm = hs + mi * CPB * nthp;
+        const C* hm = hs + mi * hp;
         C acc[CPB];
 #pragma unroll
         for (int c = 0; c < CPB; ++c) acc[c] = cmake<C>(0, 0);
@@ -890,12 +903,15 @@ __global__ void k_l2l_out(int nbox_c, const C* __restrict__ H, int Lc, int nthc,
         const int col = wrap(mi - Lc, n);
 #pragma unroll
         for (int c = 0; c < CPB; ++c)
-            if (c < ncb) buf0[(c * nthc + i) * n + col] = acc[c];
+            if (c < ncb) buf0[(c * nthc + i) * pn + col] = acc[c];
     }
     __syncthreads();
-    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false);
+    const C* res = fft_rows(buf0, buf1, nr, fp, stw, false, pn);
     C* g0 = G + (int64_t)c0 * nthc * n;
-    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) g0[idx] = cadd(g0[idx], res[idx]);
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
+        const int row = (int)fp.dn.div((unsigned)idx), col = idx - row * n;
+        g0[idx] = cadd(g0[idx], res[row * pn + col]);
+    }
 }
 
 // Y[mi][c][i'] = 0 for the boxes c of the given ranges (forest boxes without a parent: the
@@ -920,11 +936,11 @@ __global__ void k_zero_orphans(const int2* __restrict__ ranges, int nranges, int
 
 // children per CTA of the fused kernels, a power of two in [2, kMaxCPB] (0: the level pair
 // takes the three-kernel path); extra = complex elements per child staged besides the two
-// FFT buffers
+// FFT buffers (rows of ``pitch`` elements), fixed = elements per CTA besides the twiddles
 constexpr size_t kFusedSmemBytes = 40 * 1024;
-static int fused_children(int nthc, int n, int extra, size_t csz) {
-    const size_t per = ((size_t)2 * nthc * n + extra) * csz;
-    const size_t avail = kFusedSmemBytes - (size_t)n * csz;
+static int fused_children(int nthc, int n, int pitch, int extra, int fixed, size_t csz) {
+    const size_t per = ((size_t)2 * nthc * pitch + extra) * csz;
+    const size_t avail = kFusedSmemBytes - (size_t)(n + fixed) * csz;
     int c = 0;
     for (int t = 2; t <= kMaxCPB; t *= 2)
         if ((size_t)t * per <= avail) c = t;
@@ -948,7 +964,8 @@ static void launch_m2m_in(int CPB, int nbox_c, const C* F, int Lc, int nthc, int
 template <typename C, typename R>
 static void launch_l2l_out(int CPB, int nbox_c, const C* H, int Lc, int nthc, int nthp, const FftPlan& fp, const C* tw,
                            const R* Bt, C* G, cudaStream_t s) {
-    const size_t sm = ((size_t)CPB * (2 * nthc * fp.n + (2 * Lc + 1) * nthp) + fp.n) * sizeof(C);
+    const size_t sm =
+        ((size_t)CPB * (2 * nthc * (fp.n + 1) + (2 * Lc + 1) * nthp) + fp.n + (2 * Lc + 1)) * sizeof(C);
     const FastDiv d = FastDiv::make(nthc);
     const int tail = nbox_c % CPB ? nbox_c % CPB : CPB;      // children of the last CTA
     const FastDiv dt = FastDiv::make(tail * nthp), df = FastDiv::make(CPB * nthp);
@@ -1127,7 +1144,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         const int Lc = Ch.L;
         const int64_t rows_c = TC.nbox * (int64_t)Ch.nth;
         const int budget = (int)(kFftSmemBytes / sizeof(C));
-        const int CPB = fused_children(Ch.nth, Ch.nph, 0, sizeof(C));
+        const int CPB = fused_children(Ch.nth, Ch.nph, Ch.nph, 0, 0, sizeof(C));
         StageTimer st(p, MLFMA_STAGE_M2M, l, NR * (CPB ? 2 : 3));
         for (int r = 0; r < NR; ++r) {
             const C* Fc = (const C*)Ch.F + r * sF(l + 1);
@@ -1139,8 +1156,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
                                     (R)(1.0 / Ch.nph), (const R*)F.At, (C*)F.Y, s);
             } else {
                 // A: forward FFT of the children's rows, modes |m| <= Lc
-                int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - Ch.nph, 2 * Ch.nph);
-                sm = ((size_t)2 * RB * Ch.nph + Ch.nph) * sizeof(C);
+                int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - Ch.nph, 2 * (Ch.nph + 1));
+                sm = ((size_t)2 * RB * (Ch.nph + 1) + Ch.nph) * sizeof(C);
                 k_fft_fwd_rows<C, R><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, Fc, Lc, Ch.fft, (const C*)Ch.tw,
                                                                           (R)(1.0 / Ch.nph), RB, FastDiv::make(RB),
                                                                           (C*)F.X);
@@ -1150,8 +1167,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
             }
             // C: z-shift per mode, inverse FFT, xy-shift, sum over children
             const int pbudget = (int)(kParentSmemBytes / sizeof(C));
-            const int RT = balanced_rows(F.nth, tile_rows(F.nth, pbudget - F.nph, 8 * F.nph));
-            sm = ((size_t)8 * RT * F.nph + F.nph) * sizeof(C);
+            const int RT = balanced_rows(F.nth, tile_rows(F.nth, pbudget - F.nph, 8 * (F.nph + 1)));
+            sm = ((size_t)8 * RT * (F.nph + 1) + F.nph) * sizeof(C);
             k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(
                 T.child_begin, T.child_end, TC.key, (int)TC.nbox, (const C*)F.Y, Lc, F.nth, F.fft, (const C*)F.tw,
                 (const C*)F.Sz, (const C*)F.Sxy, RT, FastDiv::make(RT), FastDiv::make(F.nph), Fp);
@@ -1170,15 +1187,15 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         if (l > p.top) {
             FarLevel& Pf = p.far[l - 1];
             const int Lc = F.L;
-            const int CPB = fused_children(F.nth, F.nph, (2 * Lc + 1) * Pf.nth, sizeof(C));
+            const int CPB = fused_children(F.nth, F.nph, F.nph + 1, (2 * Lc + 1) * Pf.nth, 2 * Lc + 1, sizeof(C));
             StageTimer st(p, MLFMA_STAGE_L2L, l, NR * ((CPB ? 2 : 3) + (T.n_orphans > 0)));
             const int budget = (int)(kFftSmemBytes / sizeof(C));
             const int pbudget = (int)(kParentSmemBytes / sizeof(C));
-            const int RT = balanced_rows(Pf.nth, tile_rows(Pf.nth, pbudget - Pf.nph, 8 * Pf.nph));
+            const int RT = balanced_rows(Pf.nth, tile_rows(Pf.nth, pbudget - Pf.nph, 8 * (Pf.nph + 1)));
             for (int r = 0; r < NR; ++r) {
                 const C* Gp = (const C*)Pf.G + r * sF(l - 1);
                 C* Gc = (C*)F.G + r * sF(l);
-                size_t sm = ((size_t)8 * RT * Pf.nph + Pf.nph) * sizeof(C);
+                size_t sm = ((size_t)8 * RT * (Pf.nph + 1) + Pf.nph) * sizeof(C);
                 k_l2l_fft_in<C, R><<<dim3((unsigned)TP.nbox, nblk(Pf.nth, RT)), 128, sm, s>>>(
                     TP.child_begin, TP.child_end, T.key, (int)T.nbox, Gp, Lc, Pf.nth, Pf.fft, (const C*)Pf.tw,
                     (const C*)Pf.Sz, (const C*)Pf.Sxy, RT, FastDiv::make(RT), FastDiv::make(Pf.nph), (R)(1.0 / Pf.nph),
@@ -1197,8 +1214,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
                 } else {
                     launch_theta_map<R, C>(p, T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, (const C*)Pf.Y, (C*)Pf.X, s);
                     const int64_t rows_c = T.nbox * (int64_t)F.nth;
-                    int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * F.nph);
-                    sm = ((size_t)2 * RB * F.nph + F.nph) * sizeof(C);
+                    int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * (F.nph + 1));
+                    sm = ((size_t)2 * RB * (F.nph + 1) + F.nph) * sizeof(C);
                     k_l2l_fft_out<C><<<nblk(rows_c, RB), 128, sm, s>>>((int)rows_c, (const C*)Pf.X, Lc, F.fft,
                                                                         (const C*)F.tw, RB, FastDiv::make(RB), Gc);
                     MLFMA_LAUNCH_CHECK();

@@ -34,13 +34,14 @@ FftPlan make_fft_plan(int n) {
     FftPlan p;
     p.n = n;
     int m = n;
-    for (int r : {7, 5, 4, 3, 2})
+    for (int r : {7, 5, 3, 4, 2})   // odd radices first: their strided writes are conflict-free
         while (m % r == 0) {
             if (p.ns >= 16) fail(MLFMA_ERR_UNSUPPORTED, "FFT length %d has too many factors", n);
             p.r[p.ns++] = r;
             m /= r;
         }
     if (m != 1) fail(MLFMA_ERR_UNSUPPORTED, "FFT length %d is not 7-smooth", n);
+    p.dn = FastDiv::make((unsigned)n);
     int Ns = 1;
     for (int st = 0; st < p.ns; ++st) {
         p.Ns[st] = Ns;
