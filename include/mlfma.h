@@ -73,7 +73,9 @@ typedef struct mlfma_options {
                                      amplified by |T| at quarter-wavelength boxes grows with L and
                                      dominates the error) */
     void* stream;                 /* cudaStream_t for all work; NULL = the legacy default stream */
-    /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
+    /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree.
+       It must return 256-byte aligned device memory (the kernels stage operators by TMA and move
+       samples in 16-byte vectors); a misaligned block fails the call with MLFMA_ERR_INVALID_ARG. */
     void* (*alloc)(size_t bytes, void* stream, void* ctx);
     void (*free)(void* ptr, void* stream, void* ctx);
     void* alloc_ctx;

@@ -39,6 +39,10 @@ void* Allocator::get(size_t n) {
     if (alloc) {
         ptr = alloc(n, (void*)stream, ctx);
         if (!ptr) fail(MLFMA_ERR_OUT_OF_MEMORY, "allocator callback returned NULL for %zu bytes", n);
+        if ((uintptr_t)ptr & 255) {
+            if (free) free(ptr, (void*)stream, ctx);
+            fail(MLFMA_ERR_INVALID_ARG, "allocator callback returned %p, not 256-byte aligned", ptr);
+        }
     } else {
         cudaError_t e = cudaMalloc(&ptr, n);
         if (e != cudaSuccess) {
