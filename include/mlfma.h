@@ -260,6 +260,38 @@ mlfma_status mlfma_plan_timings(mlfma_plan* plan, mlfma_timings* out, int reset)
  */
 mlfma_status mlfma_apply_near_noalloc(mlfma_plan* plan, const void* q, void* phi);
 
+/* Outcome of mlfma_solve_gmres. */
+typedef struct {
+    int iterations;               /* Krylov steps taken (one matvec each) */
+    int restarts;                 /* cycles begun after the first */
+    int matvecs;                  /* applies of the plan, including one per cycle for the true residual */
+    int converged;                /* 1 when the true relative residual reached tol */
+    double rel_residual;          /* ||b - (sigma x + A x)||_2 / ||b||_2 at exit, from a fresh matvec */
+} mlfma_solve_info;
+
+/*
+ * Iterative solve around the matvec (Sec. 1: the potential evaluation is the kernel of
+ * an iterative integral-equation solver): restarted GMRES(restart) for
+ *     (sigma I + A) x = b,
+ * A the matrix the plan applies (no diagonal: pairs i = j contribute nothing) and
+ * sigma = sigma_re + i sigma_im a diagonal term.  Orthogonalisation is classical
+ * Gram-Schmidt applied twice per step on the device; the Hessenberg least-squares
+ * problem (Givens rotations) is solved on the host, one small device-to-host copy
+ * per step.  Each cycle starts from the true residual of a fresh matvec, and the
+ * returned rel_residual is recomputed that way at exit.
+ *   b  [n] complex (precision of the plan), DEVICE, caller order; not modified.
+ *   x  [n] complex, DEVICE: the initial guess on entry, the iterate on exit.
+ *   tol in (0, 1): stop when ||b - (sigma x + A x)|| <= tol ||b|| (the MLFMA's own
+ *       error, about 10^-digits, bounds what tol can be met).
+ *   restart in [1, 256]; max_iter >= 1 (Krylov steps over all cycles).
+ * Scratch: (restart + 2) n complex values from the plan's allocator, released before
+ * return.  Blocks until the solve ends.  Not converging is not an error (info->converged
+ * = 0).  b = 0 gives x = 0.  Errors: INVALID_ARG (null or host pointers, parameters out
+ * of range, non-finite sigma), OUT_OF_MEMORY, CUDA, TIMEOUT (as mlfma_apply).
+ */
+mlfma_status mlfma_solve_gmres(mlfma_plan* plan, const void* b, void* x, double sigma_re, double sigma_im,
+                               double tol, int restart, int max_iter, mlfma_solve_info* info);
+
 /* Releases all device memory of the plan after synchronising its stream.  NULL-safe. */
 void mlfma_destroy(mlfma_plan* plan);
 

@@ -59,6 +59,11 @@ class Timings(ctypes.Structure):
                 ("m2l_ms", ctypes.c_double * (MAX_LEVELS + 1)), ("applies", ctypes.c_int64)]
 
 
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("matvecs", ctypes.c_int),
+                ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+
+
 class MLFMAError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -108,6 +113,8 @@ def load(build_if_missing: bool = False):
     lib.mlfma_plan_timings.restype = ci
     lib.mlfma_apply_near_noalloc.argtypes = [vp, vp, vp]
     lib.mlfma_apply_near_noalloc.restype = ci
+    lib.mlfma_solve_gmres.argtypes = [vp, vp, vp, cd, cd, cd, ci, ci, ctypes.POINTER(SolveInfo)]
+    lib.mlfma_solve_gmres.restype = ci
     lib.mlfma_destroy.argtypes = [vp]
     lib.mlfma_destroy.restype = None
     lib.mlfma_last_error.argtypes = []
@@ -212,6 +219,14 @@ def mlfma_plan_timings(plan, reset=True) -> Timings:
 def mlfma_apply_near_noalloc(plan, q, phi):
     """Near-field part of A q into phi (device tensors), allocating nothing."""
     _check(load().mlfma_apply_near_noalloc(plan, _ptr(q), _ptr(phi)))
+
+
+def mlfma_solve_gmres(plan, b, x, sigma, tol, restart, max_iter) -> SolveInfo:
+    info = SolveInfo()
+    sigma = complex(sigma)
+    _check(load().mlfma_solve_gmres(plan, _ptr(b), _ptr(x), sigma.real, sigma.imag, float(tol), int(restart),
+                                    int(max_iter), ctypes.byref(info)))
+    return info
 
 
 def mlfma_destroy(plan):
@@ -327,6 +342,17 @@ class Plan:
         with self.torch.cuda.device(self.device):
             mlfma_apply_grad(self.handle, q, phi, grad, nrhs)
         return phi, grad
+
+    def solve(self, b, sigma=0.0, tol=1e-3, restart=30, max_iter=300, x0=None):
+        """x with (sigma I + A) x = b by restarted GMRES on the device; returns (x, info dict)."""
+        b = self._vec(b, "b")
+        if b.dim() != 1:
+            raise ValueError("solve takes one right-hand side [n]")
+        x = self.torch.zeros_like(b) if x0 is None else self._vec(x0, "x0").clone()
+        with self.torch.cuda.device(self.device):
+            i = mlfma_solve_gmres(self.handle, b, x, sigma, tol, restart, max_iter)
+        return x, dict(iterations=i.iterations, restarts=i.restarts, matvecs=i.matvecs, converged=bool(i.converged),
+                       rel_residual=i.rel_residual)
 
     def info(self) -> dict:
         i = mlfma_plan_info(self.handle)

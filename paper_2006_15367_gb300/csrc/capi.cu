@@ -262,6 +262,13 @@ static void apply_impl(Plan& P, const void* q, void* phi, int nrhs, bool adjoint
     if (!dphi || !dq) MLFMA_CUDA(cudaStreamSynchronize(P.stream));
 }
 
+void apply_device(Plan& P, const void* q) {
+    ensure_io_buffers(P, 1, false);
+    MLFMA_CUDA(cudaMemcpyAsync(P.qin, q, (size_t)P.ntot * csize(P), cudaMemcpyDeviceToDevice, P.stream));
+    run(P, 1, false, false);
+    if (P.profiling) P.acc.applies += 1;
+}
+
 static void init_streams(Plan& P, int nsub) {
     MLFMA_CUDA(cudaStreamCreateWithFlags(&P.gstream, cudaStreamNonBlocking));
     MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming));
@@ -482,6 +489,19 @@ mlfma_status mlfma_apply_grad(mlfma_plan* plan, const void* q, void* phi, void* 
         if (!plan) fail(MLFMA_ERR_INVALID_ARG, "null plan");
         if (!grad) fail(MLFMA_ERR_INVALID_ARG, "null grad");
         apply_impl(plan->p, q, phi, nrhs, false, grad);
+    });
+}
+
+mlfma_status mlfma_solve_gmres(mlfma_plan* plan, const void* b, void* x, double sigma_re, double sigma_im, double tol,
+                               int restart, int max_iter, mlfma_solve_info* info) {
+    return guarded([&] {
+        if (!plan || !b || !x || !info) fail(MLFMA_ERR_INVALID_ARG, "null plan, b, x or info");
+        if (!is_device_ptr(b) || !is_device_ptr(x)) fail(MLFMA_ERR_INVALID_ARG, "b and x must be device pointers");
+        if (!(tol > 0 && tol < 1)) fail(MLFMA_ERR_INVALID_ARG, "tol must be in (0, 1) (got %g)", tol);
+        if (restart < 1 || restart > 256) fail(MLFMA_ERR_INVALID_ARG, "restart must be in [1, 256] (got %d)", restart);
+        if (max_iter < 1) fail(MLFMA_ERR_INVALID_ARG, "max_iter must be >= 1 (got %d)", max_iter);
+        if (!std::isfinite(sigma_re) || !std::isfinite(sigma_im)) fail(MLFMA_ERR_INVALID_ARG, "sigma must be finite");
+        gmres_solve(plan->p, b, x, sigma_re, sigma_im, tol, restart, max_iter, info);
     });
 }
 

@@ -294,6 +294,11 @@ void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout,
 // nr right-hand sides per pass (1, or kMaxNR without gradients): q and phi r n apart
 void apply_pipeline(Plan& p, const void* qs_r, void* phis_r, void* grads_r, int nr);
 void far_apply(Plan& p, const void* qs, void* phis, void* grads, int nr);
+// one apply of a top-level plan on a device vector in caller order; the result stays in P.phiout
+void apply_device(Plan& P, const void* q);
+// restarted GMRES on (sigma I + A) x = b with the plan's matvec (solve.cu)
+void gmres_solve(Plan& P, const void* b, void* x, double sr, double si, double tol, int restart, int max_iter,
+                 mlfma_solve_info* info);
 // ld: row stride of the caller-order vectors (default n)
 void permute_out3(Plan& p, const void* gs, void* g, int nrhs, int64_t ld = -1);
 void permute_in(Plan& p, const void* q, void* qs, int nrhs, bool conj, int64_t ld = -1);
