@@ -19,7 +19,17 @@
 
 namespace mlfma {
 
-__device__ __forceinline__ void sc(float x, float& s, float& c) { sincosf(x, &s, &c); }
+// sin and cos of the leaf phases (C2M, L2O).  complex64: x is reduced to [-pi, pi] by a
+// two-constant Cody-Waite step, x - n 2pi with 2pi = hi + lo (hi the float nearest 2pi, lo
+// the remainder; the reduction adds less than 1.2e-7 for |x| <= 200, no more than the
+// rounding of x itself beyond), then the SFU approximations, whose documented absolute
+// error on [-pi, pi] is 2^-21.4.  complex128: the libm-accurate sincos.
+__device__ __forceinline__ void sc(float x, float& s, float& c) {
+    const float n = rintf(x * 0.159154936671257f);
+    float r = fmaf(-n, 6.28318548202514648f, x);
+    r = fmaf(-n, -1.74845553146952e-7f, r);
+    __sincosf(r, &s, &c);
+}
 __device__ __forceinline__ void sc(double x, double& s, double& c) { sincos(x, &s, &c); }
 
 static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -79,6 +89,7 @@ __global__ void __launch_bounds__(128) k_c2m(int64_t nleaf, const int* __restric
                 R x = sp[wl][t][0], y = sp[wl][t][1], z = sp[wl][t][2];
 #pragma unroll
                 for (int u = 0; u < kC2MPass; ++u) {
+                    if (p0 + 32 * u >= K) break;          // warp-uniform: no sample of this slot
                     R ph = d[u][0] * x + d[u][1] * y + d[u][2] * z;
                     R s, c;
                     sc(ph, s, c);
