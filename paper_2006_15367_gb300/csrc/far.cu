@@ -49,19 +49,30 @@ static inline int balanced_rows(int nrows, int rmax) {
 constexpr int kC2MPass = 4;   // samples per lane per pass
 
 // NR right-hand sides share each exponential: charges qs[r sn + j], signatures F[r sF + b K + p].
+// The leaf's points (at most kSmallLeaf) and charges are staged in shared memory once; each
+// pass then covers 32 kC2MPass samples with every point.
 template <typename R, typename C, int NR>
 __global__ void __launch_bounds__(128) k_c2m(int64_t nleaf, const int* __restrict__ leaf_box, const int* __restrict__ begin,
                                              const int* __restrict__ end, const double* __restrict__ center,
                                              const double* __restrict__ pos, const C* __restrict__ qs, int64_t sn,
                                              const R* __restrict__ dirs, int64_t K, R k, C* __restrict__ F, int64_t sF) {
-    __shared__ R sp[4][32][3];
-    __shared__ C sq[4][NR][32];
+    __shared__ R sp[4][kSmallLeaf][3];
+    __shared__ C sq[4][NR][kSmallLeaf];
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t w = (int64_t)blockIdx.x * 4 + wl;
     if (w >= nleaf) return;
     const int b = leaf_box[w];
-    const int b0 = begin[b], b1 = end[b];
+    const int b0 = begin[b], np = min(end[b] - b0, kSmallLeaf);
     const double cx = center[3 * b], cy = center[3 * b + 1], cz = center[3 * b + 2];
+    for (int t = lane; t < np; t += 32) {
+        const int64_t j = b0 + t;
+        sp[wl][t][0] = (R)(pos[3 * j] - cx);
+        sp[wl][t][1] = (R)(pos[3 * j + 1] - cy);
+        sp[wl][t][2] = (R)(pos[3 * j + 2] - cz);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) sq[wl][r][t] = qs[r * sn + j];
+    }
+    __syncwarp();
     C* Fb = F + (int64_t)b * K;
     for (int64_t p0 = 0; p0 < K; p0 += 32 * kC2MPass) {
         C acc[kC2MPass][NR];
@@ -74,31 +85,18 @@ __global__ void __launch_bounds__(128) k_c2m(int64_t nleaf, const int* __restric
             int64_t pp = p < K ? p : K - 1;
             d[u][0] = -k * dirs[4 * pp]; d[u][1] = -k * dirs[4 * pp + 1]; d[u][2] = -k * dirs[4 * pp + 2];
         }
-        for (int j0 = b0; j0 < b1; j0 += 32) {
-            int j = j0 + lane;
-            if (j < b1) {
-                sp[wl][lane][0] = (R)(pos[3 * (int64_t)j] - cx);
-                sp[wl][lane][1] = (R)(pos[3 * (int64_t)j + 1] - cy);
-                sp[wl][lane][2] = (R)(pos[3 * (int64_t)j + 2] - cz);
+        for (int t = 0; t < np; ++t) {
+            const R x = sp[wl][t][0], y = sp[wl][t][1], z = sp[wl][t][2];
 #pragma unroll
-                for (int r = 0; r < NR; ++r) sq[wl][r][lane] = qs[r * sn + j];
+            for (int u = 0; u < kC2MPass; ++u) {
+                if (p0 + 32 * u >= K) break;              // warp-uniform: no sample of this slot
+                R ph = d[u][0] * x + d[u][1] * y + d[u][2] * z;
+                R s, c;
+                sc(ph, s, c);
+                const C e = cmake<C>(c, s);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) cfma(acc[u][r], sq[wl][r][t], e);
             }
-            __syncwarp();
-            int cnt = min(32, b1 - j0);
-            for (int t = 0; t < cnt; ++t) {
-                R x = sp[wl][t][0], y = sp[wl][t][1], z = sp[wl][t][2];
-#pragma unroll
-                for (int u = 0; u < kC2MPass; ++u) {
-                    if (p0 + 32 * u >= K) break;          // warp-uniform: no sample of this slot
-                    R ph = d[u][0] * x + d[u][1] * y + d[u][2] * z;
-                    R s, c;
-                    sc(ph, s, c);
-                    const C e = cmake<C>(c, s);
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) cfma(acc[u][r], sq[wl][r][t], e);
-                }
-            }
-            __syncwarp();
         }
 #pragma unroll
         for (int u = 0; u < kC2MPass; ++u) {
