@@ -688,16 +688,19 @@ __device__ __forceinline__ int parent_quadrants(int c0, int c1, const uint64_t* 
     return *s_nq;
 }
 
+// items a thread of the per-parent kernels gathers at once (all loads issued before use)
+constexpr int kGatherBatch = 4;
+
 // M2M last step, per parent P and tile of RT parent rows i' (the present xy-quadrants q are
 // transformed together):
 //   W_q[i'][m] = sum_{children c = (q, sz)} Sz[sz][i'] Y[mi][c][i']          (z part of the shift, per mode)
 //   F_P[i'][j'] = sum_q Sxy[q][i'][j'] sum_m W_q[i'][m] e^{+i m phi'_j'}     (inverse FFT, xy part of the shift)
-// dRT divides by RT, dn by n.
+// dRT divides by RT, dqm by RT nm, dn by n.
 template <typename C>
 __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict__ ce, const uint64_t* __restrict__ ckey,
                               int nbox_c, const C* __restrict__ Y, int Lc, int nthp, FftPlan fp, const C* __restrict__ tw,
-                              const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, FastDiv dRT, FastDiv dn,
-                              C* __restrict__ Fp) {
+                              const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, FastDiv dRT, FastDiv dqm,
+                              FastDiv dn, C* __restrict__ Fp) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_child[4][2];
     __shared__ int s_q[4], s_nq;
@@ -716,19 +719,40 @@ __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict_
     const int nq = parent_quadrants(c0, c1, ckey, s_child, s_q, &s_nq);
     for (int idx = threadIdx.x; idx < nq * nr * pn; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
     __syncthreads();
-    // rows of the qi-th present quadrant occupy buf0[(qi * nr + r) * pn ...]
-    for (int qi = 0; qi < nq; ++qi) {
-        const int q = s_q[qi];
-        const int ca = s_child[q][0], cz = s_child[q][1];
-        for (int idx = threadIdx.x; idx < RT * nm; idx += blockDim.x) {
-            const int mi = (int)dRT.div((unsigned)idx), r = idx - mi * RT;
-            if (r >= nr) continue;
-            const C* Ym = Y + (int64_t)mi * nbox_c * nthp;
-            C w = cmake<C>(0, 0);
-            if (ca >= 0) cfma(w, Sz[i0 + r], Ym[(int64_t)ca * nthp + i0 + r]);
-            if (cz >= 0) cfma(w, Sz[nthp + i0 + r], Ym[(int64_t)cz * nthp + i0 + r]);
-            buf0[(qi * nr + r) * pn + wrap(mi - Lc, n)] = w;
+    // rows of the qi-th present quadrant occupy buf0[(qi * nr + r) * pn ...]; items (qi, mi, r)
+    // in one loop, kGatherBatch of them per thread with all their loads issued first
+    const int tot = nq * RT * nm;
+    for (int i0b = 0; i0b < tot; i0b += kGatherBatch * blockDim.x) {
+        C ya[kGatherBatch], yz[kGatherBatch];
+        int dst[kGatherBatch], rr[kGatherBatch];
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) {
+            const int idx = i0b + u * blockDim.x + threadIdx.x;
+            ya[u] = yz[u] = cmake<C>(0, 0);
+            dst[u] = -1;
+            rr[u] = 0;
+            if (idx < tot) {
+                const int qi = (int)dqm.div((unsigned)idx), rem = idx - qi * RT * nm;
+                const int mi = (int)dRT.div((unsigned)rem), r = rem - mi * RT;
+                if (r < nr) {
+                    const int q = s_q[qi];
+                    const int ca = s_child[q][0], cz = s_child[q][1];
+                    const C* Ym = Y + (int64_t)mi * nbox_c * nthp + i0 + r;
+                    if (ca >= 0) ya[u] = Ym[(int64_t)ca * nthp];
+                    if (cz >= 0) yz[u] = Ym[(int64_t)cz * nthp];
+                    dst[u] = (qi * nr + r) * pn + wrap(mi - Lc, n);
+                    rr[u] = r;
+                }
+            }
         }
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u)
+            if (dst[u] >= 0) {
+                C w = cmake<C>(0, 0);
+                cfma(w, Sz[i0 + rr[u]], ya[u]);
+                cfma(w, Sz[nthp + i0 + rr[u]], yz[u]);
+                buf0[dst[u]] = w;
+            }
     }
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true, pn);
@@ -804,14 +828,17 @@ __global__ void k_l2l_fft_out(int nrows_tot, const C* __restrict__ H, int Lc, Ff
     for (int idx = threadIdx.x; idx < nr * pn; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
     __syncthreads();
+    // the zero fill above is complete (barrier) before the copies overwrite the mode columns
     for (int idx = threadIdx.x; idx < RB * nm; idx += blockDim.x) {
         const int mi = (int)dRB.div((unsigned)idx), row = idx - mi * RB;
         if (row >= nr) continue;
-        buf0[row * pn + wrap(mi - Lc, n)] = H[(int64_t)mi * nrows_tot + r0 + row];
+        cp_async_zfill<sizeof(C)>(buf0 + row * pn + wrap(mi - Lc, n), H + (int64_t)mi * nrows_tot + r0 + row, true);
     }
+    cp_async_wait_all();
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nr, fp, stw, false, pn);
     C* g0 = G + (int64_t)r0 * n;
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
         const int row = (int)fp.dn.div((unsigned)idx), col = idx - row * n;
         g0[idx] = cadd(g0[idx], res[row * pn + col]);
@@ -1180,7 +1207,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
             sm = ((size_t)8 * RT * (F.nph + 1) + F.nph) * sizeof(C);
             k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(
                 T.child_begin, T.child_end, TC.key, (int)TC.nbox, (const C*)F.Y, Lc, F.nth, F.fft, (const C*)F.tw,
-                (const C*)F.Sz, (const C*)F.Sxy, RT, FastDiv::make(RT), FastDiv::make(F.nph), Fp);
+                (const C*)F.Sz, (const C*)F.Sxy, RT, FastDiv::make(RT), FastDiv::make(RT * (2 * Lc + 1)),
+                FastDiv::make(F.nph), Fp);
             MLFMA_LAUNCH_CHECK();
         }
     }
