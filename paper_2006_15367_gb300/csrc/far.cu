@@ -788,10 +788,16 @@ __global__ void k_l2l_fft_in(const int* __restrict__ cb, const int* __restrict__
     C* buf1 = buf0 + 4 * RT * pn;
     C* stw = buf1 + 4 * RT * pn;
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
+    // the tile G_P[i0 .. i0 + nr) is contiguous: stage it in buf1 (free until the transform),
+    // in flight while the quadrants are scanned
+    const C* gsrc = Gp + (int64_t)P * Kp + (int64_t)i0 * n;
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) cp_async_zfill<sizeof(C)>(buf1 + idx, gsrc + idx, true);
     const int nq = parent_quadrants(c0, c1, ckey, s_child, s_q, &s_nq);
+    cp_async_wait_all();
+    __syncthreads();
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
         const int64_t g = (int64_t)i0 * n + idx;
-        const C gv = Gp[(int64_t)P * Kp + g];
+        const C gv = buf1[idx];
         const int r = (int)dn.div((unsigned)idx), j = idx - r * n;
         for (int qi = 0; qi < nq; ++qi)
             buf0[(qi * nr + r) * pn + j] = cmul(cconj(Sxy[(int64_t)s_q[qi] * Kp + g]), gv);
