@@ -759,8 +759,9 @@ __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict_
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
         const int r = (int)dn.div((unsigned)idx), j = idx - r * n;
         C acc = cmake<C>(0, 0);
-        for (int qi = 0; qi < nq; ++qi)
-            cfma(acc, Sxy[(int64_t)s_q[qi] * Kp + (int64_t)(i0 + r) * n + j], res[(qi * nr + r) * pn + j]);
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi)                  // fixed bound: the loads issue together
+            if (qi < nq) cfma(acc, Sxy[(int64_t)s_q[qi] * Kp + (int64_t)(i0 + r) * n + j], res[(qi * nr + r) * pn + j]);
         Fp[(int64_t)P * Kp + (int64_t)i0 * n + idx] = acc;
     }
 }
@@ -799,8 +800,9 @@ __global__ void k_l2l_fft_in(const int* __restrict__ cb, const int* __restrict__
         const int64_t g = (int64_t)i0 * n + idx;
         const C gv = buf1[idx];
         const int r = (int)dn.div((unsigned)idx), j = idx - r * n;
-        for (int qi = 0; qi < nq; ++qi)
-            buf0[(qi * nr + r) * pn + j] = cmul(cconj(Sxy[(int64_t)s_q[qi] * Kp + g]), gv);
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi)
+            if (qi < nq) buf0[(qi * nr + r) * pn + j] = cmul(cconj(Sxy[(int64_t)s_q[qi] * Kp + g]), gv);
     }
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true, pn);
