@@ -350,7 +350,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename C, int NR, int NT>
 __device__ __forceinline__ void m2l_parent(int lane, int t0, const uint64_t* __restrict__ ckey,
                                            const unsigned long long* __restrict__ le, int ne, const C* Fp, int64_t sF,
-                                           const C* Tl, bool ok, int64_t K, int64_t p0, C* __restrict__ G) {
+                                           const C* Tl, bool ok, int64_t K, int64_t p0, C* __restrict__ G,
+                                           C* red) {
     int cr[NT];     // child part of the row index, times 32
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
@@ -383,11 +384,17 @@ __device__ __forceinline__ void m2l_parent(int lane, int t0, const uint64_t* __r
                 }
         }
     }
-    if (ok)
+    if (red) {                                    // a partial sum over part of the list
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) red[(t * NR + r) * 32 + lane] = acc[t][r];
+    } else if (ok) {
 #pragma unroll
         for (int t = 0; t < NT; ++t)
 #pragma unroll
             for (int r = 0; r < NR; ++r) G[r * sF + (int64_t)(t0 + t) * K + p0 + lane] = acc[t][r];
+    }
 }
 
 __device__ __forceinline__ bool m2l_bar_wait(uint32_t bar, uint32_t phase) {
@@ -409,14 +416,18 @@ __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __r
                                                    const int* __restrict__ loff, const unsigned long long* __restrict__ lsrc,
                                                    const uint64_t* __restrict__ ckey, const __grid_constant__ CUtensorMap tmT,
                                                    const C* __restrict__ F, int64_t K, int64_t sF, C* __restrict__ G,
-                                                   int* __restrict__ err) {
+                                                   int Q, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t tbar;
     // operator slice Ts[344][32] at a 128-byte boundary (TMA destination)
     C* Ts = reinterpret_cast<C*>(smem_raw + ((128 - ((uintptr_t)smem_raw & 127)) & 127));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t p0 = (int64_t)blockIdx.y * 32;
-    const int64_t P0 = (int64_t)blockIdx.x * (NW * kM2LParentsPerWarp);
+    // Q = 1: a warp takes kM2LParentsPerWarp parents in turn.  Q > 1 (levels with few, wide
+    // parents): Q warps share a parent, each summing a contiguous Q-th of its list into shared
+    // memory after the operator slice, and the first of them adds the Q partial sums.
+    const int PPC = Q > 1 ? NW / Q : NW * kM2LParentsPerWarp;    // parents per CTA
+    const int64_t P0 = (int64_t)blockIdx.x * PPC;
     // stage the slice with two TMA boxes of kTBoxRows rows (rows 343 and samples past K read as
     // zero) completing on one mbarrier
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&tbar);
@@ -447,17 +458,44 @@ __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __r
     const bool ok = p0 + lane < K;
     const C* Fp = F + (ok ? p0 + lane : K - 1);       // lane's sample; + (src * K) per source
     const C* Tl = Ts + lane;
-    for (int pw = 0; pw < kM2LParentsPerWarp; ++pw) {
-        const int64_t P = P0 + (int64_t)pw * NW + warp;
+    C* red = Q > 1 ? Ts + 2 * kTBoxRows * 32 + (size_t)warp * 8 * NR * 32 : nullptr;   // [warp][8][NR][32]
+    const int nround = Q > 1 ? 1 : kM2LParentsPerWarp;
+    for (int pw = 0; pw < nround; ++pw) {
+        const int64_t P = Q > 1 ? P0 + warp % PPC : P0 + (int64_t)pw * NW + warp;
         if (P >= npar) break;
         const int t0 = pcb[P], nt = pce[P] - t0;
-        const unsigned long long* le = lsrc + loff[P];
-        const int ne = loff[P + 1] - loff[P];
+        int e0 = loff[P], ne = loff[P + 1] - e0;
+        if (Q > 1) {
+            const int q = warp / PPC;
+            const int a = (int)((int64_t)ne * q / Q), b = (int)((int64_t)ne * (q + 1) / Q);
+            e0 += a;
+            ne = b - a;
+        }
+        const unsigned long long* le = lsrc + e0;
         switch (nt) {
-#define M2L_NT(n) case n: m2l_parent<C, NR, n>(lane, t0, ckey, le, ne, Fp, sF, Tl, ok, K, p0, G); break;
+#define M2L_NT(n) case n: m2l_parent<C, NR, n>(lane, t0, ckey, le, ne, Fp, sF, Tl, ok, K, p0, G, red); break;
             M2L_NT(1) M2L_NT(2) M2L_NT(3) M2L_NT(4) M2L_NT(5) M2L_NT(6) M2L_NT(7) M2L_NT(8)
 #undef M2L_NT
             default: break;
+        }
+    }
+    if (Q > 1) {
+        __syncthreads();
+        const int64_t P = P0 + warp;
+        if (warp < PPC && P < npar && ok) {
+            const int t0 = pcb[P], nt = pce[P] - t0;
+            const C* r0 = Ts + 2 * kTBoxRows * 32;
+            for (int t = 0; t < nt; ++t)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    C v = cmake<C>(0, 0);
+                    for (int q = 0; q < Q; ++q) {
+                        const C u = r0[(((size_t)(q * PPC + warp) * 8 + t) * NR + r) * 32 + lane];
+                        v.x += u.x;
+                        v.y += u.y;
+                    }
+                    G[r * sF + (int64_t)(t0 + t) * K + p0 + lane] = v;
+                }
         }
     }
 }
@@ -471,16 +509,27 @@ template <typename C, int NR> struct M2LShape {
 template <typename R, typename C>
 static size_t m2l_smem() { return (size_t)2 * kTBoxRows * 32 * sizeof(C) + 128; }
 
+// list split of a level (see k_m2l): complex64 levels with K >= 49152 samples (L >= 156: the
+// widest top levels, which hold few parents, so most warps of a CTA would idle and each
+// source load's latency would be exposed).  The rule depends on K alone, so a level splits
+// the same way in every plan that holds it (batched plans stay bit-identical to single ones).
+// On the 2^20-point sphere the 8-parent level 3 drops from 305 to 197 us; at the 56-parent
+// level 4 (K = 22050) the split was slower (157 -> 301 us: 7x the operator-slice loads).
+template <typename C, int NR>
+static int m2l_split(int64_t K) { return sizeof(C) == 8 && K >= 49152 ? 4 : 1; }
+
 template <typename R, typename C, int NR>
 static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
     constexpr int NW = M2LShape<C, NR>::NW;
     const FarLevel& F = p.far[l];
     const TreeLevel& T = p.lev[l];
     const TreeLevel& TP = p.lev[l - 1];
-    const dim3 grid(nblk(TP.nbox, NW * kM2LParentsPerWarp), nblk(F.K, 32));
-    k_m2l<R, C, NR, NW><<<grid, 32 * NW, m2l_smem<R, C>(), s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off,
-                                                                TP.m2l_src, T.key, F.tmT, (const C*)F.F, F.K,
-                                                                T.nbox * F.K, (C*)F.G, p.dev_err);
+    const int Q = m2l_split<C, NR>(F.K);
+    const int ppc = Q > 1 ? NW / Q : NW * kM2LParentsPerWarp;
+    const size_t sm = m2l_smem<R, C>() + (Q > 1 ? (size_t)NW * 8 * NR * 32 * sizeof(C) : 0);
+    const dim3 grid(nblk(TP.nbox, ppc), nblk(F.K, 32));
+    k_m2l<R, C, NR, NW><<<grid, 32 * NW, sm, s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off, TP.m2l_src, T.key,
+                                                  F.tmT, (const C*)F.F, F.K, T.nbox * F.K, (C*)F.G, Q, p.dev_err);
     MLFMA_LAUNCH_CHECK();
 }
 
