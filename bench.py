@@ -42,6 +42,17 @@ def _dist():
     return ws, rank, local
 
 
+def job_time_and_value(ms, points_per_rank, ws, dist=None, device="cpu"):
+    """Replicas: the step time is the slowest rank's (max over ranks) and the value is the
+    whole job's points per second, ws x points_per_rank / that time."""
+    if dist is not None and ws > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, points_per_rank * ws / (ms / 1e3)
+
+
 class Clocks:
     """Samples nvidia-smi clocks and throttle reasons while running."""
 
@@ -484,11 +495,7 @@ def main():
     if dist:
         dist.barrier()
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * nrhs * ws / (ms / 1e3)
+    ms, value = job_time_and_value(ms, n * nrhs, ws, dist, dev)
 
     # ---- per-stage times (CUDA events on the plan stream), same workload
     plan.profile(True)
