@@ -116,7 +116,9 @@ def peaks():
 
 
 def work_model(info):
-    """Algorithmic work per apply and per stage (roofline section)."""
+    """Algorithmic work per apply and per stage: M2L 8 flops per complex MAC over the V pairs,
+    unique bytes F read + G write + 316 K complex64 operators per level; M2M/L2L the complex MACs
+    of the dense per-mode formulation (phi DFT, theta map, inverse DFT per child)."""
     nl, top = info["nlev"], info["top"]
     cb = 8  # complex64 bytes
     m2l_flops = sum(8.0 * info["nv"][l] * info["K"][l] for l in range(top, nl + 1))

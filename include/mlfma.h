@@ -47,13 +47,13 @@ typedef enum {
     MLFMA_ERR_OUT_OF_MEMORY = 2,  /* a device allocation failed; nothing leaked */
     MLFMA_ERR_CUDA = 3,           /* a CUDA runtime call failed (message has the CUDA error) */
     MLFMA_ERR_TIMEOUT = 4,        /* a bounded device wait ran out */
-    MLFMA_ERR_UNSUPPORTED = 5     /* valid request outside what this build implements */
+    MLFMA_ERR_UNSUPPORTED = 5     /* valid request outside what this library implements */
 } mlfma_status;
 
 typedef enum {
     MLFMA_PREC_FP64 = 0,          /* complex128 data, FP64 arithmetic on every stage */
     MLFMA_PREC_FP32 = 1,          /* complex64 data, FP32 arithmetic; operators built in FP64 */
-    MLFMA_PREC_FP32_BF16X3 = 2,   /* reserved: split-BF16 tensor-core contractions (UNSUPPORTED in this build) */
+    MLFMA_PREC_FP32_BF16X3 = 2,   /* reserved: split-BF16 tensor-core contractions (not implemented: UNSUPPORTED) */
     MLFMA_PREC_FP32_TF32X3 = 3    /* as FP32, but the theta maps of the interpolation (Sec. 3.2.2) and
                                      anterpolation (Sec. 3.2.4) on level pairs too large to fuse run on
                                      the tensor cores as split-TF32 GEMMs (x = hi + lo, products hi*hi +

@@ -10,7 +10,9 @@ Sec. 3.2.3), L2L (shift -> anterpolate -> add, Sec. 3.2.4), L2O (Sec. 3.2.5),
 plus the near-field direct sums at the leaves (Sec. 2).  The paper omits the
 mathematics (Sec. 2 defers it to its references), so the formulas below are the
 standard diagonal plane-wave form derived from the Gegenbauer addition theorem
-and the Funk-Hecke identity (derivation in the design doc):
+(expanding e^{ik|X+d|}/|X+d| over spherical Bessel and Hankel functions) and the
+Funk-Hecke identity (replacing each j_n(k|d|) P_n by a quadrature of plane waves
+over the unit sphere):
 
   e^{ik|X+d|}/|X+d| ~= (ik/4pi) sum_p w_p e^{ik khat_p.d} T_X(khat_p),
   T_X(khat) = sum_{n=0}^{L} i^n (2n+1) h_n(k|X|) P_n(khat.Xhat)
@@ -21,7 +23,7 @@ and the Funk-Hecke identity (derivation in the design doc):
   L2L  G_c    += W_c^{-1} I^T W_P [e^{+ik khat.(c_c - c_P)} G_P]
   L2O  phi_i  += (ik/4pi) sum_p w_p e^{ik khat_p.(r_i - c_b)} G_b(p)
 
-Readings (listed in the design doc): kernel e^{+ikR}/R without 1/(4 pi), self term and
+Readings where the paper is silent: kernel e^{+ikR}/R without 1/(4 pi), self term and
 coincident points excluded; sampling grid = (L+1) Gauss-Legendre nodes in
 cos(theta) (ascending) x nph uniform phi nodes (nph = smallest even 7-smooth number
 >= 2L+2), sample p = i nph + j, weights w_p = w_i^GL 2pi/nph; global interpolation by spherical-harmonic
@@ -41,7 +43,7 @@ from . import tree as tr
 
 # d0 = digits + DIGIT_MARGIN in the truncation rule.  Calibrated once on the
 # 4,096-point sphere (radius 2, 3 digits) so that the relative L2 error against the
-# FP64 direct sum stays below 10^-digits, then frozen (see DESIGN.md).
+# FP64 direct sum stays below 10^-digits, then frozen.
 DIGIT_MARGIN = 1
 
 

@@ -14,7 +14,7 @@ Follows the paper's tree rules:
   edge or node; far (the V list) if they are not near but their parents are.
   Near-field sums happen only at the leaves.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 
 * root cube centred on the bounding-box centre; the uniform tree (leaf_max == 0)
   has leaf edge ``leaf_edge`` and root edge leaf_edge * 2^(L-1); the adaptive tree

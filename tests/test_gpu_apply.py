@@ -1,6 +1,6 @@
 """GPU MLFMA apply vs the oracle: every stage, the final potentials, and the API contract.
 
-Tolerances (derivation in the design doc):
+Tolerances:
 * FP64 path vs the FP64 oracle MLFMA (same grids, lists and operators): only
   summation order differs -> 1e-11 per stage and end to end.
 * FP32 path vs the oracle: rounding of complex64 data and operators, ~1e-7 per
