@@ -406,6 +406,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32x3"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--digits", type=int, default=0, help="override the workload's digits (0: keep)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the default interpolation tile budgets instead of the plan-time autotuner "
+                         "(--ncu always does: kernels outside the capture run slower under the profiler)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision / batching / adjoint form comparisons added to the JSON line")
     ap.add_argument("--mode", default="apply", choices=["apply", "grad"],
@@ -437,7 +440,7 @@ def main():
     qd = torch.as_tensor(Q.astype(cdt), device=dev)
     out = torch.empty_like(qd)
     plan = mf.Plan(ptd, prm["k"], prm["digits"], leaf_max=prm.get("leaf_max", 0), precision=args.precision,
-                   offsets=offsets)
+                   offsets=offsets, autotune=not (args.no_autotune or args.ncu))
     info = plan.info()
     stream = plan.stream
 
@@ -609,7 +612,8 @@ def main():
         "accuracy": {"rel_err_vs_fp64_direct": rel_err, "targets": int(sum(len(g[2]) for g in groups)),
                      "reference": "GPU FP64 direct sum"},
         "plan": {"levels": info["nlev"], "top": info["top"], "L": info["L"], "n_geom": info["n_geom"],
-                 "device_bytes": info["device_bytes"]},
+                 "device_bytes": info["device_bytes"], "autotune": not args.no_autotune,
+                 "tile_bytes": info["tile_bytes"]},
         "stage_ms": stage_ms, "setup_ms": info["setup_ms"], "m2l": m2l, "interp_rates": stages,
         "roofline": roof, "peaks_source": pk_kind, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,

@@ -81,6 +81,11 @@ typedef struct mlfma_options {
     void* alloc_ctx;
     int disable_graphs;           /* 0 (default): the apply sweep is captured once per (nrhs, kind) as a
                                      CUDA graph and replayed; 1: launch the kernels directly every time */
+    int autotune;                 /* 0 (default): the interpolation kernels use the shared-memory tile
+                                     budgets 20 / 32 / 40 KB (row tiles, per-parent tiles, fused level
+                                     pairs); 1: plan creation times four candidate budget sets on this
+                                     plan's own geometry (a few applies each, on a zero vector) and
+                                     keeps the fastest; mlfma_plan_info reports the choice */
 } mlfma_options;
 
 /* Summary of a plan (levels are numbered from the root, level 1). */
@@ -102,6 +107,8 @@ typedef struct mlfma_info {
     double setup_ms;                         /* wall time of mlfma_plan_create */
     int n_geom;                              /* geometries (1 unless created by mlfma_plan_create_batched;
                                                 per-level fields are then those of geometry 0) */
+    int tile_bytes[3];                       /* shared-memory budgets of the interpolation tiles in use:
+                                                row tiles, per-parent tiles, fused level pairs */
 } mlfma_info;
 
 /* Tree and list arrays that mlfma_plan_export can copy out (for verification). */

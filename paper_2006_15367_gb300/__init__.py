@@ -38,7 +38,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 class Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("precision", ctypes.c_int), ("leaf_edge", ctypes.c_double),
                 ("max_depth", ctypes.c_int), ("digit_margin", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("disable_graphs", ctypes.c_int)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("disable_graphs", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -48,7 +49,7 @@ class Info(ctypes.Structure):
                 ("nleaf", ctypes.c_int64 * (MAX_LEVELS + 1)), ("L", ctypes.c_int * (MAX_LEVELS + 1)),
                 ("K", ctypes.c_int64 * (MAX_LEVELS + 1)), ("nv", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("near_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
-                ("n_geom", ctypes.c_int)]
+                ("n_geom", ctypes.c_int), ("tile_bytes", ctypes.c_int * 3)]
 
 
 STAGES = ["PERMUTE", "P2P", "C2M", "M2M", "M2L", "L2L", "L2O"]
@@ -271,7 +272,7 @@ class Plan:
     """
 
     def __init__(self, points, k, digits=3, leaf_max=0, precision="fp32", leaf_edge=0.0, max_depth=12,
-                 digit_margin=-1, stream=None, use_torch_allocator=True, offsets=None, graphs=True):
+                 digit_margin=-1, stream=None, use_torch_allocator=True, offsets=None, graphs=True, autotune=False):
         import torch
         self.torch = torch
         load()
@@ -296,6 +297,7 @@ class Plan:
             o.digit_margin = int(digit_margin)
             o.stream = self.stream.cuda_stream
             o.disable_graphs = 0 if graphs else 1
+            o.autotune = 1 if autotune else 0
             self._alloc = None
             if use_torch_allocator:
                 self._alloc = _TorchAllocator(self.device)
@@ -361,7 +363,8 @@ class Plan:
                     root_edge=i.root_edge, root_corner=list(i.root_corner),
                     nbox=list(i.nbox[:nl + 1]), nleaf=list(i.nleaf[:nl + 1]), L=list(i.L[:nl + 1]),
                     K=list(i.K[:nl + 1]), nv=list(i.nv[:nl + 1]), near_pairs=i.near_pairs,
-                    device_bytes=i.device_bytes, setup_ms=i.setup_ms, n_geom=i.n_geom)
+                    device_bytes=i.device_bytes, setup_ms=i.setup_ms, n_geom=i.n_geom,
+                    tile_bytes=list(i.tile_bytes))
 
     def export(self, item, level=0):
         """Copies a tree/list/signature array to a host numpy array."""

@@ -269,6 +269,62 @@ void apply_device(Plan& P, const void* q) {
     if (P.profiling) P.acc.applies += 1;
 }
 
+// Plan-time choice of the interpolation tile budgets (row tiles, per-parent tiles, fused level
+// pairs).  Each candidate runs the apply sweep eagerly on a zero charge vector (the instruction
+// stream does not depend on the values): once to warm up, then three times timed by CUDA events
+// on the plan stream; the smallest median wins.  Captured graphs are dropped afterwards.
+static void set_tiles(Plan& P, const int* t) {
+    P.tile_fft = t[0];
+    P.tile_parent = t[1];
+    P.tile_fused = t[2];
+    for (Plan* sp : P.subs) set_tiles(*sp, t);
+}
+
+static void autotune_tiles(Plan& P) {
+    static const int cand[4][3] = {{20 << 10, 32 << 10, 40 << 10},
+                                   {16 << 10, 24 << 10, 32 << 10},
+                                   {32 << 10, 64 << 10, 64 << 10},
+                                   {12 << 10, 16 << 10, 24 << 10}};
+    ensure_io_buffers(P, 1, false);
+    MLFMA_CUDA(cudaMemsetAsync(P.qin, 0, (size_t)P.ntot * csize(P), P.stream));
+    cudaEvent_t a = nullptr, b = nullptr;
+    MLFMA_CUDA(cudaEventCreate(&a));
+    MLFMA_CUDA(cudaEventCreate(&b));
+    const bool graphs = P.use_graphs;
+    P.use_graphs = false;
+    int best = 0;
+    float best_ms = 0;
+    try {
+        for (int c = 0; c < 4; ++c) {
+            set_tiles(P, cand[c]);
+            run(P, 1, false, false);
+            float t[3];
+            for (int r = 0; r < 3; ++r) {
+                MLFMA_CUDA(cudaEventRecord(a, P.stream));
+                run(P, 1, false, false);
+                MLFMA_CUDA(cudaEventRecord(b, P.stream));
+                MLFMA_CUDA(cudaEventSynchronize(b));
+                MLFMA_CUDA(cudaEventElapsedTime(&t[r], a, b));
+            }
+            std::sort(t, t + 3);
+            if (c == 0 || t[1] < best_ms) {
+                best_ms = t[1];
+                best = c;
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        P.use_graphs = graphs;
+        throw;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    set_tiles(P, cand[best]);
+    P.use_graphs = graphs;
+    drop_graphs(P);
+}
+
 static void init_streams(Plan& P, int nsub) {
     MLFMA_CUDA(cudaStreamCreateWithFlags(&P.gstream, cudaStreamNonBlocking));
     MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming));
@@ -414,6 +470,7 @@ mlfma_status mlfma_plan_create(const double* points, int64_t n, double k, int di
             pts = d;
         }
         build_plan(p, pts);
+        if (o.autotune) autotune_tiles(p);
         p.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         *out = h;
     });
@@ -460,6 +517,7 @@ mlfma_status mlfma_plan_create_batched(const double* points, const int64_t* offs
             P.forest = true;
         }
         MLFMA_CUDA(cudaStreamSynchronize(P.stream));
+        if (o.autotune) autotune_tiles(P);
         P.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         *out = h;
     });
@@ -544,6 +602,9 @@ mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info) {
         info->near_pairs = p.near_pairs;
         info->device_bytes = (int64_t)p.mem.bytes;
         info->setup_ms = p.setup_ms;
+        info->tile_bytes[0] = p.tile_fft;
+        info->tile_bytes[1] = p.tile_parent;
+        info->tile_bytes[2] = p.tile_fused;
         info->n_geom = p.subs.empty() ? 1 : (int)p.subs.size();
         if (p.forest) {                                // the merged levels (height above the leaves)
             for (const Plan* sp : p.subs) info->device_bytes += (int64_t)sp->mem.bytes;

@@ -237,6 +237,10 @@ struct Plan {
     int64_t ntot = 0;              // points of the plan (sum over geometries for batched plans)
     // CUDA graphs of the apply sweep, keyed by nrhs * 4 + adjoint * 2 + grad
     bool use_graphs = true;
+    // shared-memory budgets (bytes) of the interpolation tiles: row-tile FFT kernels, per-parent
+    // kernels, fused level pairs; defaults from sweeps on a 2^20-point sphere, or chosen by the
+    // plan-time autotuner
+    int tile_fft = 20 * 1024, tile_parent = 32 * 1024, tile_fused = 40 * 1024;
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::map<int64_t, cudaGraphExec_t> graphs;

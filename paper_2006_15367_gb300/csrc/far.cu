@@ -679,11 +679,9 @@ __device__ C* fft_rows(C* buf0, C* buf1, int nrows, const FftPlan& fp, const C* 
 
 __device__ __forceinline__ int wrap(int m, int n) { return m < 0 ? m + n : m; }
 
-// shared-memory budget of one FFT CTA: small enough for several resident CTAs per SM
-constexpr size_t kFftSmemBytes = 20 * 1024;
-// the per-parent transforms (quadrant rows of one parent) take larger tiles: fewer row tiles
-// per parent, 5 CTAs of 128 threads per SM
-constexpr size_t kParentSmemBytes = 32 * 1024;
+// Shared-memory budgets of the interpolation tiles are plan fields: Plan::tile_fft for one
+// row-tile FFT CTA (20 KB by default: several resident CTAs per SM) and Plan::tile_parent for
+// the per-parent transforms (32 KB: quadrant rows of one parent in fewer row tiles).
 
 // M2M first step: X[mi][c][i] = scale sum_j F[c][i][j] e^{-i m phi_j}, |m| <= Lc, for the rows
 // r = c nth + i of all children (rows are contiguous in F; X is mode-major).  dRB divides by RB.
@@ -1030,10 +1028,11 @@ __global__ void k_zero_orphans(const int2* __restrict__ ranges, int nranges, int
 // children per CTA of the fused kernels, a power of two in [2, kMaxCPB] (0: the level pair
 // takes the three-kernel path); extra = complex elements per child staged besides the two
 // FFT buffers (rows of ``pitch`` elements), fixed = elements per CTA besides the twiddles
-constexpr size_t kFusedSmemBytes = 40 * 1024;
-static int fused_children(int nthc, int n, int pitch, int extra, int fixed, size_t csz) {
+// (budget: Plan::tile_fused, 40 KB by default)
+static int fused_children(size_t budget, int nthc, int n, int pitch, int extra, int fixed, size_t csz) {
     const size_t per = ((size_t)2 * nthc * pitch + extra) * csz;
-    const size_t avail = kFusedSmemBytes - (size_t)(n + fixed) * csz;
+    if (budget < (size_t)(n + fixed) * csz) return 0;
+    const size_t avail = budget - (size_t)(n + fixed) * csz;
     int c = 0;
     for (int t = 2; t <= kMaxCPB; t *= 2)
         if ((size_t)t * per <= avail) c = t;
@@ -1236,8 +1235,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         TreeLevel& TC = p.lev[l + 1];
         const int Lc = Ch.L;
         const int64_t rows_c = TC.nbox * (int64_t)Ch.nth;
-        const int budget = (int)(kFftSmemBytes / sizeof(C));
-        const int CPB = fused_children(Ch.nth, Ch.nph, Ch.nph, 0, 0, sizeof(C));
+        const int budget = (int)(p.tile_fft / sizeof(C));
+        const int CPB = fused_children(p.tile_fused, Ch.nth, Ch.nph, Ch.nph, 0, 0, sizeof(C));
         StageTimer st(p, MLFMA_STAGE_M2M, l, NR * (CPB ? 2 : 3));
         for (int r = 0; r < NR; ++r) {
             const C* Fc = (const C*)Ch.F + r * sF(l + 1);
@@ -1259,7 +1258,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
                 launch_theta_map<R, C>(p, TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, (const C*)F.X, (C*)F.Y, s);
             }
             // C: z-shift per mode, inverse FFT, xy-shift, sum over children
-            const int pbudget = (int)(kParentSmemBytes / sizeof(C));
+            const int pbudget = (int)(p.tile_parent / sizeof(C));
             const int RT = balanced_rows(F.nth, tile_rows(F.nth, pbudget - F.nph, 8 * (F.nph + 1)));
             sm = ((size_t)8 * RT * (F.nph + 1) + F.nph) * sizeof(C);
             k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(
@@ -1281,10 +1280,11 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         if (l > p.top) {
             FarLevel& Pf = p.far[l - 1];
             const int Lc = F.L;
-            const int CPB = fused_children(F.nth, F.nph, F.nph + 1, (2 * Lc + 1) * Pf.nth, 2 * Lc + 1, sizeof(C));
+            const int CPB =
+                fused_children(p.tile_fused, F.nth, F.nph, F.nph + 1, (2 * Lc + 1) * Pf.nth, 2 * Lc + 1, sizeof(C));
             StageTimer st(p, MLFMA_STAGE_L2L, l, NR * ((CPB ? 2 : 3) + (T.n_orphans > 0)));
-            const int budget = (int)(kFftSmemBytes / sizeof(C));
-            const int pbudget = (int)(kParentSmemBytes / sizeof(C));
+            const int budget = (int)(p.tile_fft / sizeof(C));
+            const int pbudget = (int)(p.tile_parent / sizeof(C));
             const int RT = balanced_rows(Pf.nth, tile_rows(Pf.nth, pbudget - Pf.nph, 8 * (Pf.nph + 1)));
             for (int r = 0; r < NR; ++r) {
                 const C* Gp = (const C*)Pf.G + r * sF(l - 1);
@@ -1361,6 +1361,15 @@ static void prepare_fft_kernels() {
     allow_max_smem(k_m2m_fft_out<C>);
     allow_max_smem(k_l2l_fft_in<C, R>);
     allow_max_smem(k_fft_fwd_rows<C, R>);
+    // fused level pairs: budgets above 48 KB (autotuner candidates) need the opt-in limit
+    allow_max_smem(k_m2m_in<C, R, 2>);
+    allow_max_smem(k_m2m_in<C, R, 4>);
+    allow_max_smem(k_m2m_in<C, R, 8>);
+    allow_max_smem(k_m2m_in<C, R, 16>);
+    allow_max_smem(k_l2l_out<C, R, 2>);
+    allow_max_smem(k_l2l_out<C, R, 4>);
+    allow_max_smem(k_l2l_out<C, R, 8>);
+    allow_max_smem(k_l2l_out<C, R, 16>);
     allow_max_smem(k_l2l_fft_out<C>);
     allow_max_smem(k_theta_map<R, C, 16>);
     allow_max_smem(k_theta_map<R, C, 32>);

@@ -266,3 +266,22 @@ def test_rhs_passes_batched_geometries():
         ref = direct.direct(pts[a:b], Q[4][a:b].astype(np.complex128), K)
         assert rel(batch[4][a:b], ref) < 1e-3
     plan.close()
+
+
+TILE_CANDIDATES = [[20480, 32768, 40960], [16384, 24576, 32768], [32768, 65536, 65536], [12288, 16384, 24576]]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_autotuned_tiles_keep_results(sphere4k, prec):
+    """The plan-time autotuner picks one of its candidate tile budgets; the potentials match the
+    default plan up to the summation order of the theta maps (a budget can move a level pair
+    between the fused kernels and the GEMM path)."""
+    pts, q, prm = sphere4k
+    plan0 = make_plan(pts, K, 3, prec)
+    plan1 = make_plan(pts, K, 3, prec, autotune=True)
+    assert plan0.info()["tile_bytes"] == TILE_CANDIDATES[0]
+    assert plan1.info()["tile_bytes"] in TILE_CANDIDATES
+    a = apply_plan(plan0, q[0], prec)
+    b = apply_plan(plan1, q[0], prec)
+    assert rel(b, a) < (1e-12 if prec == "fp64" else 1e-5)
+    assert rel(b, direct.direct(pts, q[0], K)) < 1e-3
