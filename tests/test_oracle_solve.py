@@ -53,3 +53,21 @@ def test_solution_residual_through_direct_sum():
         x = solve.solve_dense(pts, b, K, sigma)
         r = b - sigma * x - direct.direct(pts, x, K)
         assert np.linalg.norm(r) < 1e-11 * np.linalg.norm(b)
+
+
+def _kappa(pts, sigma):
+    A = solve.dense_matrix(pts, K)
+    A[np.diag_indices_from(A)] += sigma
+    sv = np.linalg.svd(A, compute_uv=False)
+    return sv[0] / sv[-1]
+
+
+def test_condition_numbers_behind_the_gpu_solve_bounds(sphere4k):
+    """The GPU GMRES tests bound ||x - x*|| / ||x*|| by kappa ||r|| / ||b|| with kappa <= 10 on
+    the 4,096-point sphere at sigma = 100i and kappa <= 25 on the three ellipsoid blocks of
+    the batched test; check both bounds against an SVD of the dense matrix."""
+    pts = sphere4k[0]
+    assert _kappa(pts, 100j) <= 10.0
+    geoms, sizes, _ = synth.ellipsoid_batch(3, seed=4101, nmin=800, nmax=2500, amin=0.8, amax=2.0)
+    for g in geoms:
+        assert _kappa(g, 100j) <= 25.0
