@@ -1,0 +1,20 @@
+"""Host logic of bench.py on CPU: the roofline traffic is read from the committed ncu summary only
+while the kernel sources hash to the value recorded there."""
+import bench
+
+
+def test_traffic_applies_to_the_committed_sources():
+    t = bench.measured_traffic("sphere1m", "fp32", 1, "apply")
+    assert t is not None and t["bytes_per_step"] > 1e9
+    assert t["source"] == "profiles/k_m2l_sphere1m.md"
+
+
+def test_traffic_is_none_for_other_workloads_and_changed_sources(monkeypatch, tmp_path):
+    assert bench.measured_traffic("sphere256k", "fp32", 1, "apply") is None
+    assert bench.measured_traffic("sphere1m", "fp64", 1, "apply") is None
+    assert bench.measured_traffic("sphere1m", "fp32", 4, "apply") is None
+    # a kernel source that differs from the profiled one: the summary no longer applies
+    changed = tmp_path / "far.cu"
+    changed.write_text("// changed\n")
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", (str(changed),))
+    assert bench.measured_traffic("sphere1m", "fp32", 1, "apply") is None
