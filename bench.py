@@ -169,6 +169,28 @@ def measured_traffic(workload, precision, nrhs, mode):
     return {"bytes_per_step": float(vals["dram_bytes_per_step"]), "source": "profiles/k_m2l_sphere1m.md"}
 
 
+def oracle_mlfma_rate():
+    """The oracle's plain FP64 MLFMA (numpy) on the 4,096-point sphere at 3 digits: points/s of
+    one apply (median of three after a warm-up; setup excluded), a CPU reference for the fast
+    algorithm beside the direct sum.  A failure is reported, not fatal."""
+    try:
+        import synth
+        from oracle import mlfma as om
+        pts, q, prm = synth.workload("sphere4k")
+        o = om.OracleMLFMA(pts, prm["k"], prm["digits"])
+        o.apply(q[0])
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            o.apply(q[0])
+            ts.append(time.perf_counter() - t0)
+        dt = float(np.median(ts))
+        return {"kind": "oracle MLFMA (numpy, FP64)", "workload": "sphere N=4096 r=2 wavelengths, 3 digits",
+                "value": pts.shape[0] / dt, "unit": "points/s", "apply_s": dt}
+    except Exception as e:                                # pragma: no cover - reported in the line
+        return {"error": f"{type(e).__name__}: {e}"[:200]}
+
+
 def run_reference(args, ws, rank):
     """CPU oracle: FP64 direct sum at a bounded sample of targets per step."""
     if rank != 0:
@@ -600,7 +622,8 @@ def main():
         cpu = {"value": ct.shape[0] / cdt_s, "unit": "points/s", "cores": direct.max_threads(), "kind": "oracle",
                "sample": f"FP64 direct sum (oracle, C/OpenMP) at {ct.shape[0]} sampled targets over all {b - a} "
                          f"sources of their geometry",
-               "rel_err_gpu_vs_oracle_direct": float(np.linalg.norm(o0h[ct] - cref) / np.linalg.norm(cref))}
+               "rel_err_gpu_vs_oracle_direct": float(np.linalg.norm(o0h[ct] - cref) / np.linalg.norm(cref)),
+               "oracle_mlfma": oracle_mlfma_rate()}
 
     cfg = config_dict(args, n, prm)
     line = {

@@ -18,3 +18,9 @@ def test_traffic_is_none_for_other_workloads_and_changed_sources(monkeypatch, tm
     changed.write_text("// changed\n")
     monkeypatch.setattr(bench, "KERNEL_SOURCES", (str(changed),))
     assert bench.measured_traffic("sphere1m", "fp32", 1, "apply") is None
+
+
+def test_oracle_mlfma_cpu_reference_runs():
+    r = bench.oracle_mlfma_rate()
+    assert "error" not in r, r
+    assert r["value"] > 0 and r["unit"] == "points/s" and r["apply_s"] > 0
