@@ -269,6 +269,13 @@ class Plan:
     k         wavenumber; digits: requested accuracy; leaf_max: 0 = level-uniform tree
     precision "fp32" (complex64 data), "fp64" (complex128 data) or "tf32x3" (complex64 data, theta
               maps of the large level pairs on the tensor cores as split-TF32 GEMMs)
+    offsets   concatenated geometries: offsets[g] .. offsets[g + 1] are geometry g's points (one
+              batched plan; the matrix is block diagonal)
+    graphs    replay the apply as a captured CUDA graph (default) or launch the kernels each time
+    autotune  time candidate interpolation tile budgets at creation and keep the fastest
+
+    Methods: apply (A q), adjoint (A^H r), apply_grad (A q and its gradient at the points),
+    solve ((sigma I + A) x = b by restarted GMRES), info, export, profile, timings, close.
     """
 
     def __init__(self, points, k, digits=3, leaf_max=0, precision="fp32", leaf_edge=0.0, max_depth=12,
