@@ -248,3 +248,27 @@ def test_sample_count_quadruples_per_level():
     ratios = [Ks[j + 1] / Ks[j] for j in range(len(Ks) - 1)]
     # the excess bandwidth O((kD)^(1/3)) makes the ratio approach 4 from below
     assert all(r > 1.5 for r in ratios) and ratios[-1] > ratios[0] and abs(ratios[-1] - 4.0) < 0.3
+
+
+def test_smooth_even_matches_enumerated_products():
+    """The phi-grid length rule: the smallest even 7-smooth number >= m, against the 7-smooth
+    numbers enumerated as products 2^a 3^b 5^c 7^d (not by trial division)."""
+    bound = 4096
+    smooth = set()
+    p2 = 1
+    while p2 <= bound:
+        p3 = p2
+        while p3 <= bound:
+            p5 = p3
+            while p5 <= bound:
+                p7 = p5
+                while p7 <= bound:
+                    smooth.add(p7)
+                    p7 *= 7
+                p5 *= 5
+            p3 *= 3
+        p2 *= 2
+    even = sorted(v for v in smooth if v % 2 == 0)
+    for m in range(1, 2000):
+        want = next(v for v in even if v >= m)
+        assert mlfma.smooth_even(m) == want, m
