@@ -272,3 +272,14 @@ def test_smooth_even_matches_enumerated_products():
     for m in range(1, 2000):
         want = next(v for v in even if v >= m)
         assert mlfma.smooth_even(m) == want, m
+
+
+def test_direct_pairs_matches_the_c_direct_sum():
+    """The oracle MLFMA's near-field block sum (numpy) against the C direct sum on the same set,
+    with a coincident pair that both must skip."""
+    pts = synth.sphere(300, 1.0, seed=31)
+    pts[5] = pts[9]
+    q = synth.complex_normal(32, 300)[0]
+    ref = direct.direct(pts, q, K)
+    got = mlfma.direct_pairs(pts, pts, q, K)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
