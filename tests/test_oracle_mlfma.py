@@ -283,3 +283,25 @@ def test_direct_pairs_matches_the_c_direct_sum():
     ref = direct.direct(pts, q, K)
     got = mlfma.direct_pairs(pts, pts, q, K)
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("L", [3, 8, 13, 20])
+def test_grid_quadrature_exact_and_antipodally_symmetric(L):
+    """The level grid integrates (a . khat)^n over the sphere exactly for n <= 2L + 1 (closed form
+    4 pi / (n + 1) for even n, 0 for odd n; any unit a), and is antipodally symmetric: -khat of
+    sample (i, j) is sample (L - i, j + nph / 2) with the same weight."""
+    g = mlfma.Grid(L)
+    assert np.allclose(np.linalg.norm(g.dirs, axis=1), 1.0, atol=1e-14)
+    rng = np.random.default_rng(L)
+    for _ in range(3):
+        a = rng.standard_normal(3)
+        a /= np.linalg.norm(a)
+        t = g.dirs @ a
+        for n in range(2 * L + 2):
+            want = 4.0 * math.pi / (n + 1) if n % 2 == 0 else 0.0
+            assert abs(np.sum(g.w * t ** n) - want) < 1e-12 * 4.0 * math.pi
+    i = np.arange(g.nth)[:, None]
+    j = np.arange(g.nph)[None, :]
+    anti = ((L - i) * g.nph + (j + g.nph // 2) % g.nph).reshape(-1)
+    assert np.allclose(g.dirs[anti], -g.dirs, atol=1e-14)
+    assert np.allclose(g.w[anti], g.w, rtol=1e-14)
