@@ -115,26 +115,32 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def work_model(info):
-    """Algorithmic work per apply and per stage: M2L 8 flops per complex MAC over the V pairs,
-    unique bytes F read + G write + 316 K complex64 operators per level; M2M/L2L the complex MACs
-    of the dense per-mode formulation (phi DFT, theta map, inverse DFT per child)."""
+def work_model(info, cb=8):
+    """Algorithmic work per apply and per stage (cb = bytes per complex number).
+
+    M2L: 8 flops per complex MAC over the V pairs; unique bytes = F read + G write per box and
+    sample + the 316 K operators of each level.  M2M: one read of every child signature F_c and
+    one write of every parent signature F_p per level pair; L2L: one read of every parent G_p and
+    a read-modify-write of every child G_c (the HBM bytes a fused interpolation must move)."""
     nl, top = info["nlev"], info["top"]
-    cb = 8  # complex64 bytes
     m2l_flops = sum(8.0 * info["nv"][l] * info["K"][l] for l in range(top, nl + 1))
     m2l_bytes = sum(info["nbox"][l] * info["K"][l] * 2 * cb + 316 * info["K"][l] * cb for l in range(top, nl + 1))
-    interp_flops = 0.0
+    m2m_bytes = l2l_bytes = 0.0
     for l in range(top, nl):
-        Lc, Lp = info["L"][l + 1], info["L"][l]
-        nc = info["nbox"][l + 1]
-        nthc, nphc, nthp, nphp, nm = Lc + 1, 2 * Lc + 2, Lp + 1, 2 * Lp + 2, 2 * Lc + 1
-        # dense phi-DFT on the children, real theta map per mode, inverse DFT per (parent, xy-pair)
-        dft_c = 8.0 * nc * nthc * nphc * nm
-        theta = 4.0 * nc * nm * nthc * nthp
-        inv_p = 8.0 * (nc / 2.0) * nthp * nphp * nm
-        interp_flops += dft_c + theta + inv_p
-    return {"M2L": {"flops": m2l_flops, "bytes": m2l_bytes}, "M2M": {"flops": interp_flops},
-            "L2L": {"flops": interp_flops}}
+        fc = info["nbox"][l + 1] * info["K"][l + 1] * cb
+        fp = info["nbox"][l] * info["K"][l] * cb
+        m2m_bytes += fc + fp
+        l2l_bytes += fp + 2 * fc
+    return {"M2L": {"flops": m2l_flops, "bytes": m2l_bytes}, "M2M": {"bytes": m2m_bytes},
+            "L2L": {"bytes": l2l_bytes}}
+
+
+def fp32_alu_peak(dev, sm_mhz):
+    """FP32 FMA peak derived from the device: SMs (read at run time) x 128 FP32 lanes per SM
+    (Blackwell) x 2 flops x the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, sms
 
 
 KERNEL_SOURCES = ("paper_2006_15367_gb300/csrc/far.cu", "paper_2006_15367_gb300/csrc/common.cuh")
@@ -169,24 +175,24 @@ def measured_traffic(workload, precision, nrhs, mode):
     return {"bytes_per_step": float(vals["dram_bytes_per_step"]), "source": "profiles/k_m2l_sphere1m.md"}
 
 
-def oracle_mlfma_rate():
-    """The oracle's plain FP64 MLFMA (numpy) on the 4,096-point sphere at 3 digits: points/s of
-    one apply (median of three after a warm-up; setup excluded), a CPU reference for the fast
-    algorithm beside the direct sum.  A failure is reported, not fatal."""
+def oracle_mlfma_rate(name="sphere256k"):
+    """The oracle's plain FP64 MLFMA (numpy) on a sphere of the bench workload's family (same point
+    density, quarter-wavelength leaves, 3 digits; 2^18 points on radius 16 by default): points/s
+    of one apply (setup excluded), the CPU rate of the same fast algorithm beside the direct sum.
+    A failure is reported, not fatal."""
     try:
         import synth
         from oracle import mlfma as om
-        pts, q, prm = synth.workload("sphere4k")
+        pts, q, prm = synth.workload(name)
+        t0 = time.perf_counter()
         o = om.OracleMLFMA(pts, prm["k"], prm["digits"])
+        setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
         o.apply(q[0])
-        ts = []
-        for _ in range(3):
-            t0 = time.perf_counter()
-            o.apply(q[0])
-            ts.append(time.perf_counter() - t0)
-        dt = float(np.median(ts))
-        return {"kind": "oracle MLFMA (numpy, FP64)", "workload": "sphere N=4096 r=2 wavelengths, 3 digits",
-                "value": pts.shape[0] / dt, "unit": "points/s", "apply_s": dt}
+        dt = time.perf_counter() - t0
+        return {"kind": "oracle MLFMA (numpy, FP64)", "workload": WORKLOADS[name], "n": int(pts.shape[0]),
+                "value": pts.shape[0] / dt, "unit": "points/s", "apply_s": dt, "setup_s": setup,
+                "cores": os.cpu_count(), "threads": "numpy: BLAS calls may use every core, the stage loops one"}
     except Exception as e:                                # pragma: no cover - reported in the line
         return {"error": f"{type(e).__name__}: {e}"[:200]}
 
@@ -586,14 +592,15 @@ def main():
     # ---- roofline of the dominant kernel: k_m2l (one launch per far level, timed by the M2L stage events)
     pk, pk_kind = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
+    fp32_peak, nsm = fp32_alu_peak(dev, sm_max)               # TFLOP/s, FMA = 2 flops
     roof = {"kernel": "k_m2l", "bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s", "achieved": None, "frac": None,
             "traffic": None,
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (clock from MEASURED_PEAKS.json)"}
+            "peak_source": f"derived: {nsm} SMs (device query) x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz "
+                           f"(maximum SM clock from MEASURED_PEAKS.json)"}
     m2l = None
     stages = None
     if offsets is None and info["top"]:
-        wm = work_model(info)
+        wm = work_model(info, 16 if args.precision == "fp64" else 8)
         reps = nrhs * (2 if args.mode == "grad" else 1)
         nl = info["nlev"] - info["top"] + 1
         ach = wm["M2L"]["flops"] * reps / (stage_ms["M2L"] / 1e3) / 1e12
@@ -606,8 +613,13 @@ def main():
         m2l = {"ms": stage_ms["M2L"], "flops": wm["M2L"]["flops"] * reps, "unique_bytes": wm["M2L"]["bytes"] * reps,
                "tflops": ach,
                "hbm_frac_unique_bytes": wm["M2L"]["bytes"] * reps / (stage_ms["M2L"] / 1e3) / 1e9 / pk["hbm_gbs"]}
-        stages = {s: {"ms": stage_ms[s], "dense_equiv_tflops": wm[s]["flops"] * reps / (stage_ms[s] / 1e3) / 1e12}
-                  for s in ("M2M", "L2L")}
+        stages = {}
+        for s in ("M2M", "L2L"):
+            b = wm[s]["bytes"] * reps
+            gbs = b / (stage_ms[s] / 1e3) / 1e9
+            stages[s] = {"ms": stage_ms[s], "algorithmic_bytes": b, "achieved_gbs": gbs,
+                         "hbm_frac": gbs / pk["hbm_gbs"],
+                         "bytes_model": "M2M: F_c read + F_p write; L2L: G_p read + G_c read and write (per level pair)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -27,6 +27,12 @@
  *     creation and never keeps a caller pointer.
  *   - Errors are returned as mlfma_status; nothing aborts or traps.  A
  *     thread-local message is available from mlfma_last_error().
+ *   - Every device wait of a kernel (a copy or a tensor-core MMA to complete) is
+ *     bounded; a kernel whose wait runs out raises the plan's error flag and returns.
+ *     Calls that synchronise the plan stream (applies with host pointers,
+ *     mlfma_apply_vjp, mlfma_solve_gmres, mlfma_plan_info, mlfma_plan_export,
+ *     mlfma_plan_timings) report a raised flag as MLFMA_ERR_TIMEOUT once and clear it;
+ *     an asynchronous apply's timeout is reported by the next such call.
  *   - A plan is not thread-safe: calls on one plan must not overlap.
  */
 #ifndef MLFMA_H
@@ -86,6 +92,18 @@ typedef struct mlfma_options {
                                      pairs); 1: plan creation times four candidate budget sets on this
                                      plan's own geometry (a few applies each, on a zero vector) and
                                      keeps the fastest; mlfma_plan_info reports the choice */
+    int recompute_signatures;     /* reverse mode (mlfma_apply_vjp).  0 (default): a differentiable
+                                     forward pass keeps grad phi of its charges (3 n complex values per
+                                     right-hand side, from mlfma_apply_grad) for the backward pass;
+                                     1: it keeps nothing (plain mlfma_apply) and mlfma_apply_vjp
+                                     recomputes grad phi with one more gradient sweep.  The library
+                                     reports the choice in mlfma_info; wrappers follow it */
+    int test_fail_waits;          /* test hook, 0 (default) in normal use.  1: every bounded device
+                                     wait of the apply (the M2L operator-slice copy, the tensor-core
+                                     MMA completion) gives up at its first poll; the kernel then waits
+                                     for its own copies in flight with the normal limit, raises the
+                                     plan's error flag and returns, so MLFMA_ERR_TIMEOUT can be
+                                     exercised without a stalled GPU */
 } mlfma_options;
 
 /* Summary of a plan (levels are numbered from the root, level 1). */
@@ -109,6 +127,7 @@ typedef struct mlfma_info {
                                                 per-level fields are then those of geometry 0) */
     int tile_bytes[3];                       /* shared-memory budgets of the interpolation tiles in use:
                                                 row tiles, per-parent tiles, fused level pairs */
+    int recompute_signatures;                /* the plan's mlfma_options.recompute_signatures */
 } mlfma_info;
 
 /* Tree and list arrays that mlfma_plan_export can copy out (for verification). */
@@ -211,6 +230,31 @@ mlfma_status mlfma_apply_adjoint(mlfma_plan* plan, const void* r, void* g, int n
  * Errors: INVALID_ARG (null plan/q/grad, host pointers, nrhs < 1), CUDA.
  */
 mlfma_status mlfma_apply_grad(mlfma_plan* plan, const void* q, void* phi, void* grad, int nrhs);
+
+/*
+ * Reverse mode of phi = A(r) q (Sec. 2, Eq. (1)): given the upstream gradient g of a real
+ * loss L with respect to phi, the gradients of L with respect to the charges and the
+ * positions.  Complex gradients follow PyTorch's convention, g = dL/dRe(phi) + i dL/dIm(phi).
+ * A is complex symmetric, so with psi = A conj(g):
+ *     grad_q   = dL/dRe(q) + i dL/dIm(q) = A^H g = conj(psi)
+ *     grad_r_i = dL/dr_i = sum over right-hand sides of Re[conj(g_i) grad phi_i + q_i grad psi_i]
+ * where grad phi_i and grad psi_i are gradients with respect to the target position r_i: the
+ * first term is r_i's role as a target of phi_i, the second its role as a source of every other
+ * phi_j (the kernel is symmetric, so those derivatives sum to the target gradient of psi).  One
+ * gradient sweep computes psi and grad psi (the conjugations are folded into the permutation
+ * kernels) and one kernel forms grad_r; with gphi = NULL a second gradient sweep recomputes
+ * grad phi first.
+ *   q       [nrhs][n] complex, device: the forward charges
+ *   g       [nrhs][n] complex, device: upstream gradient
+ *   gphi    [nrhs][n][3] complex, device, from mlfma_apply_grad on q; NULL = recompute
+ *   grad_q  [nrhs][n] complex, device, or NULL (not wanted)
+ *   grad_r  [n][3] FP64, device, or NULL (not wanted); summed over the right-hand sides
+ * Scratch: plan-owned buffers (grown on first use, kept).  Synchronises the plan stream.
+ * Errors: INVALID_ARG (null plan/q/g, host pointers, nrhs < 1, both outputs NULL), CUDA,
+ * OUT_OF_MEMORY, TIMEOUT.
+ */
+mlfma_status mlfma_apply_vjp(mlfma_plan* plan, const void* q, const void* g, const void* gphi, void* grad_q,
+                             double* grad_r, int nrhs);
 
 /* Fills *info.  INVALID_ARG on null pointers. */
 mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info);

@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("precision", ctypes.c_int), ("leaf_edge", ctypes.c_double),
                 ("max_depth", ctypes.c_int), ("digit_margin", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("disable_graphs", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("recompute_signatures", ctypes.c_int), ("test_fail_waits", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -49,7 +49,7 @@ class Info(ctypes.Structure):
                 ("nleaf", ctypes.c_int64 * (MAX_LEVELS + 1)), ("L", ctypes.c_int * (MAX_LEVELS + 1)),
                 ("K", ctypes.c_int64 * (MAX_LEVELS + 1)), ("nv", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("near_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
-                ("n_geom", ctypes.c_int), ("tile_bytes", ctypes.c_int * 3)]
+                ("n_geom", ctypes.c_int), ("tile_bytes", ctypes.c_int * 3), ("recompute_signatures", ctypes.c_int)]
 
 
 STAGES = ["PERMUTE", "P2P", "C2M", "M2M", "M2L", "L2L", "L2O"]
@@ -102,6 +102,8 @@ def load(build_if_missing: bool = False):
     lib.mlfma_apply_adjoint.restype = ci
     lib.mlfma_apply_grad.argtypes = [vp, vp, vp, vp, ci]
     lib.mlfma_apply_grad.restype = ci
+    lib.mlfma_apply_vjp.argtypes = [vp, vp, vp, vp, vp, vp, ci]
+    lib.mlfma_apply_vjp.restype = ci
     lib.mlfma_plan_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.mlfma_plan_info.restype = ci
     lib.mlfma_plan_export.argtypes = [vp, ci, ci, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
@@ -184,6 +186,10 @@ def mlfma_apply_adjoint(plan, r, g, nrhs):
 
 def mlfma_apply_grad(plan, q, phi, grad, nrhs):
     _check(load().mlfma_apply_grad(plan, _ptr(q), _ptr(phi), _ptr(grad), int(nrhs)))
+
+
+def mlfma_apply_vjp(plan, q, g, gphi, grad_q, grad_r, nrhs):
+    _check(load().mlfma_apply_vjp(plan, _ptr(q), _ptr(g), _ptr(gphi), _ptr(grad_q), _ptr(grad_r), int(nrhs)))
 
 
 def mlfma_plan_info(plan) -> Info:
@@ -273,13 +279,20 @@ class Plan:
               batched plan; the matrix is block diagonal)
     graphs    replay the apply as a captured CUDA graph (default) or launch the kernels each time
     autotune  time candidate interpolation tile budgets at creation and keep the fastest
+    recompute_signatures  reverse mode: False keeps grad phi of the forward charges for the backward
+              pass, True recomputes it there (mlfma_options.recompute_signatures)
+    test_fail_waits  test hook: every bounded device wait gives up at once (MLFMA_ERR_TIMEOUT path)
+    allocator a custom (alloc, free) pair of ctypes callbacks (ALLOC_FN, FREE_FN) instead of
+              PyTorch's caching allocator
 
     Methods: apply (A q), adjoint (A^H r), apply_grad (A q and its gradient at the points),
-    solve ((sigma I + A) x = b by restarted GMRES), info, export, profile, timings, close.
+    vjp (reverse mode of the matvec), solve ((sigma I + A) x = b by restarted GMRES), info, export,
+    profile, timings, close.
     """
 
     def __init__(self, points, k, digits=3, leaf_max=0, precision="fp32", leaf_edge=0.0, max_depth=12,
-                 digit_margin=-1, stream=None, use_torch_allocator=True, offsets=None, graphs=True, autotune=False):
+                 digit_margin=-1, stream=None, use_torch_allocator=True, offsets=None, graphs=True, autotune=False,
+                 recompute_signatures=False, test_fail_waits=False, allocator=None):
         import torch
         self.torch = torch
         load()
@@ -305,8 +318,13 @@ class Plan:
             o.stream = self.stream.cuda_stream
             o.disable_graphs = 0 if graphs else 1
             o.autotune = 1 if autotune else 0
+            o.recompute_signatures = 1 if recompute_signatures else 0
+            o.test_fail_waits = 1 if test_fail_waits else 0
             self._alloc = None
-            if use_torch_allocator:
+            if allocator is not None:
+                self._alloc = allocator
+                o.alloc, o.free = allocator
+            elif use_torch_allocator:
                 self._alloc = _TorchAllocator(self.device)
                 o.alloc = self._alloc.alloc
                 o.free = self._alloc.free
@@ -318,6 +336,7 @@ class Plan:
                     raise ValueError("offsets[-1] must equal the number of points")
                 self.handle = mlfma_plan_create_batched(pts, off, off.shape[0] - 1, self.k, digits, leaf_max, o)
         self._points = pts
+        self.recompute_signatures = bool(recompute_signatures)
 
     def _vec(self, x, name):
         t = self.torch
@@ -352,6 +371,25 @@ class Plan:
             mlfma_apply_grad(self.handle, q, phi, grad, nrhs)
         return phi, grad
 
+    def vjp(self, q, g, gphi=None, want_q=True, want_r=True):
+        """Reverse mode of phi = A(r) q: (grad_q, grad_r) for the upstream gradient g (PyTorch's
+        convention); gphi = grad phi of q from apply_grad, or None to recompute it."""
+        t = self.torch
+        q = self._vec(q, "q")
+        g = self._vec(g, "g")
+        nrhs = 1 if q.dim() == 1 else q.shape[0]
+        if g.shape != q.shape:
+            raise ValueError("g must have the shape of q")
+        if gphi is not None:
+            gphi = gphi.contiguous()
+            if tuple(gphi.shape) != tuple(q.shape) + (3,) or gphi.dtype != self.cdtype:
+                raise ValueError("gphi must be [..., n, 3] of the plan's complex type")
+        gq = t.empty_like(q) if want_q else None
+        gr = t.empty((self.n, 3), dtype=t.float64, device=q.device) if want_r else None
+        with t.cuda.device(self.device):
+            mlfma_apply_vjp(self.handle, q, g, gphi, gq, gr, nrhs)
+        return gq, gr
+
     def solve(self, b, sigma=0.0, tol=1e-3, restart=30, max_iter=300, x0=None):
         """x with (sigma I + A) x = b by restarted GMRES on the device; returns (x, info dict)."""
         b = self._vec(b, "b")
@@ -371,7 +409,7 @@ class Plan:
                     nbox=list(i.nbox[:nl + 1]), nleaf=list(i.nleaf[:nl + 1]), L=list(i.L[:nl + 1]),
                     K=list(i.K[:nl + 1]), nv=list(i.nv[:nl + 1]), near_pairs=i.near_pairs,
                     device_bytes=i.device_bytes, setup_ms=i.setup_ms, n_geom=i.n_geom,
-                    tile_bytes=list(i.tile_bytes))
+                    tile_bytes=list(i.tile_bytes), recompute_signatures=bool(i.recompute_signatures))
 
     def export(self, item, level=0):
         """Copies a tree/list/signature array to a host numpy array."""
@@ -431,20 +469,22 @@ def _function():
     class MLFMAFunction(torch.autograd.Function):
         """phi = A(r) q with gradients for the complex charges q and the positions r.
 
-        backward (PyTorch's convention, g = grad_output):
-          q.grad = A^H g = conj(A conj(g)) = conj(psi),  psi = A conj(g)
-          r.grad = Re[conj(g) * grad phi + q * grad psi]   (per point, 3 components)
-        where grad phi and grad psi are the target-position gradients from
-        mlfma_apply_grad; the tree of the plan is kept fixed.
+        forward: mlfma_apply_grad (phi and grad phi, kept for the backward pass) or, for plans
+        created with recompute_signatures, mlfma_apply (grad phi is recomputed in the backward).
+        backward: mlfma_apply_vjp with the upstream gradient (PyTorch's convention), which forms
+        q.grad = A^H g and r.grad = Re[conj(g) grad phi + q grad psi], psi = A conj(g), in the
+        library's kernels.  The tree of the plan is kept fixed.
         """
 
         @staticmethod
         def forward(ctx, q, points, plan):
-            if points is not None and points.requires_grad:
+            keep = points is not None and points.requires_grad and not plan.recompute_signatures
+            if keep:
                 phi, gphi = plan.apply_grad(q)
             else:
                 phi, gphi = plan.apply(q), None
             ctx.plan = plan
+            ctx.rdtype = points.dtype if points is not None else None
             ctx.has_gphi = gphi is not None
             ctx.save_for_backward(q, gphi if gphi is not None else q.new_zeros(0))
             return phi
@@ -452,19 +492,13 @@ def _function():
         @staticmethod
         def backward(ctx, g):
             q, gphi = ctx.saved_tensors
-            plan = ctx.plan
-            cg = torch.conj_physical(g.to(q.dtype)).contiguous()
-            want_r = ctx.needs_input_grad[1]
-            if want_r:
-                psi, gpsi = plan.apply_grad(cg)
-            else:
-                psi, gpsi = plan.apply(cg), None
-            grad_q = torch.conj(psi) if ctx.needs_input_grad[0] else None
-            grad_r = None
-            if want_r:
-                t = torch.conj(g).to(q.dtype)[..., None] * gphi + q[..., None] * gpsi
-                grad_r = t.real.to(torch.float64)
-            return grad_q, grad_r, None
+            want_q, want_r = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+            if not (want_q or want_r):
+                return None, None, None
+            gq, gr = ctx.plan.vjp(q, g.contiguous(), gphi if ctx.has_gphi else None, want_q=want_q, want_r=want_r)
+            if gr is not None and gr.dtype != ctx.rdtype:
+                gr = gr.to(ctx.rdtype)              # the positions' own dtype (the library writes FP64)
+            return gq, gr, None
 
     return MLFMAFunction
 

@@ -2,6 +2,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -79,6 +80,8 @@ void Allocator::release_all() {
 
 size_t csize(const Plan& p) { return p.prec == MLFMA_PREC_FP64 ? 16 : 8; }
 
+// A pointer the current device's kernels can dereference: managed memory, or device memory of
+// the current device (another GPU's memory would need peer access; such pointers are refused).
 static bool is_device_ptr(const void* ptr) {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, ptr);
@@ -86,7 +89,13 @@ static bool is_device_ptr(const void* ptr) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type != cudaMemoryTypeDevice) return false;
+    int dev = 0;
+    MLFMA_CUDA(cudaGetDevice(&dev));
+    if (a.device != dev)
+        fail(MLFMA_ERR_INVALID_ARG, "pointer %p is memory of device %d, not of the current device %d", ptr, a.device, dev);
+    return true;
 }
 
 static void drop_graphs(Plan& p) {
@@ -245,6 +254,26 @@ static void run(Plan& P, int nrhs, bool adjoint, bool grad) {
     MLFMA_CUDA(cudaStreamWaitEvent(P.stream, P.ev_join, 0));
 }
 
+// Error flags raised by kernels that gave up a bounded wait (this plan and its sub-plans):
+// synchronises the streams, reports a raised flag as MLFMA_ERR_TIMEOUT and clears it.
+// Flag values: 1 = a tensor-core MMA did not complete, 2 = the M2L operator-slice copy did not land.
+static void check_device_errors(const Plan& p) {
+    auto one = [](const Plan& q) {
+        if (!q.dev_err) return;
+        int e = 0;
+        MLFMA_CUDA(cudaStreamSynchronize(q.stream));
+        MLFMA_CUDA(cudaMemcpy(&e, q.dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            MLFMA_CUDA(cudaMemset(q.dev_err, 0, sizeof(int)));
+            fail(MLFMA_ERR_TIMEOUT, "a bounded device wait ran out (%s)",
+                 e == 1 ? "tensor-core MMA completion" : e == 2 ? "M2L operator-slice copy" : "unknown wait");
+        }
+    };
+    one(p);
+    if (p.gstream) MLFMA_CUDA(cudaStreamSynchronize(p.gstream));
+    for (const Plan* sp : p.subs) one(*sp);
+}
+
 static void apply_impl(Plan& P, const void* q, void* phi, int nrhs, bool adjoint, void* grad = nullptr) {
     if (!q || (!phi && !grad)) fail(MLFMA_ERR_INVALID_ARG, "null q or phi");
     if (nrhs < 1) fail(MLFMA_ERR_INVALID_ARG, "nrhs must be >= 1 (got %d)", nrhs);
@@ -259,7 +288,46 @@ static void apply_impl(Plan& P, const void* q, void* phi, int nrhs, bool adjoint
         MLFMA_CUDA(cudaMemcpyAsync(phi, P.phiout, bytes, dphi ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P.stream));
     if (grad) MLFMA_CUDA(cudaMemcpyAsync(grad, P.gout, 3 * bytes, cudaMemcpyDeviceToDevice, P.stream));
     if (P.profiling) P.acc.applies += nrhs;
-    if (!dphi || !dq) MLFMA_CUDA(cudaStreamSynchronize(P.stream));
+    if (!dphi || !dq) {
+        MLFMA_CUDA(cudaStreamSynchronize(P.stream));
+        check_device_errors(P);
+    }
+}
+
+// Reverse mode (see mlfma_apply_vjp): psi = A conj(g) and grad psi by one adjoint gradient sweep
+// (phiout = conj(psi) = A^H g), grad phi from the caller or from a second gradient sweep, and
+// the position gradient assembled by one kernel.
+static void vjp_impl(Plan& P, const void* q, const void* g, const void* gphi, void* grad_q, double* grad_r, int nrhs) {
+    if (!q || !g) fail(MLFMA_ERR_INVALID_ARG, "null q or g");
+    if (!grad_q && !grad_r) fail(MLFMA_ERR_INVALID_ARG, "grad_q and grad_r are both NULL");
+    if (nrhs < 1) fail(MLFMA_ERR_INVALID_ARG, "nrhs must be >= 1 (got %d)", nrhs);
+    if (!is_device_ptr(q) || !is_device_ptr(g) || (gphi && !is_device_ptr(gphi)) || (grad_q && !is_device_ptr(grad_q)) ||
+        (grad_r && !is_device_ptr(grad_r)))
+        fail(MLFMA_ERR_INVALID_ARG, "mlfma_apply_vjp takes device pointers only");
+    const size_t bytes = (size_t)nrhs * P.ntot * csize(P);
+    const bool want_r = grad_r != nullptr;
+    ensure_io_buffers(P, nrhs, want_r);
+    const void* gphi_use = gphi;
+    if (want_r && !gphi) {
+        // recompute grad phi of the forward charges and keep it while the adjoint sweep runs
+        if (nrhs > P.nrhs_vjp) {
+            P.mem.drop(P.vjp_buf);
+            P.vjp_buf = nullptr;
+            P.vjp_buf = P.mem.get(3 * bytes);
+            P.nrhs_vjp = nrhs;
+        }
+        MLFMA_CUDA(cudaMemcpyAsync(P.qin, q, bytes, cudaMemcpyDeviceToDevice, P.stream));
+        run(P, nrhs, false, true);
+        MLFMA_CUDA(cudaMemcpyAsync(P.vjp_buf, P.gout, 3 * bytes, cudaMemcpyDeviceToDevice, P.stream));
+        gphi_use = P.vjp_buf;
+    }
+    MLFMA_CUDA(cudaMemcpyAsync(P.qin, g, bytes, cudaMemcpyDeviceToDevice, P.stream));
+    run(P, nrhs, true, want_r);
+    if (grad_q) MLFMA_CUDA(cudaMemcpyAsync(grad_q, P.phiout, bytes, cudaMemcpyDeviceToDevice, P.stream));
+    if (want_r) position_grad(P, P.ntot, nrhs, q, g, gphi_use, P.gout, grad_r, P.stream);
+    if (P.profiling) P.acc.applies += nrhs * (want_r && !gphi ? 2 : 1);
+    MLFMA_CUDA(cudaStreamSynchronize(P.stream));
+    check_device_errors(P);
 }
 
 void apply_device(Plan& P, const void* q) {
@@ -402,8 +470,12 @@ static mlfma_options checked_options(const mlfma_options* opt, double k, int dig
     mlfma_options o;
     mlfma_options_init(&o);
     if (opt) {
-        if (opt->struct_size < sizeof(mlfma_options)) fail(MLFMA_ERR_INVALID_ARG, "options.struct_size too small");
-        o = *opt;
+        // callers built against an older header pass a shorter struct: the fields they know are
+        // taken, the newer ones keep their defaults
+        constexpr size_t kOldest = offsetof(mlfma_options, autotune) + sizeof(int);
+        if (opt->struct_size < kOldest) fail(MLFMA_ERR_INVALID_ARG, "options.struct_size too small");
+        memcpy(&o, opt, std::min(opt->struct_size, sizeof(mlfma_options)));
+        o.struct_size = sizeof(mlfma_options);
     }
     if (o.precision == MLFMA_PREC_FP32_BF16X3)
         fail(MLFMA_ERR_UNSUPPORTED, "precision FP32_BF16X3 is not built (use FP32_TF32X3)");
@@ -413,6 +485,9 @@ static mlfma_options checked_options(const mlfma_options* opt, double k, int dig
     if (o.digit_margin < -1 || o.digit_margin > 8) fail(MLFMA_ERR_INVALID_ARG, "digit_margin must be in [-1, 8]");
     if (!std::isfinite(o.leaf_edge)) fail(MLFMA_ERR_INVALID_ARG, "leaf_edge must be finite");
     if ((o.alloc == nullptr) != (o.free == nullptr)) fail(MLFMA_ERR_INVALID_ARG, "alloc and free must be given together");
+    if (o.recompute_signatures != 0 && o.recompute_signatures != 1)
+        fail(MLFMA_ERR_INVALID_ARG, "recompute_signatures must be 0 or 1");
+    if (o.test_fail_waits != 0 && o.test_fail_waits != 1) fail(MLFMA_ERR_INVALID_ARG, "test_fail_waits must be 0 or 1");
     return o;
 }
 
@@ -432,6 +507,8 @@ static void configure(Plan& p, int64_t n, double k, int digits, int leaf_max, co
     p.mem.free = o.free;
     p.mem.ctx = o.alloc_ctx;
     p.mem.stream = p.stream;
+    p.wait_first = o.test_fail_waits ? 0 : (1ll << 22);
+    p.recompute = o.recompute_signatures ? 1 : 0;
 }
 
 // tree, lists, grids and operators of one point set (device points)
@@ -550,6 +627,14 @@ mlfma_status mlfma_apply_grad(mlfma_plan* plan, const void* q, void* phi, void* 
     });
 }
 
+mlfma_status mlfma_apply_vjp(mlfma_plan* plan, const void* q, const void* g, const void* gphi, void* grad_q,
+                             double* grad_r, int nrhs) {
+    return guarded([&] {
+        if (!plan) fail(MLFMA_ERR_INVALID_ARG, "null plan");
+        vjp_impl(plan->p, q, g, gphi, grad_q, grad_r, nrhs);
+    });
+}
+
 mlfma_status mlfma_solve_gmres(mlfma_plan* plan, const void* b, void* x, double sigma_re, double sigma_im, double tol,
                                int restart, int max_iter, mlfma_solve_info* info) {
     return guarded([&] {
@@ -560,20 +645,8 @@ mlfma_status mlfma_solve_gmres(mlfma_plan* plan, const void* b, void* x, double 
         if (max_iter < 1) fail(MLFMA_ERR_INVALID_ARG, "max_iter must be >= 1 (got %d)", max_iter);
         if (!std::isfinite(sigma_re) || !std::isfinite(sigma_im)) fail(MLFMA_ERR_INVALID_ARG, "sigma must be finite");
         gmres_solve(plan->p, b, x, sigma_re, sigma_im, tol, restart, max_iter, info);
+        check_device_errors(plan->p);
     });
-}
-
-// error flags raised by kernels that gave up a bounded wait (this plan and its sub-plans)
-static void check_device_errors(const Plan& p) {
-    auto one = [](const Plan& q) {
-        if (!q.dev_err) return;
-        int e = 0;
-        MLFMA_CUDA(cudaStreamSynchronize(q.stream));
-        MLFMA_CUDA(cudaMemcpy(&e, q.dev_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (e) fail(MLFMA_ERR_TIMEOUT, "a tensor-core kernel timed out waiting for its MMAs (flag %d)", e);
-    };
-    one(p);
-    for (const Plan* sp : p.subs) one(*sp);
 }
 
 mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info) {
@@ -606,6 +679,7 @@ mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info) {
         info->tile_bytes[1] = p.tile_parent;
         info->tile_bytes[2] = p.tile_fused;
         info->n_geom = p.subs.empty() ? 1 : (int)p.subs.size();
+        info->recompute_signatures = p.recompute;
         if (p.forest) {                                // the merged levels (height above the leaves)
             for (const Plan* sp : p.subs) info->device_bytes += (int64_t)sp->mem.bytes;
         } else if (!p.subs.empty()) {
@@ -682,7 +756,7 @@ mlfma_status mlfma_plan_export(const mlfma_plan* plan, int item, int level, void
         if (needed) *needed = tot;
         if (!dst) return;
         if (bytes < tot) fail(MLFMA_ERR_INVALID_ARG, "buffer of %zu bytes < %zu needed", bytes, tot);
-        MLFMA_CUDA(cudaStreamSynchronize(p.stream));
+        check_device_errors(p);
         size_t off = 0;
         for (auto& x : parts) {
             if (x.second) MLFMA_CUDA(cudaMemcpy((char*)dst + off, x.first, x.second, cudaMemcpyDefault));
@@ -724,8 +798,8 @@ static cudaEvent_t take_event(Plan& p) {
     return e;
 }
 
-StageTimer::StageTimer(Plan& plan, int stage, int level, int launches) : p(plan) {
-    if (!p.profiling) return;
+StageTimer::StageTimer(Plan& plan, int stage, int level, int launches, bool on) : p(plan) {
+    if (!p.profiling || !on) return;
     Plan::EventRec r{stage, level, launches, take_event(p), take_event(p)};
     MLFMA_CUDA(cudaEventRecord(r.a, p.stream));
     p.recs.push_back(r);
@@ -766,6 +840,7 @@ mlfma_status mlfma_plan_timings(mlfma_plan* plan, mlfma_timings* out, int reset)
     return guarded([&] {
         if (!plan || !out) fail(MLFMA_ERR_INVALID_ARG, "null plan or out");
         Plan& P = plan->p;
+        check_device_errors(P);
         collect_timings(P);
         for (Plan* sp : P.subs) {
             collect_timings(*sp);

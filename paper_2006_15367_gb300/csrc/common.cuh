@@ -187,6 +187,10 @@ struct Plan {
     int digits = 0, leaf_max = 0, max_depth = 12, margin = 1;
     mlfma_precision prec = MLFMA_PREC_FP32;
     int* dev_err = nullptr;        // raised by kernels whose bounded waits ran out
+    long long wait_first = 1ll << 22;   // polls of a kernel's first try of a bounded wait (0: test hook)
+    int recompute = 0;             // mlfma_options.recompute_signatures
+    void* vjp_buf = nullptr;       // [nrhs_vjp][n][3] complex: grad psi kept while grad phi is recomputed
+    int nrhs_vjp = 0;
     int far_nr = 1;                // right-hand sides the far-level signatures F, G have room for
     bool graphs_stale = false;     // buffers captured by earlier graphs were replaced
     double leaf_edge = 0, a1 = 0, D0 = 0;
@@ -267,7 +271,7 @@ struct Plan {
 struct StageTimer {
     Plan& p;
     int idx = -1;
-    StageTimer(Plan& plan, int stage, int level, int launches);
+    StageTimer(Plan& plan, int stage, int level, int launches, bool on = true);
     ~StageTimer();
 };
 void collect_timings(Plan& p);
@@ -305,6 +309,9 @@ void gmres_solve(Plan& P, const void* b, void* x, double sr, double si, double t
                  mlfma_solve_info* info);
 // ld: row stride of the caller-order vectors (default n)
 void permute_out3(Plan& p, const void* gs, void* g, int nrhs, int64_t ld = -1);
+// grad_r[i][a] = sum_r Re[conj(g[r][i]) gphi[r][i][a] + q[r][i] gpsi[r][i][a]] (caller order, FP64 out)
+void position_grad(const Plan& p, int64_t n, int nrhs, const void* q, const void* g, const void* gphi, const void* gpsi,
+                   double* grad_r, cudaStream_t s);
 void permute_in(Plan& p, const void* q, void* qs, int nrhs, bool conj, int64_t ld = -1);
 void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj, int64_t ld = -1);
 void direct_fp64(const double* pts, int64_t n, const void* q, double k, const int64_t* tg, int64_t nt,
@@ -314,8 +321,9 @@ void direct_fp64(const double* pts, int64_t n, const void* q, double k, const in
 int64_t scan_tmp_ints(int64_t n);
 int scan_exclusive(const int* in, int* out, int64_t n, int* tmp, cudaStream_t s);
 
-// near field only (P2P over the near lists), one right-hand side, sorted order
-void near_only(Plan& p, const void* qs, void* phis);
+// near field only (P2P over the near lists), one right-hand side, sorted order; timed = false
+// records no stage events even while the plan is profiling
+void near_only(Plan& p, const void* qs, void* phis, bool timed = true);
 
 }  // namespace mlfma
 

@@ -397,8 +397,10 @@ __device__ __forceinline__ void m2l_parent(int lane, int t0, const uint64_t* __r
     }
 }
 
-__device__ __forceinline__ bool m2l_bar_wait(uint32_t bar, uint32_t phase) {
-    for (long long i = 0; i < (1ll << 22); ++i) {
+constexpr long long kM2LWaitLimit = 1ll << 22;
+
+__device__ __forceinline__ bool m2l_bar_wait(uint32_t bar, uint32_t phase, long long limit = kM2LWaitLimit) {
+    for (long long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __r
                                                    const int* __restrict__ loff, const unsigned long long* __restrict__ lsrc,
                                                    const uint64_t* __restrict__ ckey, const __grid_constant__ CUtensorMap tmT,
                                                    const C* __restrict__ F, int64_t K, int64_t sF, C* __restrict__ G,
-                                                   int Q, int* __restrict__ err) {
+                                                   int Q, int* __restrict__ err, long long wait_first) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t tbar;
     // operator slice Ts[344][32] at a 128-byte boundary (TMA destination)
@@ -450,9 +452,9 @@ __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __r
                 : "memory");
         }
     }
-    if (!__syncthreads_and(m2l_bar_wait(bar, 0))) {
+    if (!__syncthreads_and(m2l_bar_wait(bar, 0, wait_first))) {
         if (threadIdx.x == 0) atomicExch(err, 2);
-        m2l_bar_wait(bar, 0);                     // bounded: let the copies in flight land
+        m2l_bar_wait(bar, 0);                     // normal limit: let the copies in flight land
         return;
     }
     const bool ok = p0 + lane < K;
@@ -529,7 +531,8 @@ static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
     const size_t sm = m2l_smem<R, C>() + (Q > 1 ? (size_t)NW * 8 * NR * 32 * sizeof(C) : 0);
     const dim3 grid(nblk(TP.nbox, ppc), nblk(F.K, 32));
     k_m2l<R, C, NR, NW><<<grid, 32 * NW, sm, s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off, TP.m2l_src, T.key,
-                                                  F.tmT, (const C*)F.F, F.K, T.nbox * F.K, (C*)F.G, Q, p.dev_err);
+                                                  F.tmT, (const C*)F.F, F.K, T.nbox * F.K, (C*)F.G, Q, p.dev_err,
+                                                  std::min(p.wait_first, kM2LWaitLimit));
     MLFMA_LAUNCH_CHECK();
 }
 

@@ -319,7 +319,7 @@ void permute_out(Plan& p, const void* phis, void* phi, int nrhs, bool conj, int6
 }
 
 template <typename R, int NR>
-static void near_apply(Plan& p, const void* qs, void* phis, void* grads) {
+static void near_apply(Plan& p, const void* qs, void* phis, void* grads, bool timed = true) {
     using C = typename Cx<R>::T;
     LevelRanges LR;
     for (int l = 0; l <= kMaxLev; ++l) {
@@ -329,7 +329,7 @@ static void near_apply(Plan& p, const void* qs, void* phis, void* grads) {
     }
     const int64_t nl = p.n_small, sn = p.n;
     const R kpi = (R)(p.k / M_PI);
-    StageTimer st(p, MLFMA_STAGE_P2P, 0, (nl > 0) + (p.n_tiles > 0));
+    StageTimer st(p, MLFMA_STAGE_P2P, 0, (nl > 0) + (p.n_tiles > 0), timed);
     if (nl > 0) {
         if (grads)
             k_p2p<R, C, true, 1><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off,
@@ -354,9 +354,9 @@ static void near_apply(Plan& p, const void* qs, void* phis, void* grads) {
     }
 }
 
-void near_only(Plan& p, const void* qs, void* phis) {
-    if (p.prec == MLFMA_PREC_FP64) near_apply<double, 1>(p, qs, phis, nullptr);
-    else near_apply<float, 1>(p, qs, phis, nullptr);
+void near_only(Plan& p, const void* qs, void* phis, bool timed) {
+    if (p.prec == MLFMA_PREC_FP64) near_apply<double, 1>(p, qs, phis, nullptr, timed);
+    else near_apply<float, 1>(p, qs, phis, nullptr, timed);
 }
 
 // nr right-hand sides (q and phi n apart): 1, or kMaxNR without gradients
@@ -390,6 +390,38 @@ void permute_out3(Plan& p, const void* gs, void* g, int nrhs, int64_t ld) {
         k_permute_out3<double2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, ld, p.perm, (const double2*)gs, (double2*)g);
     else
         k_permute_out3<float2><<<nblk(tot, 256), 256, 0, p.stream>>>(p.n, nrhs, ld, p.perm, (const float2*)gs, (float2*)g);
+    MLFMA_LAUNCH_CHECK();
+}
+
+// grad_r[i][a] = sum_r Re[conj(g_ri) gphi_ri[a] + q_ri gpsi_ri[a]]: the derivative of a real loss
+// with respect to the position r_i (reverse mode of phi = A(r) q; g = dL/dRe phi + i dL/dIm phi,
+// psi = A conj(g)).  One thread per (point, component), caller order, FP64 result.
+template <typename C>
+__global__ void k_position_grad(int64_t n, int nrhs, const C* __restrict__ q, const C* __restrict__ g,
+                                const C* __restrict__ gphi, const C* __restrict__ gpsi, double* __restrict__ grad_r) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= 3 * n) return;
+    const int64_t i = idx / 3;
+    double acc = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+        const C gv = g[r * n + i], qv = q[r * n + i];
+        const C a = gphi[r * 3 * n + idx], b = gpsi[r * 3 * n + idx];
+        // Re(conj(g) a) + Re(q b)
+        acc += (double)gv.x * (double)a.x + (double)gv.y * (double)a.y + (double)qv.x * (double)b.x -
+               (double)qv.y * (double)b.y;
+    }
+    grad_r[idx] = acc;
+}
+
+void position_grad(const Plan& p, int64_t n, int nrhs, const void* q, const void* g, const void* gphi, const void* gpsi,
+                   double* grad_r, cudaStream_t s) {
+    const int64_t tot = 3 * n;
+    if (p.prec == MLFMA_PREC_FP64)
+        k_position_grad<double2><<<nblk(tot, 256), 256, 0, s>>>(n, nrhs, (const double2*)q, (const double2*)g,
+                                                                (const double2*)gphi, (const double2*)gpsi, grad_r);
+    else
+        k_position_grad<float2><<<nblk(tot, 256), 256, 0, s>>>(n, nrhs, (const float2*)q, (const float2*)g,
+                                                               (const float2*)gphi, (const float2*)gpsi, grad_r);
     MLFMA_LAUNCH_CHECK();
 }
 

@@ -67,8 +67,8 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
         : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    for (long long i = 0; i < kWaitLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit = kWaitLimit) {
+    for (long long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -94,7 +94,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 // Npmax: the MMA N of the widest tile of the launch (sizes the B region of shared memory)
 __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc, int nin, int nout, int Npmax,
                                                                 const float* __restrict__ Mt, const float2* __restrict__ in,
-                                                                float2* __restrict__ out, int* __restrict__ err) {
+                                                                float2* __restrict__ out, int* __restrict__ err,
+                                                                long long wait_first) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t s_taddr;
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
         }
         issued = true;
         // the MMAs read the staged chunk: wait before it is overwritten (and before the epilogue)
-        ok = __syncthreads_and(mbar_wait(bar, phase));       // one decision for the whole CTA
+        ok = __syncthreads_and(mbar_wait(bar, phase, wait_first));   // one decision for the whole CTA
         issued = !ok;
         phase ^= 1;
     }
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
         }
     } else {
         if (threadIdx.x == 0) atomicExch(err, 1);
-        if (issued) mbar_wait(bar, phase ^ 1);                          // let the MMAs in flight finish (bounded)
+        if (issued) mbar_wait(bar, phase ^ 1);        // let the MMAs in flight finish (bounded, normal limit)
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -254,7 +255,8 @@ void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout,
     const dim3 grid((unsigned)((nbox + kTcBoxes - 1) / kTcBoxes), (unsigned)((nout + kTcMaxN - 1) / kTcMaxN), (unsigned)nm);
     const int Npmax = ((std::min(nout, kTcMaxN) + 15) / 16) * 16;
     const size_t smem = 2 * (size_t)kABytes + 2 * (size_t)Npmax * kTcKC * 4;
-    k_theta_map_tc<<<grid, kTcThreads, smem, s>>>((int)nbox, Lc, nin, nout, Npmax, M, in, out, p.dev_err);
+    k_theta_map_tc<<<grid, kTcThreads, smem, s>>>((int)nbox, Lc, nin, nout, Npmax, M, in, out, p.dev_err,
+                                                  std::min<long long>(p.wait_first, kWaitLimit));
     MLFMA_LAUNCH_CHECK();
 }
 

