@@ -59,7 +59,9 @@ typedef enum {
 typedef enum {
     MLFMA_PREC_FP64 = 0,          /* complex128 data, FP64 arithmetic on every stage */
     MLFMA_PREC_FP32 = 1,          /* complex64 data, FP32 arithmetic; operators built in FP64 */
-    MLFMA_PREC_FP32_BF16X3 = 2,   /* reserved: split-BF16 tensor-core contractions (not implemented: UNSUPPORTED) */
+    MLFMA_PREC_FP32_BF16X3 = 2,   /* as FP32_TF32X3 with BF16 operand parts (hi = x rounded to BF16,
+                                     lo = x - hi rounded to BF16; kind::f16 MMAs at twice the TF32 rate):
+                                     products good to about 2^-16 relative, enough for 4 digits */
     MLFMA_PREC_FP32_TF32X3 = 3    /* as FP32, but the theta maps of the interpolation (Sec. 3.2.2) and
                                      anterpolation (Sec. 3.2.4) on level pairs too large to fuse run on
                                      the tensor cores as split-TF32 GEMMs (x = hi + lo, products hi*hi +

@@ -477,9 +477,8 @@ static mlfma_options checked_options(const mlfma_options* opt, double k, int dig
         memcpy(&o, opt, std::min(opt->struct_size, sizeof(mlfma_options)));
         o.struct_size = sizeof(mlfma_options);
     }
-    if (o.precision == MLFMA_PREC_FP32_BF16X3)
-        fail(MLFMA_ERR_UNSUPPORTED, "precision FP32_BF16X3 is not built (use FP32_TF32X3)");
-    if (o.precision != MLFMA_PREC_FP64 && o.precision != MLFMA_PREC_FP32 && o.precision != MLFMA_PREC_FP32_TF32X3)
+    if (o.precision != MLFMA_PREC_FP64 && o.precision != MLFMA_PREC_FP32 && o.precision != MLFMA_PREC_FP32_TF32X3 &&
+        o.precision != MLFMA_PREC_FP32_BF16X3)
         fail(MLFMA_ERR_INVALID_ARG, "unknown precision %d", (int)o.precision);
     if (o.max_depth < 1 || o.max_depth > kMaxLev) fail(MLFMA_ERR_INVALID_ARG, "max_depth must be in [1, %d]", kMaxLev);
     if (o.digit_margin < -1 || o.digit_margin > 8) fail(MLFMA_ERR_INVALID_ARG, "digit_margin must be in [-1, 8]");

@@ -327,12 +327,12 @@ __global__ void __launch_bounds__(128) k_l2o_big(const int2* __restrict__ tiles,
 // G_t = sum over s in V(t) of T_{t-s} F_s, organised per parent P: a warp takes P and a
 // 32-sample slice of the grid (p = tile * 32 + lane), walks the list of P's colleagues'
 // children that are far from some child of P (entries (src * K) << 32 | far-children mask
-// << 16 | base), loads each source's samples once and adds them to every child of P it is
-// far from.  The operators of the slice are staged in shared memory as the full 7^3 offset
-// cube Ts[343][32] (the 27 near rows zero), so the row of a (child, source) pair is
-// base(source) + c(child).  The child count NT is a template argument, so each entry costs
-// NT predicated child slots.  NR right-hand sides (signatures r sF apart) share every
-// operator load.
+// << 16 | base), loads each source's samples once and adds them to every child of P.  The
+// operators of the slice are staged in shared memory as the full 7^3 offset cube Ts[343][32]
+// (the 27 near rows zero), so the row of a (child, source) pair is base(source) + c(child),
+// and a child near the source reads a zero row: the child slots need no predicates.  The
+// child count NT is a template argument, so each entry costs exactly NT child slots.  NR
+// right-hand sides (signatures r sF apart) share every operator load.
 constexpr int kM2LParentsPerWarp = 4;
 
 // cp.async of B bytes global -> shared; v = false fills the B bytes with zeros (nothing is read)
@@ -363,25 +363,22 @@ __device__ __forceinline__ void m2l_parent(int lane, int t0, const uint64_t* __r
     for (int t = 0; t < NT; ++t)
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[t][r] = cmake<C>(0, 0);
-    // the lanes fetch 32 list entries at once and broadcast them one by one
-    for (int eb = 0; eb < ne; eb += 32) {
-        const unsigned long long mine = eb + lane < ne ? __ldg(le + eb + lane) : 0ull;
-        const int cnt = ne - eb < 32 ? ne - eb : 32;
-        for (int j = 0; j < cnt; ++j) {
-            const unsigned long long w = __shfl_sync(0xffffffffu, mine, j);
-            const unsigned lo = (unsigned)w;
-            const C* fs = Fp + (unsigned)(w >> 32);
-            C f[NR];
+    // every lane reads each list entry from the same address (one broadcast load); each entry
+    // costs NT child slots without predicates: a child that is not far from the source reads one
+    // of the 27 zero (near-offset) rows of the cube, which adds exactly nothing
+    for (int j = 0; j < ne; ++j) {
+        const unsigned long long w = __ldg(le + j);
+        const unsigned lo = (unsigned)w;
+        const C* fs = Fp + (unsigned)(w >> 32);
+        C f[NR];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) f[r] = fs[r * sF];
-            const C* Tb = Tl + (lo & 511u) * 32;
+        for (int r = 0; r < NR; ++r) f[r] = fs[r * sF];
+        const C* Tb = Tl + (lo & 511u) * 32;
 #pragma unroll
-            for (int t = 0; t < NT; ++t)
-                if (lo & (0x10000u << t)) {
-                    const C tv = Tb[cr[t]];
+        for (int t = 0; t < NT; ++t) {
+            const C tv = Tb[cr[t]];
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) cfma(acc[t][r], tv, f[r]);
-                }
+            for (int r = 0; r < NR; ++r) cfma(acc[t][r], tv, f[r]);
         }
     }
     if (red) {                                    // a partial sum over part of the list
@@ -623,42 +620,56 @@ __device__ __forceinline__ void small_dft(const C (&v)[R], C (&X)[R]) {
     }
 }
 
-// one radix-R butterfly of a Stockham stage: inputs a[j + r nb], outputs b[q Ns R + k + kk Ns]
-// with q = j / Ns, k = j mod Ns, twiddles tw[k r tstep]
+// Radix-R butterflies of one Stockham stage for the same butterfly index j in up to kFftRows
+// rows (row, row + 1, ...): inputs a[j + r nb], outputs b[q Ns R + k + kk Ns] with q = j / Ns,
+// k = j mod Ns, twiddles tw[k r tstep].  The index arithmetic and the twiddle loads are done
+// once for all the rows.
+constexpr int kFftRows = 2;
+
 template <int R, bool INV, typename C>
-__device__ __forceinline__ void fft_bfly(const C* __restrict__ a, C* __restrict__ b, int j, int nb, int Ns, int q, int tstep,
-                                         const C* __restrict__ tw) {
+__device__ __forceinline__ void fft_bfly_rows(const C* __restrict__ a, C* __restrict__ b, int nr, int pitch, int j, int nb,
+                                              int Ns, int q, int tstep, const C* __restrict__ tw) {
     const int k = j - q * Ns;
-    C v[R];
+    C w[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        C x = a[j + r * nb];
-        if (r > 0) x = cmul(x, twid(tw, k * r * tstep, INV));
-        v[r] = x;
-    }
-    C X[R];
-    small_dft<R, INV>(v, X);
+    for (int r = 1; r < R; ++r) w[r] = twid(tw, k * r * tstep, INV);
     const int idxD = q * Ns * R + k;
 #pragma unroll
-    for (int kk = 0; kk < R; ++kk) b[idxD + kk * Ns] = X[kk];
+    for (int u = 0; u < kFftRows; ++u) {
+        if (u < nr) {
+            const C* ar = a + u * pitch;
+            C* br = b + u * pitch;
+            C v[R];
+            v[0] = ar[j];
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(ar[j + r * nb], w[r]);
+            C X[R];
+            small_dft<R, INV>(v, X);
+#pragma unroll
+            for (int kk = 0; kk < R; ++kk) br[idxD + kk * Ns] = X[kk];
+        }
+    }
 }
 
+// one stage over nrows rows: a thread takes a butterfly index j and a group of kFftRows rows
 template <bool INV, typename C>
 __device__ __forceinline__ void fft_stage(const C* __restrict__ in, C* __restrict__ out, int nrows, const FftPlan& fp, int st,
                                           const C* __restrict__ tw, int pitch) {
     const int R = fp.r[st], nb = fp.nb[st], Ns = fp.Ns[st], tstep = fp.tstep[st];
     const FastDiv dnb = fp.dnb[st], dNs = fp.dNs[st];
-    for (int idx = threadIdx.x; idx < nrows * nb; idx += blockDim.x) {
-        const int row = (int)dnb.div((unsigned)idx), j = idx - row * nb;
+    const int ngroups = (nrows + kFftRows - 1) / kFftRows;
+    for (int idx = threadIdx.x; idx < ngroups * nb; idx += blockDim.x) {
+        const int g = (int)dnb.div((unsigned)idx), j = idx - g * nb;
         const int q = (int)dNs.div((unsigned)j);
+        const int row = g * kFftRows, nr = min(kFftRows, nrows - row);
         const C* a = in + row * pitch;
         C* b = out + row * pitch;
         switch (R) {
-            case 2: fft_bfly<2, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
-            case 3: fft_bfly<3, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
-            case 4: fft_bfly<4, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
-            case 5: fft_bfly<5, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
-            default: fft_bfly<7, INV>(a, b, j, nb, Ns, q, tstep, tw); break;
+            case 2: fft_bfly_rows<2, INV>(a, b, nr, pitch, j, nb, Ns, q, tstep, tw); break;
+            case 3: fft_bfly_rows<3, INV>(a, b, nr, pitch, j, nb, Ns, q, tstep, tw); break;
+            case 4: fft_bfly_rows<4, INV>(a, b, nr, pitch, j, nb, Ns, q, tstep, tw); break;
+            case 5: fft_bfly_rows<5, INV>(a, b, nr, pitch, j, nb, Ns, q, tstep, tw); break;
+            default: fft_bfly_rows<7, INV>(a, b, nr, pitch, j, nb, Ns, q, tstep, tw); break;
         }
     }
 }
@@ -1183,7 +1194,7 @@ template <typename R, typename C>
 static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const R* M, const C* in, C* out,
                              cudaStream_t s) {
     if constexpr (sizeof(C) == 8) {
-        if (p.prec == MLFMA_PREC_FP32_TF32X3) {
+        if (p.prec == MLFMA_PREC_FP32_TF32X3 || p.prec == MLFMA_PREC_FP32_BF16X3) {
             launch_theta_map_tc(p, nbox, Lc, nin, nout, (const float*)M, (const float2*)in, (float2*)out, s);
             return;
         }
@@ -1382,7 +1393,7 @@ static void prepare_fft_kernels() {
 void prepare_kernels(Plan& p) {
     if (p.prec == MLFMA_PREC_FP64) prepare_fft_kernels<double2, double>();
     else prepare_fft_kernels<float2, float>();
-    if (p.prec == MLFMA_PREC_FP32_TF32X3) prepare_theta_tc();
+    if (p.prec == MLFMA_PREC_FP32_TF32X3 || p.prec == MLFMA_PREC_FP32_BF16X3) prepare_theta_tc();
     if (p.prec == MLFMA_PREC_FP64) {
         allow_max_smem(k_m2l<double, double2, 1, M2LShape<double2, 1>::NW>);
         allow_max_smem(k_m2l<double, double2, kMaxNR, M2LShape<double2, kMaxNR>::NW>);

@@ -1,18 +1,25 @@
 // Theta maps of the interpolation (Sec. 3.2.2) and anterpolation (Sec. 3.2.4) on the
-// 5th-generation tensor cores, split-TF32 form (MLFMA_PREC_FP32_TF32X3):
+// 5th-generation tensor cores, split-TF32 (MLFMA_PREC_FP32_TF32X3) or split-BF16
+// (MLFMA_PREC_FP32_BF16X3) form:
 //
 //   out[mi][c][o] = sum_i M[|m|][i][o] in[mi][c][i],   m = mi - Lc
 //
 // a real matrix applied to complex vectors, one GEMM per Fourier mode.  A CTA takes 64
 // boxes of one mode: the A operand has 128 rows (row 2b = Re in[c0+b][.], row 2b+1 = Im),
 // the B operand is the mode's map with N <= 256 output rows as K-major rows.  Both are
-// split into TF32 parts while staged in shared memory, x = hi + lo with hi = x truncated to
-// TF32 and lo = x - hi (exact), and the product is accumulated in FP32 in tensor memory
-// as hi*hi + hi*lo + lo*hi (the dropped lo*lo term is below 2^-22 relative), so the result
-// carries FP32-level accuracy.  The K dimension is staged in chunks of 32; one thread
-// issues tcgen05.mma (kind::tf32, M = 128) and tcgen05.commit signals an mbarrier; the
+// split into two parts while staged in shared memory, x = hi + lo, and the product is
+// accumulated in FP32 in tensor memory as hi*hi + hi*lo + lo*hi:
+//   TF32: hi = x truncated to TF32, lo = x - hi (exact); the dropped lo*lo term is below
+//         2^-22 relative, so the result carries FP32-level accuracy (kind::tf32, K = 8 per MMA);
+//   BF16: hi = x rounded to BF16, lo = (x - hi) rounded to BF16; hi + lo keeps 16 significant
+//         bits, the products are good to about 2^-16 relative (kind::f16 with BF16 operands,
+//         K = 16 per MMA, twice the tensor rate of TF32).
+// The K dimension is staged in chunks of 128 bytes per row (32 TF32 or 64 BF16 values); one
+// thread issues tcgen05.mma (M = 128) and tcgen05.commit signals an mbarrier; the
 // accumulator is read back with tcgen05.ld.  Every wait has an iteration limit after which
 // the kernel raises the plan's error flag, releases its tensor memory and returns.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -23,48 +30,77 @@ namespace {
 
 constexpr int kTcBoxes = 64;                 // boxes per CTA (A rows 2b, 2b + 1)
 constexpr int kTcM = 128;                    // MMA M
-constexpr int kTcKC = 32;                    // K elements per staged chunk (4 MMA K-steps)
+constexpr int kTcRowBytes = 128;             // bytes of one operand row per staged K chunk (4 MMA K-steps)
 constexpr int kTcMaxN = 256;                 // output rows per CTA (MMA N <= 256)
 constexpr int kTcThreads = 128;
-constexpr uint32_t kABytes = kTcM * kTcKC * 4;        // one TF32 part of the A chunk (16 KB)
-constexpr uint32_t kBBytesMax = kTcMaxN * kTcKC * 4;  // one TF32 part of the widest B chunk (32 KB)
+constexpr uint32_t kABytes = kTcM * kTcRowBytes;          // one part of the A chunk (16 KB)
+constexpr uint32_t kBBytesMax = kTcMaxN * kTcRowBytes;    // one part of the widest B chunk (32 KB)
 constexpr size_t kTcSmemMax = 2 * (size_t)kABytes + 2 * (size_t)kBBytesMax;   // 96 KB
 constexpr long long kWaitLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Canonical K-major layout without swizzle: core matrices of 8 rows x 16 bytes (4 TF32),
-// core (row / 8, k / 4) at byte ((row / 8) (KC / 4) + k / 4) 128, row r % 8 at 16 (r % 8).
-// Leading-dimension offset (next core along K) 128 B, stride offset (next 8 rows) KC / 4 * 128 B.
+// The two operand forms: element type in shared memory, K elements per chunk, the split of an
+// FP32 value into hi + lo, the instruction descriptor (D = F32, A and B of the same type, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24) and the MMA kind.
+struct SplitTF32 {
+    using T = float;
+    static constexpr int KC = kTcRowBytes / 4;       // 32
+    __device__ static void split(float x, T& hi, T& lo) {
+        hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+        lo = x - hi;
+    }
+    __device__ static uint32_t idesc(int M, int N) {
+        return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    }
+    __device__ static void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+};
+
+struct SplitBF16 {
+    using T = __nv_bfloat16;
+    static constexpr int KC = kTcRowBytes / 2;       // 64
+    __device__ static void split(float x, T& hi, T& lo) {
+        hi = __float2bfloat16_rn(x);
+        lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+    __device__ static uint32_t idesc(int M, int N) {
+        return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    }
+    __device__ static void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+};
+
+// Canonical K-major layout without swizzle: core matrices of 8 rows x 16 bytes (EPC = 16 /
+// sizeof(T) elements), core (row / 8, k / EPC) at byte ((row / 8) (KC / EPC) + k / EPC) 128, row
+// r % 8 at 16 (r % 8).  Leading-dimension offset (next core along K) 128 B, stride offset (next
+// 8 rows) KC / EPC * 128 = 1024 B for both forms.
+template <typename Op>
 __device__ __forceinline__ uint32_t core_off(int row, int k) {
-    return (uint32_t)(((row >> 3) * (kTcKC / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+    constexpr int ES = (int)sizeof(typename Op::T), EPC = 16 / ES;
+    return (uint32_t)(((row >> 3) * (Op::KC / EPC) + k / EPC) * 128 + (row & 7) * 16 + (k % EPC) * ES);
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);                    // start address
     d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;                       // leading-dimension byte offset
-    d |= (uint64_t)(((kTcKC / 4) * 128u >> 4) & 0x3FFFu) << 32;         // stride-dimension byte offset
+    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;                      // stride-dimension byte offset
     d |= (uint64_t)1 << 46;                                             // descriptor version of tcgen05
     return d;                                                           // base offset 0, no swizzle
 }
 
-// instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, N >> 3, M >> 4
-__device__ __forceinline__ uint32_t instr_desc_tf32(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-    hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-    lo = x - hi;
-}
-
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
+template <typename T> __device__ __forceinline__ void st_part(unsigned char* base, uint32_t off, T v) {
+    *reinterpret_cast<T*>(base + off) = v;
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit = kWaitLimit) {
@@ -92,6 +128,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 // Npmax: the MMA N of the widest tile of the launch (sizes the B region of shared memory)
+template <typename Op>
 __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc, int nin, int nout, int Npmax,
                                                                 const float* __restrict__ Mt, const float2* __restrict__ in,
                                                                 float2* __restrict__ out, int* __restrict__ err,
@@ -106,7 +143,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
     const int N = min(kTcMaxN, nout - n0);
     const int Np = (N + 15) & ~15;                                      // MMA N: multiple of 16 for M = 128
     const uint32_t ncols = Np <= 32 ? 32u : Np <= 64 ? 64u : Np <= 128 ? 128u : 256u;
-    const uint32_t bbytes = (uint32_t)Npmax * kTcKC * 4;              // one TF32 part of the B chunk
+    constexpr int KC = Op::KC;
+    using T = typename Op::T;
+    const uint32_t bbytes = (uint32_t)Npmax * kTcRowBytes;            // one part of the B chunk
     // plain stores (no compiler barrier between them, so the global loads of the staging
     // loops overlap); the async-proxy fence before the MMAs orders them
     unsigned char* pA[2] = {smem_raw, smem_raw + kABytes};
@@ -132,18 +171,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
 
     const float* Mm = Mt + (int64_t)m * nin * nout;
     const float2* inm = in + (int64_t)mi * nbox * nin;
-    const uint32_t idesc = instr_desc_tf32(kTcM, Np);
+    const uint32_t idesc = Op::idesc(kTcM, Np);
     uint32_t phase = 0;
     bool ok = true;
     bool issued = false;                                                // MMAs committed but not yet waited for
-    const int nchunks = (nin + kTcKC - 1) / kTcKC;
+    const int nchunks = (nin + KC - 1) / KC;
     for (int ch = 0; ch < nchunks && ok; ++ch) {
-        const int k0 = ch * kTcKC;
+        const int k0 = ch * KC;
         // A: a warp stores 4 boxes x 8 columns, so its 32 stores of one part cover the banks
         // (row mod 8, k mod 4) at most twice; reads are 4 runs of 8 contiguous samples.  Each
         // thread issues its kAPer loads before any store.
         {
-            constexpr int kAPer = kTcBoxes * kTcKC / kTcThreads;
+            constexpr int kAPer = kTcBoxes * KC / kTcThreads;
             float2 va[kAPer];
 #pragma unroll
             for (int it = 0; it < kAPer; ++it) {
@@ -157,13 +196,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
                 const int idx = threadIdx.x + it * kTcThreads;
                 const int w = idx >> 5, l = idx & 31;
                 const int b = (w & 15) * 4 + (l >> 3), k = (w >> 4) * 8 + (l & 7);
-                float h, lo;
-                split_tf32(va[it].x, h, lo);
-                *reinterpret_cast<float*>(pA[0] + core_off(2 * b, k)) = h;
-                *reinterpret_cast<float*>(pA[1] + core_off(2 * b, k)) = lo;
-                split_tf32(va[it].y, h, lo);
-                *reinterpret_cast<float*>(pA[0] + core_off(2 * b + 1, k)) = h;
-                *reinterpret_cast<float*>(pA[1] + core_off(2 * b + 1, k)) = lo;
+                T h, lo;
+                Op::split(va[it].x, h, lo);
+                st_part(pA[0], core_off<Op>(2 * b, k), h);
+                st_part(pA[1], core_off<Op>(2 * b, k), lo);
+                Op::split(va[it].y, h, lo);
+                st_part(pA[0], core_off<Op>(2 * b + 1, k), h);
+                st_part(pA[1], core_off<Op>(2 * b + 1, k), lo);
             }
         }
         // B: output row n, column k, B[n][k] = M[|m|][k0 + k][n0 + n]; a warp stores 8 rows x 4
@@ -172,7 +211,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
         {
             constexpr int kBBatch = 8;
             const int ng = Np >> 3;
-            const int tot = Np * kTcKC;                      // a multiple of kTcThreads * kBBatch / 2
+            const int tot = Np * KC;                         // a multiple of kTcThreads * kBBatch / 2
             for (int base = 0; base < tot; base += kTcThreads * kBBatch) {
                 float vb[kBBatch];
 #pragma unroll
@@ -190,10 +229,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
                     const int w = idx >> 5, l = idx & 31;
                     const int kq = w / ng, nq = w - kq * ng;
                     const int n = nq * 8 + (l >> 2), k = kq * 4 + (l & 3);
-                    float h, lo;
-                    split_tf32(vb[it], h, lo);
-                    *reinterpret_cast<float*>(pB[0] + core_off(n, k)) = h;
-                    *reinterpret_cast<float*>(pB[1] + core_off(n, k)) = lo;
+                    T h, lo;
+                    Op::split(vb[it], h, lo);
+                    st_part(pB[0], core_off<Op>(n, k), h);
+                    st_part(pB[1], core_off<Op>(n, k), lo);
                 }
             }
         }
@@ -202,11 +241,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
         if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-            for (int s = 0; s < kTcKC / 8; ++s) {
-                const uint32_t ko = (uint32_t)s * 256;                  // two 16-byte cores along K per step
-                mma_tf32(tmem, smem_desc(sA[0] + ko), smem_desc(sB[0] + ko), idesc, ch > 0 || s > 0);
-                mma_tf32(tmem, smem_desc(sA[0] + ko), smem_desc(sB[1] + ko), idesc, 1);
-                mma_tf32(tmem, smem_desc(sA[1] + ko), smem_desc(sB[0] + ko), idesc, 1);
+            for (int s = 0; s < 4; ++s) {
+                const uint32_t ko = (uint32_t)s * 256;          // one MMA K-step: two 16-byte cores along K
+                Op::mma(tmem, smem_desc(sA[0] + ko), smem_desc(sB[0] + ko), idesc, ch > 0 || s > 0);
+                Op::mma(tmem, smem_desc(sA[0] + ko), smem_desc(sB[1] + ko), idesc, 1);
+                Op::mma(tmem, smem_desc(sA[1] + ko), smem_desc(sB[0] + ko), idesc, 1);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
                          : "memory");
@@ -246,7 +285,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
 }  // namespace
 
 void prepare_theta_tc() {
-    MLFMA_CUDA(cudaFuncSetAttribute(k_theta_map_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax));
+    MLFMA_CUDA(cudaFuncSetAttribute(k_theta_map_tc<SplitTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kTcSmemMax));
+    MLFMA_CUDA(cudaFuncSetAttribute(k_theta_map_tc<SplitBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kTcSmemMax));
 }
 
 void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const float* M, const float2* in,
@@ -254,9 +296,12 @@ void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout,
     const int nm = 2 * Lc + 1;
     const dim3 grid((unsigned)((nbox + kTcBoxes - 1) / kTcBoxes), (unsigned)((nout + kTcMaxN - 1) / kTcMaxN), (unsigned)nm);
     const int Npmax = ((std::min(nout, kTcMaxN) + 15) / 16) * 16;
-    const size_t smem = 2 * (size_t)kABytes + 2 * (size_t)Npmax * kTcKC * 4;
-    k_theta_map_tc<<<grid, kTcThreads, smem, s>>>((int)nbox, Lc, nin, nout, Npmax, M, in, out, p.dev_err,
-                                                  std::min<long long>(p.wait_first, kWaitLimit));
+    const size_t smem = 2 * (size_t)kABytes + 2 * (size_t)Npmax * kTcRowBytes;
+    const long long wf = std::min<long long>(p.wait_first, kWaitLimit);
+    if (p.prec == MLFMA_PREC_FP32_BF16X3)
+        k_theta_map_tc<SplitBF16><<<grid, kTcThreads, smem, s>>>((int)nbox, Lc, nin, nout, Npmax, M, in, out, p.dev_err, wf);
+    else
+        k_theta_map_tc<SplitTF32><<<grid, kTcThreads, smem, s>>>((int)nbox, Lc, nin, nout, Npmax, M, in, out, p.dev_err, wf);
     MLFMA_LAUNCH_CHECK();
 }
 

@@ -13,7 +13,8 @@ workloads use:
 * the same sphere with split-TF32 tensor-core theta maps: 1e-3 against the direct sum and
   1e-5 per level (F and G) against the FP32 plan.
 * 4,194,304 points on a cube surface with 64 dense clusters (adaptive tree, leaf_max 64,
-  4 digits): 1e-4 against the direct sum on 2,000 sampled targets.
+  4 digits), FP32 and split-BF16 tensor-core theta maps: 1e-4 against the direct sum on
+  2,000 sampled targets.
 * 256 ellipsoids in one batched plan: 1e-3 against the direct sum of each of 8 sampled
   geometries (250 targets each).
 * the (8, 4, 2) ellipsoid with 262,144 points: reverse mode (charges and positions) through
@@ -95,15 +96,22 @@ def test_sphere1m_tf32x3(sphere1m):
     assert rel(phitc[tg], direct.direct(pts, q[0], prm["k"], targets=tg)) < 1e-3
 
 
-def test_cubeclusters4m_four_digits():
+@pytest.fixture(scope="module")
+def cube4m():
     pts, q, prm = synth.workload("cubeclusters4m")
-    plan = make_plan(pts, prm["k"], prm["digits"], "fp32", leaf_max=prm["leaf_max"])
-    phi = apply_plan(plan, q[0], "fp32")
+    tg = _targets(pts.shape[0], 2000, 3003)
+    return pts, q, prm, tg, direct.direct(pts, q[0], prm["k"], targets=tg)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_cubeclusters4m_four_digits(cube4m, prec):
+    pts, q, prm, tg, ref = cube4m
+    plan = make_plan(pts, prm["k"], prm["digits"], prec, leaf_max=prm["leaf_max"])
+    phi = apply_plan(plan, q[0], prec)
     info = plan.info()
     plan.close()
     assert info["top"] > 0
-    tg = _targets(pts.shape[0], 2000, 3003)
-    assert rel(phi[tg], direct.direct(pts, q[0], prm["k"], targets=tg)) < 1e-4
+    assert rel(phi[tg], ref) < 1e-4
 
 
 def test_batch256_sampled_geometries():

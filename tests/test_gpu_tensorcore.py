@@ -1,9 +1,10 @@
-"""Split-TF32 tensor-core theta maps (precision "tf32x3") against the oracle and the FP32 path.
+"""Tensor-core theta maps (precisions "tf32x3" and "bf16x3") against the oracle and the FP32 path.
 
 The tf32x3 plans run the theta maps of the level pairs that are too large for the fused
 FFT + theta-map kernels as tcgen05 GEMMs with operands split into two TF32 parts and
 three products accumulated in FP32, so every stage keeps the FP32 tolerances (1e-5 per
-stage against the FP64 oracle, 1e-3 end to end).
+stage against the FP64 oracle, 1e-3 end to end).  The bf16x3 plans split into BF16 parts
+(16 significant bits in hi + lo): 1e-4 per stage.
 """
 import math
 
@@ -62,8 +63,43 @@ def test_tf32x3_matches_fp32_large_sphere():
     p32.close()
 
 
-def test_bf16x3_reports_unsupported():
-    import paper_2006_15367_gb300 as mf
-    with pytest.raises(mf.MLFMAError) as e:
-        make_plan(synth.sphere(100, 1.0, seed=1), K, 3, "bf16x3")
-    assert e.value.status == 5
+def test_bf16x3_stages_match_oracle_mid_sphere():
+    """Split-BF16 theta maps (hi + lo BF16 parts, three products, FP32 accumulation): every
+    stage against the FP64 oracle at 1e-4 (the products carry about 16 significant bits), the
+    potentials at the 3-digit target."""
+    pts = synth.sphere(16384 - 7, 4.0, seed=81)
+    q = synth.complex_normal(82, pts.shape[0])[0]
+    o = om.OracleMLFMA(pts, K, 3, margin=0)
+    phio, dump = o.apply(q, dump=True)
+    plan = make_plan(pts, K, 3, "bf16x3")
+    phi = apply_plan(plan, q, "bf16x3")
+    for l in range(o.top, o.tree.nlev + 1):
+        nb = o.tree.levels[l].nbox
+        assert rel(plan.export("F", l).reshape(nb, -1), dump["F"][l]) < 1e-4, ("F", l)
+        assert rel(plan.export("G", l).reshape(nb, -1), dump["G"][l]) < 1e-4, ("G", l)
+    assert rel(phi, phio) < 1e-3
+    tg = np.arange(0, pts.shape[0], 7)
+    assert rel(phi[tg], direct.direct(pts, q, K, targets=tg)) < 1e-3
+    assert plan.info()["precision"] == 2
+    plan.close()
+
+
+def test_bf16x3_matches_fp32_large_sphere():
+    """65,536 points on a radius-8 sphere: the upper levels' theta maps in split BF16, every
+    level's F and G within 1e-4 of the FP32 plan, graph replay bit-identical."""
+    pts = synth.sphere(65536, 8.0, seed=91)
+    q = synth.complex_normal(92, pts.shape[0])[0]
+    p32 = make_plan(pts, K, 3, "fp32")
+    pbf = make_plan(pts, K, 3, "bf16x3")
+    phi32 = apply_plan(p32, q, "fp32")
+    phibf = apply_plan(pbf, q, "bf16x3")
+    info = pbf.info()
+    for l in range(info["top"], info["nlev"] + 1):
+        assert rel(pbf.export("F", l), p32.export("F", l)) < 1e-4, ("F", l)
+        assert rel(pbf.export("G", l), p32.export("G", l)) < 1e-4, ("G", l)
+    assert rel(phibf, phi32) < 1e-4
+    assert np.array_equal(apply_plan(pbf, q, "bf16x3"), phibf)
+    tg = np.sort(np.random.default_rng(5).choice(pts.shape[0], 500, replace=False))
+    assert rel(phibf[tg], direct.direct(pts, q, K, targets=tg)) < 1e-3
+    pbf.close()
+    p32.close()
