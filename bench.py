@@ -511,6 +511,7 @@ def main():
     tm = plan.timings(reset=True)
     plan.profile(False)
     launches_per_step = int(sum(tm["launches"].values()))
+    m2l_launches = int(tm["launches"]["M2L"])
 
     # ---- timed region: K steps, L2 flushed between steps, device time by CUDA events
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -602,10 +603,10 @@ def main():
     if offsets is None and info["top"]:
         wm = work_model(info, 16 if args.precision == "fp64" else 8)
         reps = nrhs * (2 if args.mode == "grad" else 1)
-        nl = info["nlev"] - info["top"] + 1
         ach = wm["M2L"]["flops"] * reps / (stage_ms["M2L"] / 1e3) / 1e12
-        roof.update({"achieved": ach, "frac": ach / fp32_peak, "launches_per_step": nl * reps,
-                     "work": "8 flops per complex MAC x sum over levels of nv_l K_l (per step, all launches)"})
+        roof.update({"achieved": ach, "frac": ach / fp32_peak, "launches_per_step": int(m2l_launches),
+                     "work": "8 flops per complex MAC x sum over levels of nv_l K_l (per step, all launches of "
+                             "k_m2l and k_m2l_tail)"})
         tr = measured_traffic(args.workload, args.precision, nrhs, args.mode)
         if tr is not None:
             roof["traffic"] = tr["bytes_per_step"]

@@ -517,6 +517,89 @@ static size_t m2l_smem() { return (size_t)2 * kTBoxRows * 32 * sizeof(C) + 128; 
 template <typename C, int NR>
 static int m2l_split(int64_t K) { return sizeof(C) == 8 && K >= 49152 ? 4 : 1; }
 
+// ---- the ragged last sample slice (K mod 32 = w samples, 0 < w <= 16, one right-hand side)
+// In k_m2l a warp walks a parent's whole list for one 32-sample slice, so a last slice holding
+// w valid samples leaves 32 - w lanes idle (on the 2^20 sphere's leaf level, K = 162: 2 of
+// 32).  Here lane (g, s) takes sample K - w + s of parent g among 32 / W parents per warp (W:
+// the smallest power of two >= w).  Each lane walks its own parent's list, so the warp runs the
+// longest of its parents' lists; the child count is a runtime bound over eight predicated
+// slots.  The slice of the operators (343 rows x W samples, zero past K) is staged with plain
+// loads.  Per sample the list order and the FMA sequence are those of k_m2l, so the results
+// are identical.
+constexpr int kM2LTailWarps = 8;
+
+template <typename C, int W>
+__global__ void __launch_bounds__(32 * kM2LTailWarps) k_m2l_tail(int64_t npar, const int* __restrict__ pcb,
+                                                                 const int* __restrict__ pce, const int* __restrict__ loff,
+                                                                 const unsigned long long* __restrict__ lsrc,
+                                                                 const uint64_t* __restrict__ ckey, const C* __restrict__ T,
+                                                                 const C* __restrict__ F, int64_t K, int w,
+                                                                 C* __restrict__ G) {
+    constexpr int PPW = 32 / W;                      // parents per warp
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* Ts = reinterpret_cast<C*>(smem_raw);          // [343][W]
+    const int64_t p0 = K - w;
+    for (int idx = threadIdx.x; idx < 343 * W; idx += blockDim.x) {
+        const int row = idx / W, sm = idx % W;
+        Ts[idx] = sm < w ? T[(int64_t)row * K + p0 + sm] : cmake<C>(0, 0);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / W, sm = lane % W;
+    const int64_t P = (int64_t)blockIdx.x * kM2LTailWarps * PPW + warp * PPW + g;
+    if (P >= npar) return;                           // no barrier below
+    const int t0 = pcb[P], nt = pce[P] - t0;
+    const int e0 = loff[P], ne = loff[P + 1] - e0;
+    const bool ok = sm < w;
+    int cr[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int ct = t < nt ? (int)(ckey[t0 + t] & 7) : 0;
+        cr[t] = ((ct & 1) + 7 * ((ct >> 1) & 1) + 49 * (ct >> 2)) * W;
+    }
+    C acc[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc[t] = cmake<C>(0, 0);
+    const C* Fp = F + p0 + (ok ? sm : 0);
+    const C* Tl = Ts + sm;
+    for (int j = 0; j < ne; ++j) {
+        const unsigned long long e = __ldg(lsrc + e0 + j);
+        const unsigned lo = (unsigned)e;
+        const C f = Fp[(unsigned)(e >> 32)];
+        const C* Tb = Tl + (lo & 511u) * W;
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (t < nt) cfma(acc[t], Tb[cr[t]], f);
+    }
+    if (ok) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (t < nt) G[(int64_t)(t0 + t) * K + p0 + sm] = acc[t];
+    }
+}
+
+// samples of the ragged last slice handled by k_m2l_tail (0: k_m2l takes every slice).  The
+// tail kernel pays only with many parents and a short ragged slice: each of its warps walks the
+// longest list of 32 / W parents serially, so on levels with few parents (long lists, few warps)
+// or with w = 8 it was slower than the idle lanes of k_m2l's last slice (2^20 sphere: leaf level,
+// w = 2, 69,745 parents: 0.925 -> 0.850 ms; w = 8 levels and the 56-parent level 4 lost 20-50 us
+// each).  Both kernels compute the same values, so the choice does not change results.
+template <typename C, int NR>
+static int m2l_tail(int64_t K, int64_t npar) {
+    const int w = (int)(K % 32);
+    return NR == 1 && m2l_split<C, NR>(K) == 1 && w <= 4 && npar >= 16384 ? w : 0;
+}
+
+template <typename C>
+static size_t m2l_tail_smem(int W) { return (size_t)343 * W * sizeof(C); }
+
+// kernel launches of one level's M2L
+template <typename C, int NR>
+static int m2l_launches(int64_t K, int64_t npar) {
+    const int w = m2l_tail<C, NR>(K, npar);
+    return (K >= 32 || !w ? 1 : 0) + (w ? 1 : 0);
+}
+
 template <typename R, typename C, int NR>
 static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
     constexpr int NW = M2LShape<C, NR>::NW;
@@ -524,13 +607,36 @@ static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
     const TreeLevel& T = p.lev[l];
     const TreeLevel& TP = p.lev[l - 1];
     const int Q = m2l_split<C, NR>(F.K);
-    const int ppc = Q > 1 ? NW / Q : NW * kM2LParentsPerWarp;
-    const size_t sm = m2l_smem<R, C>() + (Q > 1 ? (size_t)NW * 8 * NR * 32 * sizeof(C) : 0);
-    const dim3 grid(nblk(TP.nbox, ppc), nblk(F.K, 32));
-    k_m2l<R, C, NR, NW><<<grid, 32 * NW, sm, s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off, TP.m2l_src, T.key,
-                                                  F.tmT, (const C*)F.F, F.K, T.nbox * F.K, (C*)F.G, Q, p.dev_err,
-                                                  std::min(p.wait_first, kM2LWaitLimit));
-    MLFMA_LAUNCH_CHECK();
+    const int w = m2l_tail<C, NR>(F.K, TP.nbox);
+    const int64_t nslices = w ? F.K / 32 : (F.K + 31) / 32;
+    if (nslices > 0) {
+        const int ppc = Q > 1 ? NW / Q : NW * kM2LParentsPerWarp;
+        const size_t sm = m2l_smem<R, C>() + (Q > 1 ? (size_t)NW * 8 * NR * 32 * sizeof(C) : 0);
+        const dim3 grid(nblk(TP.nbox, ppc), (unsigned)nslices);
+        k_m2l<R, C, NR, NW><<<grid, 32 * NW, sm, s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off, TP.m2l_src,
+                                                      T.key, F.tmT, (const C*)F.F, F.K, T.nbox * F.K, (C*)F.G, Q,
+                                                      p.dev_err, std::min(p.wait_first, kM2LWaitLimit));
+        MLFMA_LAUNCH_CHECK();
+    }
+    if (w) {
+        int W = 2;
+        while (W < w) W *= 2;
+        const int ppb = kM2LTailWarps * (32 / W);
+        const size_t sm = m2l_tail_smem<C>(W);
+        const unsigned nb = (unsigned)nblk(TP.nbox, ppb);
+        switch (W) {
+#define M2L_TAIL(v)                                                                                                  \
+    case v:                                                                                                          \
+        k_m2l_tail<C, v><<<nb, 32 * kM2LTailWarps, sm, s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off,       \
+                                                            TP.m2l_src, T.key, (const C*)F.T, (const C*)F.F, F.K, w, \
+                                                            (C*)F.G);                                                \
+        break;
+            M2L_TAIL(2) M2L_TAIL(4) M2L_TAIL(8) M2L_TAIL(16)
+#undef M2L_TAIL
+            default: fail(MLFMA_ERR_INVALID_ARG, "tail width %d", W);
+        }
+        MLFMA_LAUNCH_CHECK();
+    }
 }
 
 // raise the dynamic shared-memory limit of the M2L kernel once (before any capture)
@@ -1288,7 +1394,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         TreeLevel& T = p.lev[l];
         TreeLevel& TP = p.lev[l - 1];
         {
-            StageTimer st(p, MLFMA_STAGE_M2L, l, 1);
+            StageTimer st(p, MLFMA_STAGE_M2L, l, m2l_launches<C, NR>(F.K, TP.nbox));
             launch_m2l<R, C, NR>(p, l, s);
         }
         if (l > p.top) {
@@ -1397,6 +1503,7 @@ void prepare_kernels(Plan& p) {
     if (p.prec == MLFMA_PREC_FP64) {
         allow_max_smem(k_m2l<double, double2, 1, M2LShape<double2, 1>::NW>);
         allow_max_smem(k_m2l<double, double2, kMaxNR, M2LShape<double2, kMaxNR>::NW>);
+        allow_max_smem(k_m2l_tail<double2, 16>);
     } else {
         allow_max_smem(k_m2l<float, float2, 1, M2LShape<float2, 1>::NW>);
         allow_max_smem(k_m2l<float, float2, kMaxNR, M2LShape<float2, kMaxNR>::NW>);

@@ -66,6 +66,24 @@ def test_sphere1m_top_levels_against_oracle_stages(sphere1m):
     G4 = o.m2l(4, F[4])
     o.l2l(3, G[3], G4)
     assert rel(G[4], G4) < 1e-5
+    # the leaf level (K = 162: five full 32-sample slices and a ragged slice of two samples,
+    # taken by the tail kernel) on 400 sampled target boxes: their M2L sums from the exported
+    # F_9 plus the L2L of the exported G_8 to them
+    lev9, lev8 = o.tree.levels[9], o.tree.levels[8]
+    F9 = plan.export("F", 9).reshape(lev9.nbox, -1).astype(np.complex128)
+    G8 = plan.export("G", 8).reshape(lev8.nbox, -1).astype(np.complex128)
+    G9 = plan.export("G", 9).reshape(lev9.nbox, -1).astype(np.complex128)
+    tb = np.sort(np.random.default_rng(2003).choice(lev9.nbox, 400, replace=False))
+    offs, cols = o.V[9]
+    ref = np.zeros((tb.shape[0], F9.shape[1]), dtype=np.complex128)
+    for i, t in enumerate(tb):
+        for src in cols[offs[t]:offs[t + 1]]:
+            ref[i] += o.T(9, lev9.ijk[t] - lev9.ijk[src]) * F9[src]
+    par = lev9.parent[tb]
+    sh = np.conj(o.shift_m2m(8, lev9.center[tb] - lev8.center[par])) * G8[par]
+    ref += om.anterpolate(sh, o.grid[9], o.grid[8], o.A[8])
+    assert rel(G9[tb], ref) < 1e-5
+    assert rel(G9[tb][:, 160:], ref[:, 160:]) < 1e-5
     plan.close()
 
 
