@@ -175,6 +175,8 @@ struct FarLevel {                  // sampling grid, operators and signatures of
     // interpolation from level l+1 (child) to this level (parent); set when l+1 is far-field
     void* At = nullptr;            // [Lc+1][nth_c][nth_p] real: At[m][i][i'] = A_m[i'][i]
     void* Bt = nullptr;            // [Lc+1][nth_p][nth_c] real: Bt[m][i'][i] = A_m[i'][i] w'_i' / w_i
+    void* AtTc = nullptr;          // tensor-core precisions: At and Bt split into hi + lo parts, in the
+    void* BtTc = nullptr;          // blocks the MMA reads (one per mode, output tile and K chunk)
     void* Sz = nullptr;            // [2][nth] complex: e^{-ik cos(theta_i') dz}, dz = -+ edge/4
     void* Sxy = nullptr;           // [4][K] complex: e^{-ik sin(theta)(cos(phi) dx + sin(phi) dy)}
     void* X = nullptr;             // [nbox(l+1)][2Lc+1][nth_c] complex scratch (spectral, child grid)
@@ -295,8 +297,10 @@ bool forest_possible(const std::vector<Plan*>& subs);
 void build_forest(Plan& P);
 // theta_tc.cu: split-TF32 tensor-core theta maps (complex64 data)
 void prepare_theta_tc();
-void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const float* M, const float2* in,
+void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const void* Mtc, const float2* in,
                          float2* out, cudaStream_t s);
+size_t theta_tc_map_bytes(const Plan& p, int nmaps, int nin, int nout);
+void presplit_theta_tc(const Plan& p, int nmaps, int nin, int nout, const float* M, void* out, cudaStream_t s);
 // far.cu / near.cu
 // one right-hand side in sorted order; grads_r (nullable): [n][3] complex gradient of phi
 // nr right-hand sides per pass (1, or kMaxNR without gradients): q and phi r n apart

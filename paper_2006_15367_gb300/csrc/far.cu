@@ -855,19 +855,16 @@ __device__ __forceinline__ int parent_quadrants(int c0, int c1, const uint64_t* 
     return *s_nq;
 }
 
-// items a thread of the per-parent kernels gathers at once (all loads issued before use)
-constexpr int kGatherBatch = 4;
-
 // M2M last step, per parent P and tile of RT parent rows i' (the present xy-quadrants q are
 // transformed together):
 //   W_q[i'][m] = sum_{children c = (q, sz)} Sz[sz][i'] Y[mi][c][i']          (z part of the shift, per mode)
 //   F_P[i'][j'] = sum_q Sxy[q][i'][j'] sum_m W_q[i'][m] e^{+i m phi'_j'}     (inverse FFT, xy part of the shift)
-// dRT divides by RT, dqm by RT nm, dn by n.
+// dRT divides by RT, dn by n.
 template <typename C>
 __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict__ ce, const uint64_t* __restrict__ ckey,
                               int nbox_c, const C* __restrict__ Y, int Lc, int nthp, FftPlan fp, const C* __restrict__ tw,
-                              const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, FastDiv dRT, FastDiv dqm,
-                              FastDiv dn, C* __restrict__ Fp) {
+                              const C* __restrict__ Sz, const C* __restrict__ Sxy, int RT, FastDiv dRT, FastDiv dn,
+                              C* __restrict__ Fp) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_child[4][2];
     __shared__ int s_q[4], s_nq;
@@ -884,51 +881,56 @@ __global__ void k_m2m_fft_out(const int* __restrict__ cb, const int* __restrict_
     C* stw = buf1 + 4 * RT * pn;
     for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
     const int nq = parent_quadrants(c0, c1, ckey, s_child, s_q, &s_nq);
-    for (int idx = threadIdx.x; idx < nq * nr * pn; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
-    __syncthreads();
-    // rows of the qi-th present quadrant occupy buf0[(qi * nr + r) * pn ...]; items (qi, mi, r)
-    // in one loop, kGatherBatch of them per thread with all their loads issued first
-    const int tot = nq * RT * nm;
-    for (int i0b = 0; i0b < tot; i0b += kGatherBatch * blockDim.x) {
-        C ya[kGatherBatch], yz[kGatherBatch];
-        int dst[kGatherBatch], rr[kGatherBatch];
+    // rows of the qi-th present quadrant occupy buf0[(qi * nr + r) * pn ...].  A thread takes a
+    // (mode, row) item for every present quadrant at once: its z-shift factors and index
+    // arithmetic serve them all, and the child indices come from registers; the loads of all
+    // quadrants are issued before use.  The columns of the modes beyond Lc are zeroed apart
+    // (disjoint from the mode columns, so no barrier between the two).
+    int qa[4], qz[4];
 #pragma unroll
-        for (int u = 0; u < kGatherBatch; ++u) {
-            const int idx = i0b + u * blockDim.x + threadIdx.x;
-            ya[u] = yz[u] = cmake<C>(0, 0);
-            dst[u] = -1;
-            rr[u] = 0;
-            if (idx < tot) {
-                const int qi = (int)dqm.div((unsigned)idx), rem = idx - qi * RT * nm;
-                const int mi = (int)dRT.div((unsigned)rem), r = rem - mi * RT;
-                if (r < nr) {
-                    const int q = s_q[qi];
-                    const int ca = s_child[q][0], cz = s_child[q][1];
-                    const C* Ym = Y + (int64_t)mi * nbox_c * nthp + i0 + r;
-                    if (ca >= 0) ya[u] = Ym[(int64_t)ca * nthp];
-                    if (cz >= 0) yz[u] = Ym[(int64_t)cz * nthp];
-                    dst[u] = (qi * nr + r) * pn + wrap(mi - Lc, n);
-                    rr[u] = r;
-                }
-            }
+    for (int qi = 0; qi < 4; ++qi) {
+        const int q = qi < nq ? s_q[qi] : 0;
+        qa[qi] = qi < nq ? s_child[q][0] : -1;
+        qz[qi] = qi < nq ? s_child[q][1] : -1;
+    }
+    for (int idx = threadIdx.x; idx < nm * RT; idx += blockDim.x) {
+        const int mi = (int)dRT.div((unsigned)idx), r = idx - mi * RT;
+        if (r >= nr) continue;
+        const C sz0 = Sz[i0 + r], sz1 = Sz[nthp + i0 + r];
+        const C* Ym = Y + (int64_t)mi * nbox_c * nthp + i0 + r;
+        C ya[4], yz[4];
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi) {
+            ya[qi] = qa[qi] >= 0 ? Ym[(int64_t)qa[qi] * nthp] : cmake<C>(0, 0);
+            yz[qi] = qz[qi] >= 0 ? Ym[(int64_t)qz[qi] * nthp] : cmake<C>(0, 0);
         }
+        C* dst = buf0 + r * pn + wrap(mi - Lc, n);
 #pragma unroll
-        for (int u = 0; u < kGatherBatch; ++u)
-            if (dst[u] >= 0) {
+        for (int qi = 0; qi < 4; ++qi)
+            if (qi < nq) {
                 C w = cmake<C>(0, 0);
-                cfma(w, Sz[i0 + rr[u]], ya[u]);
-                cfma(w, Sz[nthp + i0 + rr[u]], yz[u]);
-                buf0[dst[u]] = w;
+                cfma(w, sz0, ya[qi]);
+                cfma(w, sz1, yz[qi]);
+                dst[qi * nr * pn] = w;
             }
+    }
+    const int nz = n - nm;                        // columns Lc + 1 .. n - Lc - 1
+    for (int idx = threadIdx.x; idx < nq * nr * nz; idx += blockDim.x) {
+        const int row = idx / nz, k = idx - row * nz;
+        buf0[row * pn + Lc + 1 + k] = cmake<C>(0, 0);
     }
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true, pn);
+    const C* sxy[4];                                  // xy-shift tables of the present quadrants, from row i0
+#pragma unroll
+    for (int qi = 0; qi < 4; ++qi) sxy[qi] = Sxy + (int64_t)(qi < nq ? s_q[qi] : 0) * Kp + (int64_t)i0 * n;
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
         const int r = (int)dn.div((unsigned)idx), j = idx - r * n;
+        const C* rq = res + r * pn + j;
         C acc = cmake<C>(0, 0);
 #pragma unroll
         for (int qi = 0; qi < 4; ++qi)                  // fixed bound: the loads issue together
-            if (qi < nq) cfma(acc, Sxy[(int64_t)s_q[qi] * Kp + (int64_t)(i0 + r) * n + j], res[(qi * nr + r) * pn + j]);
+            if (qi < nq) cfma(acc, sxy[qi][idx], rq[qi * nr * pn]);
         Fp[(int64_t)P * Kp + (int64_t)i0 * n + idx] = acc;
     }
 }
@@ -963,27 +965,41 @@ __global__ void k_l2l_fft_in(const int* __restrict__ cb, const int* __restrict__
     const int nq = parent_quadrants(c0, c1, ckey, s_child, s_q, &s_nq);
     cp_async_wait_all();
     __syncthreads();
+    const C* sxy[4];                                  // xy-shift tables of the present quadrants, from row i0
+#pragma unroll
+    for (int qi = 0; qi < 4; ++qi) sxy[qi] = Sxy + (int64_t)(qi < nq ? s_q[qi] : 0) * Kp + (int64_t)i0 * n;
     for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
-        const int64_t g = (int64_t)i0 * n + idx;
         const C gv = buf1[idx];
         const int r = (int)dn.div((unsigned)idx), j = idx - r * n;
+        C* dst = buf0 + r * pn + j;
 #pragma unroll
         for (int qi = 0; qi < 4; ++qi)
-            if (qi < nq) buf0[(qi * nr + r) * pn + j] = cmul(cconj(Sxy[(int64_t)s_q[qi] * Kp + g]), gv);
+            if (qi < nq) dst[qi * nr * pn] = cmul(cconj(sxy[qi][idx]), gv);
     }
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nq * nr, fp, stw, true, pn);
-    for (int qi = 0; qi < nq; ++qi) {
-        const int q = s_q[qi];
-        const int ca = s_child[q][0], cz = s_child[q][1];
-        for (int idx = threadIdx.x; idx < RT * nm; idx += blockDim.x) {
-            const int mi = (int)dRT.div((unsigned)idx), r = idx - mi * RT;
-            if (r >= nr) continue;
-            C v = res[(qi * nr + r) * pn + wrap(mi - Lc, n)];
+    // a thread takes a (mode, row) item for every present quadrant: the z-shift factors and the
+    // index arithmetic serve them all, the child indices come from registers
+    int qa[4], qz[4];
+#pragma unroll
+    for (int qi = 0; qi < 4; ++qi) {
+        const int q = qi < nq ? s_q[qi] : 0;
+        qa[qi] = qi < nq ? s_child[q][0] : -1;
+        qz[qi] = qi < nq ? s_child[q][1] : -1;
+    }
+    for (int idx = threadIdx.x; idx < RT * nm; idx += blockDim.x) {
+        const int mi = (int)dRT.div((unsigned)idx), r = idx - mi * RT;
+        if (r >= nr) continue;
+        const C sz0 = cconj(Sz[i0 + r]), sz1 = cconj(Sz[nthp + i0 + r]);
+        const C* src = res + r * pn + wrap(mi - Lc, n);
+        C* Ym = Y + (int64_t)mi * nbox_c * nthp + i0 + r;
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi) {
+            if (qi >= nq) break;
+            C v = src[qi * nr * pn];
             v.x *= inv_n; v.y *= inv_n;
-            C* Ym = Y + (int64_t)mi * nbox_c * nthp;
-            if (ca >= 0) Ym[(int64_t)ca * nthp + i0 + r] = cmul(cconj(Sz[i0 + r]), v);
-            if (cz >= 0) Ym[(int64_t)cz * nthp + i0 + r] = cmul(cconj(Sz[nthp + i0 + r]), v);
+            if (qa[qi] >= 0) Ym[(int64_t)qa[qi] * nthp] = cmul(sz0, v);
+            if (qz[qi] >= 0) Ym[(int64_t)qz[qi] * nthp] = cmul(sz1, v);
         }
     }
 }
@@ -1029,10 +1045,10 @@ __global__ void k_l2l_fft_out(int nrows_tot, const C* __restrict__ H, int Lc, Ff
 constexpr int kMaxCPB = 16;
 
 // M2M first two steps:  Y[mi][c][i'] = scale sum_i At[|m|][i][i'] sum_j F[c][i][j] e^{-i m phi_j}.
-// dnthp divides by nthp.
+// dnh divides by (nthp + 1) / 2.
 template <typename C, typename R, int CPB>
 __global__ void k_m2m_in(int nbox_c, const C* __restrict__ F, int Lc, int nthc, int nthp, FftPlan fp,
-                         const C* __restrict__ tw, R scale, const R* __restrict__ At, FastDiv dnthp, C* __restrict__ Y) {
+                         const C* __restrict__ tw, R scale, const R* __restrict__ At, FastDiv dnh, C* __restrict__ Y) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
     // unpadded rows: no loop here walks across rows with consecutive threads
@@ -1049,34 +1065,45 @@ __global__ void k_m2m_in(int nbox_c, const C* __restrict__ F, int Lc, int nthc, 
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nr, fp, stw, false, n);
     const int rowc = nthc * n;                     // stride between children in res
-    for (int idx = threadIdx.x; idx < nm * nthp; idx += blockDim.x) {
-        const int mi = (int)dnthp.div((unsigned)idx), o = idx - mi * nthp;
+    // a thread takes output rows o and o + 1 of one mode: each spectral sample it reads from
+    // shared memory feeds both (the accumulation order of every output is unchanged)
+    const int nh = (nthp + 1) >> 1;
+    for (int idx = threadIdx.x; idx < nm * nh; idx += blockDim.x) {
+        const int mi = (int)dnh.div((unsigned)idx), o = 2 * (idx - mi * nh);
+        const bool two = o + 1 < nthp;
         const int m = abs(mi - Lc);
         const R* Am = At + (int64_t)m * nthc * nthp + o;
         const C* xr = res + wrap(mi - Lc, n);
-        C acc[CPB];
+        C acc0[CPB], acc1[CPB];
 #pragma unroll
-        for (int c = 0; c < CPB; ++c) acc[c] = cmake<C>(0, 0);
+        for (int c = 0; c < CPB; ++c) acc0[c] = acc1[c] = cmake<C>(0, 0);
         for (int i = 0; i < nthc; ++i) {
-            const R a = Am[i * nthp];
+            const R a0 = Am[i * nthp], a1 = two ? Am[i * nthp + 1] : (R)0;
             const C* xi = xr + i * n;
 #pragma unroll
             for (int c = 0; c < CPB; ++c)
-                if (c < ncb) crfma(acc[c], a, xi[c * rowc]);
+                if (c < ncb) {
+                    const C x = xi[c * rowc];
+                    crfma(acc0[c], a0, x);
+                    crfma(acc1[c], a1, x);
+                }
         }
         C* yo = Y + ((int64_t)mi * nbox_c + c0) * nthp + o;
 #pragma unroll
         for (int c = 0; c < CPB; ++c)
-            if (c < ncb) yo[c * nthp] = cmake<C>(acc[c].x * scale, acc[c].y * scale);
+            if (c < ncb) {
+                yo[c * nthp] = cmake<C>(acc0[c].x * scale, acc0[c].y * scale);
+                if (two) yo[c * nthp + 1] = cmake<C>(acc1[c].x * scale, acc1[c].y * scale);
+            }
     }
 }
 
 // L2L last two steps:  G[c][i][j] += sum_m e^{-i m phi_j} sum_i' Bt[|m|][i'][i] H[mi][c][i'].
-// The CTA's slice of H is staged in shared memory first.  dnthc divides by nthc, dhrow by
-// ncb nthp (dhfull: CPB nthp, the value for every CTA but the last).
+// The CTA's slice of H is staged in shared memory first.  dnh divides by (nthc + 1) / 2, dhrow
+// by ncb nthp (dhfull: CPB nthp, the value for every CTA but the last).
 template <typename C, typename R, int CPB>
 __global__ void k_l2l_out(int nbox_c, const C* __restrict__ H, int Lc, int nthc, int nthp, FftPlan fp,
-                          const C* __restrict__ tw, const R* __restrict__ Bt, FastDiv dnthc, FastDiv dhrow,
+                          const C* __restrict__ tw, const R* __restrict__ Bt, FastDiv dnh, FastDiv dhrow,
                           FastDiv dhfull, C* __restrict__ G) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
@@ -1097,24 +1124,34 @@ __global__ void k_l2l_out(int nbox_c, const C* __restrict__ H, int Lc, int nthc,
     for (int idx = threadIdx.x; idx < nr * pn; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
     cp_async_wait_all();
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nm * nthc; idx += blockDim.x) {
-        const int mi = (int)dnthc.div((unsigned)idx), i = idx - mi * nthc;
+    // a thread takes child rows i and i + 1 of one mode: each staged sample feeds both
+    const int nh = (nthc + 1) >> 1;
+    for (int idx = threadIdx.x; idx < nm * nh; idx += blockDim.x) {
+        const int mi = (int)dnh.div((unsigned)idx), i = 2 * (idx - mi * nh);
+        const bool two = i + 1 < nthc;
         const int m = abs(mi - Lc);
         const R* Bm = Bt + (int64_t)m * nthp * nthc + i;
         const C* hm = hs + mi * hp;
-        C acc[CPB];
+        C acc0[CPB], acc1[CPB];
 #pragma unroll
-        for (int c = 0; c < CPB; ++c) acc[c] = cmake<C>(0, 0);
+        for (int c = 0; c < CPB; ++c) acc0[c] = acc1[c] = cmake<C>(0, 0);
         for (int ip = 0; ip < nthp; ++ip) {
-            const R b = Bm[ip * nthc];
+            const R b0 = Bm[ip * nthc], b1 = two ? Bm[ip * nthc + 1] : (R)0;
 #pragma unroll
             for (int c = 0; c < CPB; ++c)
-                if (c < ncb) crfma(acc[c], b, hm[c * nthp + ip]);
+                if (c < ncb) {
+                    const C h = hm[c * nthp + ip];
+                    crfma(acc0[c], b0, h);
+                    crfma(acc1[c], b1, h);
+                }
         }
         const int col = wrap(mi - Lc, n);
 #pragma unroll
         for (int c = 0; c < CPB; ++c)
-            if (c < ncb) buf0[(c * nthc + i) * pn + col] = acc[c];
+            if (c < ncb) {
+                buf0[(c * nthc + i) * pn + col] = acc0[c];
+                if (two) buf0[(c * nthc + i + 1) * pn + col] = acc1[c];
+            }
     }
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nr, fp, stw, false, pn);
@@ -1163,7 +1200,7 @@ template <typename C, typename R>
 static void launch_m2m_in(int CPB, int nbox_c, const C* F, int Lc, int nthc, int nthp, const FftPlan& fp, const C* tw,
                           R scale, const R* At, C* Y, cudaStream_t s) {
     const size_t sm = ((size_t)2 * CPB * nthc * fp.n + fp.n) * sizeof(C);
-    const FastDiv d = FastDiv::make(nthp);
+    const FastDiv d = FastDiv::make((nthp + 1) / 2);
     switch (CPB) {
 #define M2M_IN(c) case c: k_m2m_in<C, R, c><<<nblk(nbox_c, c), 128, sm, s>>>(nbox_c, F, Lc, nthc, nthp, fp, tw, scale, At, d, Y); break;
         M2M_IN(2) M2M_IN(4) M2M_IN(8) M2M_IN(16)
@@ -1178,7 +1215,7 @@ static void launch_l2l_out(int CPB, int nbox_c, const C* H, int Lc, int nthc, in
                            const R* Bt, C* G, cudaStream_t s) {
     const size_t sm =
         ((size_t)CPB * (2 * nthc * (fp.n + 1) + (2 * Lc + 1) * nthp) + fp.n + (2 * Lc + 1)) * sizeof(C);
-    const FastDiv d = FastDiv::make(nthc);
+    const FastDiv d = FastDiv::make((nthc + 1) / 2);
     const int tail = nbox_c % CPB ? nbox_c % CPB : CPB;      // children of the last CTA
     const FastDiv dt = FastDiv::make(tail * nthp), df = FastDiv::make(CPB * nthp);
     switch (CPB) {
@@ -1270,8 +1307,7 @@ __global__ void __launch_bounds__(256) k_theta_map(int nbox, int Lc, int nin, in
         __syncthreads();
         const C* a = As + (ch & 1) * BK * AP;
         const R* bb = Bs + (ch & 1) * BK * BN;
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
+        auto mac = [&](int kk) {
             C av[4];
             R bv[4];
             ld4c(a + kk * AP + ty * 4, av);
@@ -1280,6 +1316,14 @@ __global__ void __launch_bounds__(256) k_theta_map(int nbox, int Lc, int nin, in
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) crfma(acc[i][j], bv[j], av[i]);
+        };
+        const int kc = nin - ch * BK;
+        if (kc >= BK) {
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) mac(kk);
+        } else {                                  // the last, partial chunk: skip its zero fill
+#pragma unroll 4
+            for (int kk = 0; kk < kc; ++kk) mac(kk);
         }
         __syncthreads();                          // the buffer is restaged two chunks later
     }
@@ -1296,12 +1340,13 @@ __global__ void __launch_bounds__(256) k_theta_map(int nbox, int Lc, int nin, in
     }
 }
 
+// Mtc: the pre-split form of M for the tensor-core precisions
 template <typename R, typename C>
-static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const R* M, const C* in, C* out,
-                             cudaStream_t s) {
+static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const R* M, const void* Mtc,
+                             const C* in, C* out, cudaStream_t s) {
     if constexpr (sizeof(C) == 8) {
         if (p.prec == MLFMA_PREC_FP32_TF32X3 || p.prec == MLFMA_PREC_FP32_BF16X3) {
-            launch_theta_map_tc(p, nbox, Lc, nin, nout, (const float*)M, (const float2*)in, (float2*)out, s);
+            launch_theta_map_tc(p, nbox, Lc, nin, nout, Mtc, (const float2*)in, (float2*)out, s);
             return;
         }
     }
@@ -1375,7 +1420,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
                                                                           (C*)F.X);
                 MLFMA_LAUNCH_CHECK();
                 // B: theta maps per mode
-                launch_theta_map<R, C>(p, TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, (const C*)F.X, (C*)F.Y, s);
+                launch_theta_map<R, C>(p, TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, F.AtTc, (const C*)F.X, (C*)F.Y,
+                                       s);
             }
             // C: z-shift per mode, inverse FFT, xy-shift, sum over children
             const int pbudget = (int)(p.tile_parent / sizeof(C));
@@ -1383,8 +1429,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
             sm = ((size_t)8 * RT * (F.nph + 1) + F.nph) * sizeof(C);
             k_m2m_fft_out<C><<<dim3((unsigned)T.nbox, nblk(F.nth, RT)), 128, sm, s>>>(
                 T.child_begin, T.child_end, TC.key, (int)TC.nbox, (const C*)F.Y, Lc, F.nth, F.fft, (const C*)F.tw,
-                (const C*)F.Sz, (const C*)F.Sxy, RT, FastDiv::make(RT), FastDiv::make(RT * (2 * Lc + 1)),
-                FastDiv::make(F.nph), Fp);
+                (const C*)F.Sz, (const C*)F.Sxy, RT, FastDiv::make(RT), FastDiv::make(F.nph), Fp);
             MLFMA_LAUNCH_CHECK();
         }
     }
@@ -1426,7 +1471,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
                     launch_l2l_out<C, R>(CPB, (int)T.nbox, (const C*)Pf.Y, Lc, F.nth, Pf.nth, F.fft, (const C*)F.tw,
                                          (const R*)Pf.Bt, Gc, s);
                 } else {
-                    launch_theta_map<R, C>(p, T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, (const C*)Pf.Y, (C*)Pf.X, s);
+                    launch_theta_map<R, C>(p, T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, Pf.BtTc, (const C*)Pf.Y,
+                                           (C*)Pf.X, s);
                     const int64_t rows_c = T.nbox * (int64_t)F.nth;
                     int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * (F.nph + 1));
                     sm = ((size_t)2 * RB * (F.nph + 1) + F.nph) * sizeof(C);

@@ -374,6 +374,13 @@ static void build_far_levels_t(Plan& p) {
         P.Bt = p.mem.make<R>(nA);
         k_interp<R><<<nblk(nA, 128), 128, 0, s>>>(Ch.L, Ch.x, Ch.wgl, P.nth, P.x, P.wgl, (R*)P.At, (R*)P.Bt);
         MLFMA_LAUNCH_CHECK();
+        if (p.prec == MLFMA_PREC_FP32_TF32X3 || p.prec == MLFMA_PREC_FP32_BF16X3) {
+            // the maps split once into the tensor-core operand blocks (At: nth_c -> nth_p, Bt: nth_p -> nth_c)
+            P.AtTc = p.mem.get(theta_tc_map_bytes(p, Ch.L + 1, Ch.nth, P.nth));
+            P.BtTc = p.mem.get(theta_tc_map_bytes(p, Ch.L + 1, P.nth, Ch.nth));
+            presplit_theta_tc(p, Ch.L + 1, Ch.nth, P.nth, (const float*)P.At, P.AtTc, s);
+            presplit_theta_tc(p, Ch.L + 1, P.nth, Ch.nth, (const float*)P.Bt, P.BtTc, s);
+        }
         P.Sz = p.mem.make<C>(2 * P.nth);
         P.Sxy = p.mem.make<C>(4 * P.K);
         k_shifts<C><<<nblk(4 * P.K, 256), 256, 0, s>>>(P.nth, P.nph, p.k, p.lev[l].edge, P.x, (C*)P.Sz, (C*)P.Sxy);
