@@ -1108,10 +1108,11 @@ __global__ void k_l2l_out(int nbox_c, const C* __restrict__ H, int Lc, int nthc,
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
     const int pn = n + 1, hp = CPB * nthp + 1;     // padded pitches of the FFT rows and of hs
+    // hs is read only by the theta map, before the FFT needs buf1: the two share their space
     C* buf0 = reinterpret_cast<C*>(smem_raw);
-    C* buf1 = buf0 + CPB * nthc * pn;
-    C* stw = buf1 + CPB * nthc * pn;
-    C* hs = stw + n;                               // [nm][hp]: the CPB children's rows of one mode
+    C* stw = buf0 + CPB * nthc * pn;
+    C* buf1 = stw + n;
+    C* hs = buf1;                                  // [nm][hp]: the CPB children's rows of one mode
     const int c0 = blockIdx.x * CPB;
     const int ncb = min(CPB, nbox_c - c0);
     const int nr = ncb * nthc;
@@ -1213,8 +1214,8 @@ static void launch_m2m_in(int CPB, int nbox_c, const C* F, int Lc, int nthc, int
 template <typename C, typename R>
 static void launch_l2l_out(int CPB, int nbox_c, const C* H, int Lc, int nthc, int nthp, const FftPlan& fp, const C* tw,
                            const R* Bt, C* G, cudaStream_t s) {
-    const size_t sm =
-        ((size_t)CPB * (2 * nthc * (fp.n + 1) + (2 * Lc + 1) * nthp) + fp.n + (2 * Lc + 1)) * sizeof(C);
+    const size_t rows = (size_t)CPB * nthc * (fp.n + 1), hsz = (size_t)(2 * Lc + 1) * (CPB * nthp + 1);
+    const size_t sm = (rows + fp.n + std::max(rows, hsz)) * sizeof(C);
     const FastDiv d = FastDiv::make((nthc + 1) / 2);
     const int tail = nbox_c % CPB ? nbox_c % CPB : CPB;      // children of the last CTA
     const FastDiv dt = FastDiv::make(tail * nthp), df = FastDiv::make(CPB * nthp);
