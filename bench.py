@@ -234,6 +234,8 @@ WORKLOADS = {
     "sphere4k": "sphere N=4096 r=2 wavelengths (k=2pi), leaf 0.25 wavelength, 5 levels, 3 digits",
     "cubeclusters4m": "cube surface 32 wavelengths (70%) + 64 Gaussian clusters sigma 0.05 (30%), N=4194304, "
                       "adaptive leaf_max=64, far field down to 0.25-wavelength boxes, 4 digits",
+    "cubeclusters512k": "cube surface 32 wavelengths (70%) + 64 Gaussian clusters sigma 0.05 (30%), N=524288, "
+                        "adaptive leaf_max=64, far field down to 0.25-wavelength boxes, 4 digits",
     "ellipsoid256k": "ellipsoid (8,4,2) wavelengths N=262144, leaf 0.25 wavelength, 3 digits",
     "batch256": "256 random ellipsoids (semi-axes U(2,16) wavelengths, N log-uniform 1000..65536) in one batched "
                 "plan, leaf 0.25 wavelength, 3 digits",

@@ -170,4 +170,9 @@ def workload(name: str):
         pts = cube_surface_clusters(n, seed=3001)
         q = complex_normal(3002, n)
         return pts, q, dict(k=K_WAVE, digits=4, leaf_max=64)
+    if name == "cubeclusters512k":   # N = 524,288, the same construction (profiling-size case)
+        n = 1 << 19
+        pts = cube_surface_clusters(n, seed=3101)
+        q = complex_normal(3102, n)
+        return pts, q, dict(k=K_WAVE, digits=4, leaf_max=64)
     raise KeyError(name)
