@@ -301,12 +301,15 @@ def measure_forms(dev, pts, q, prm, fp32_ms):
 
     guarded("fp64", lambda: precision("fp64"))
     guarded("tf32x3", lambda: precision("tf32x3"))
+    guarded("bf16x3", lambda: precision("bf16x3"))
     if "ms" in out.get("fp64", {}):
         out["fp64"]["note"] = "plain FP64 path, same digits"
         out["fp32_speedup_vs_fp64"] = out["fp64"]["ms"] / fp32_ms
         if "ms" in out.get("tf32x3", {}):
             out["tf32x3_speedup_vs_fp64"] = out["fp64"]["ms"] / out["tf32x3"]["ms"]
             out["tf32x3_speedup_vs_fp32"] = fp32_ms / out["tf32x3"]["ms"]
+        if "ms" in out.get("bf16x3", {}):
+            out["bf16x3_speedup_vs_fp32"] = fp32_ms / out["bf16x3"]["ms"]
 
     def nrhs64():
         Q = synth.complex_normal(2003, n, nrhs=64).astype(np.complex64)
@@ -433,7 +436,7 @@ def main():
     ap.add_argument("--ncu", action="store_true",
                     help="profile-region mode: warm up, then run one step between cudaProfilerStart/Stop and exit")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32x3"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32x3", "bf16x3"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--digits", type=int, default=0, help="override the workload's digits (0: keep)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -646,7 +649,7 @@ def main():
         "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "c64 (fp32)", "fp64": "c128 (fp64)", "tf32x3": "c64 (fp32; theta maps split-tf32 x3 on "
-                  "tensor cores)"}[args.precision], "data": "synthetic", "config": cfg,
+                  "tensor cores)", "bf16x3": "c64 (fp32; theta maps split-bf16 x3 on tensor cores)"}[args.precision], "data": "synthetic", "config": cfg,
         "accuracy": {"rel_err_vs_fp64_direct": rel_err, "targets": int(sum(len(g[2]) for g in groups)),
                      "reference": "GPU FP64 direct sum"},
         "plan": {"levels": info["nlev"], "top": info["top"], "L": info["L"], "n_geom": info["n_geom"],

@@ -62,10 +62,12 @@ typedef enum {
     MLFMA_PREC_FP32_BF16X3 = 2,   /* as FP32_TF32X3 with BF16 operand parts (hi = x rounded to BF16,
                                      lo = x - hi rounded to BF16; kind::f16 MMAs at twice the TF32 rate):
                                      products good to about 2^-16 relative, enough for 4 digits */
-    MLFMA_PREC_FP32_TF32X3 = 3    /* as FP32, but the theta maps of the interpolation (Sec. 3.2.2) and
-                                     anterpolation (Sec. 3.2.4) on level pairs too large to fuse run on
-                                     the tensor cores as split-TF32 GEMMs (x = hi + lo, products hi*hi +
-                                     hi*lo + lo*hi accumulated in FP32): FP32-level accuracy */
+    MLFMA_PREC_FP32_TF32X3 = 3    /* as FP32, but the interpolation (Sec. 3.2.2) and anterpolation
+                                     (Sec. 3.2.4) run on the tensor cores as split-TF32 GEMMs (x = hi + lo,
+                                     products hi*hi + hi*lo + lo*hi accumulated in FP32): the theta maps
+                                     between the phi transforms of the level pairs too large to fuse, or
+                                     whole dense maps on the fine pairs (mlfma_options.dense_samples).
+                                     FP32-level accuracy */
 } mlfma_precision;
 
 /* Options of mlfma_plan_create.  Initialise with mlfma_options_init(). */
@@ -106,6 +108,14 @@ typedef struct mlfma_options {
                                      for its own copies in flight with the normal limit, raises the
                                      plan's error flag and returns, so MLFMA_ERR_TIMEOUT can be
                                      exercised without a stalled GPU */
+    int dense_samples;            /* tensor-core precisions (TF32X3, BF16X3), opt-in: a level pair whose
+                                     child sampling grid has at most this many samples runs its
+                                     interpolation (M2M) and anterpolation (L2L) each as one dense real
+                                     map on the tensor cores, the phi transforms, theta maps and shifts
+                                     folded into it (Sec. 3.2.2, 3.2.4), in persistent kernels that keep
+                                     a slice of the map in shared memory.  0 (default) or -1: never (the
+                                     FFT path with tensor-core theta maps runs everywhere).  Ignored by
+                                     FP32 and FP64 plans */
 } mlfma_options;
 
 /* Summary of a plan (levels are numbered from the root, level 1). */
@@ -130,6 +140,8 @@ typedef struct mlfma_info {
     int tile_bytes[3];                       /* shared-memory budgets of the interpolation tiles in use:
                                                 row tiles, per-parent tiles, fused level pairs */
     int recompute_signatures;                /* the plan's mlfma_options.recompute_signatures */
+    int dense[MLFMA_MAX_LEVELS + 1];         /* 1 where the level pair (l, l + 1) runs as dense tensor-core
+                                                maps (mlfma_options.dense_samples) */
 } mlfma_info;
 
 /* Tree and list arrays that mlfma_plan_export can copy out (for verification). */

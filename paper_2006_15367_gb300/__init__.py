@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("precision", ctypes.c_int), ("leaf_edge", ctypes.c_double),
                 ("max_depth", ctypes.c_int), ("digit_margin", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("disable_graphs", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("recompute_signatures", ctypes.c_int), ("test_fail_waits", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("recompute_signatures", ctypes.c_int), ("test_fail_waits", ctypes.c_int),
+                ("dense_samples", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -49,7 +50,8 @@ class Info(ctypes.Structure):
                 ("nleaf", ctypes.c_int64 * (MAX_LEVELS + 1)), ("L", ctypes.c_int * (MAX_LEVELS + 1)),
                 ("K", ctypes.c_int64 * (MAX_LEVELS + 1)), ("nv", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("near_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
-                ("n_geom", ctypes.c_int), ("tile_bytes", ctypes.c_int * 3), ("recompute_signatures", ctypes.c_int)]
+                ("n_geom", ctypes.c_int), ("tile_bytes", ctypes.c_int * 3), ("recompute_signatures", ctypes.c_int),
+                ("dense", ctypes.c_int * (MAX_LEVELS + 1))]
 
 
 STAGES = ["PERMUTE", "P2P", "C2M", "M2M", "M2L", "L2L", "L2O"]
@@ -273,8 +275,11 @@ class Plan:
 
     points    [n, 3] float64 (torch tensor on a CUDA device, or host array)
     k         wavenumber; digits: requested accuracy; leaf_max: 0 = level-uniform tree
-    precision "fp32" (complex64 data), "fp64" (complex128 data) or "tf32x3" (complex64 data, theta
-              maps of the large level pairs on the tensor cores as split-TF32 GEMMs)
+    precision "fp32" (complex64 data), "fp64" (complex128 data), "tf32x3" or "bf16x3" (complex64
+              data, the theta maps of the large level pairs on the tensor cores as split-TF32 /
+              split-BF16 GEMMs)
+    dense_samples  tensor-core precisions, opt-in: level pairs whose child grid has at most this many
+              samples run as dense maps (0: never; mlfma_options.dense_samples)
     offsets   concatenated geometries: offsets[g] .. offsets[g + 1] are geometry g's points (one
               batched plan; the matrix is block diagonal)
     graphs    replay the apply as a captured CUDA graph (default) or launch the kernels each time
@@ -292,7 +297,7 @@ class Plan:
 
     def __init__(self, points, k, digits=3, leaf_max=0, precision="fp32", leaf_edge=0.0, max_depth=12,
                  digit_margin=-1, stream=None, use_torch_allocator=True, offsets=None, graphs=True, autotune=False,
-                 recompute_signatures=False, test_fail_waits=False, allocator=None):
+                 recompute_signatures=False, test_fail_waits=False, allocator=None, dense_samples=0):
         import torch
         self.torch = torch
         load()
@@ -320,6 +325,7 @@ class Plan:
             o.autotune = 1 if autotune else 0
             o.recompute_signatures = 1 if recompute_signatures else 0
             o.test_fail_waits = 1 if test_fail_waits else 0
+            o.dense_samples = int(dense_samples)
             self._alloc = None
             if allocator is not None:
                 self._alloc = allocator
@@ -409,7 +415,8 @@ class Plan:
                     nbox=list(i.nbox[:nl + 1]), nleaf=list(i.nleaf[:nl + 1]), L=list(i.L[:nl + 1]),
                     K=list(i.K[:nl + 1]), nv=list(i.nv[:nl + 1]), near_pairs=i.near_pairs,
                     device_bytes=i.device_bytes, setup_ms=i.setup_ms, n_geom=i.n_geom,
-                    tile_bytes=list(i.tile_bytes), recompute_signatures=bool(i.recompute_signatures))
+                    tile_bytes=list(i.tile_bytes), recompute_signatures=bool(i.recompute_signatures),
+                    dense=list(i.dense[:nl + 1]))
 
     def export(self, item, level=0):
         """Copies a tree/list/signature array to a host numpy array."""

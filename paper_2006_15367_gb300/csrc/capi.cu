@@ -487,6 +487,7 @@ static mlfma_options checked_options(const mlfma_options* opt, double k, int dig
     if (o.recompute_signatures != 0 && o.recompute_signatures != 1)
         fail(MLFMA_ERR_INVALID_ARG, "recompute_signatures must be 0 or 1");
     if (o.test_fail_waits != 0 && o.test_fail_waits != 1) fail(MLFMA_ERR_INVALID_ARG, "test_fail_waits must be 0 or 1");
+    if (o.dense_samples < -1) fail(MLFMA_ERR_INVALID_ARG, "dense_samples must be >= -1");
     return o;
 }
 
@@ -508,6 +509,7 @@ static void configure(Plan& p, int64_t n, double k, int digits, int leaf_max, co
     p.mem.stream = p.stream;
     p.wait_first = o.test_fail_waits ? 0 : (1ll << 22);
     p.recompute = o.recompute_signatures ? 1 : 0;
+    p.dense_kc = o.dense_samples > 0 ? o.dense_samples : 0;
 }
 
 // tree, lists, grids and operators of one point set (device points)
@@ -679,6 +681,7 @@ mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info) {
         info->tile_bytes[2] = p.tile_fused;
         info->n_geom = p.subs.empty() ? 1 : (int)p.subs.size();
         info->recompute_signatures = p.recompute;
+        for (int l = 0; l <= kMaxLev; ++l) info->dense[l] = p.far[l].dense;
         if (p.forest) {                                // the merged levels (height above the leaves)
             for (const Plan* sp : p.subs) info->device_bytes += (int64_t)sp->mem.bytes;
         } else if (!p.subs.empty()) {

@@ -177,6 +177,13 @@ struct FarLevel {                  // sampling grid, operators and signatures of
     void* Bt = nullptr;            // [Lc+1][nth_p][nth_c] real: Bt[m][i'][i] = A_m[i'][i] w'_i' / w_i
     void* AtTc = nullptr;          // tensor-core precisions: At and Bt split into hi + lo parts, in the
     void* BtTc = nullptr;          // blocks the MMA reads (one per mode, output tile and K chunk)
+    // tensor-core precisions, fine level pairs: the whole interpolation (anterpolation) of the
+    // pair as one real Kp x Kc (Kc x Kp) matrix, split into the MMA's operand blocks, and the
+    // children's shifts by octant
+    int dense = 0;
+    void* DmTc = nullptr;          // M2M: Pm (child samples -> parent samples)
+    void* DlTc = nullptr;          // L2L: Qm (parent samples -> child samples)
+    void* Soct = nullptr;          // [8][K] complex: Sz[o >> 2][i'] Sxy[o & 3][i'][j']
     void* Sz = nullptr;            // [2][nth] complex: e^{-ik cos(theta_i') dz}, dz = -+ edge/4
     void* Sxy = nullptr;           // [4][K] complex: e^{-ik sin(theta)(cos(phi) dx + sin(phi) dy)}
     void* X = nullptr;             // [nbox(l+1)][2Lc+1][nth_c] complex scratch (spectral, child grid)
@@ -247,6 +254,9 @@ struct Plan {
     // kernels, fused level pairs; defaults from sweeps on a 2^20-point sphere, or chosen by the
     // plan-time autotuner
     int tile_fft = 20 * 1024, tile_parent = 32 * 1024, tile_fused = 40 * 1024;
+    // tensor-core precisions: level pairs whose child grid has at most this many samples run
+    // as dense maps (0: never, the default)
+    int dense_kc = 0;
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::map<int64_t, cudaGraphExec_t> graphs;
@@ -300,6 +310,15 @@ void prepare_theta_tc();
 void launch_theta_map_tc(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const void* Mtc, const float2* in,
                          float2* out, cudaStream_t s);
 size_t theta_tc_map_bytes(const Plan& p, int nmaps, int nin, int nout);
+// dense_tc.cu: fine level pairs as dense tensor-core maps (persistent kernels)
+void prepare_dense_tc();
+bool dense_tc_fits(const Plan& p, int Kc, int Kp);
+size_t dense_tc_map_bytes(const Plan& p, bool m2m, int K, int Nout);
+void presplit_dense_tc(const Plan& p, bool m2m, int K, int Nout, const float* M, void* out, cudaStream_t s);
+void launch_dense_m2m_tc(const Plan& p, int64_t nbox_c, int Kc, int Kp, const void* Mtc, const int* par,
+                         const uint64_t* ckey, const float2* soct, const float2* Fc, float2* Fp, cudaStream_t s);
+void launch_dense_l2l_tc(const Plan& p, int64_t nbox_c, int Kp, int Kc, const void* Mtc, const int* par,
+                         const uint64_t* ckey, const float2* soct, const float2* Gp, float2* Gc, cudaStream_t s);
 void presplit_theta_tc(const Plan& p, int nmaps, int nin, int nout, const float* M, void* out, cudaStream_t s);
 // far.cu / near.cu
 // one right-hand side in sorted order; grads_r (nullable): [n][3] complex gradient of phi

@@ -1518,6 +1518,14 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
         if (l == p.nlev) continue;
         FarLevel& Ch = p.far[l + 1];
         TreeLevel& TC = p.lev[l + 1];
+        if (F.dense) {
+            // fine pair on the tensor cores: one dense map per right-hand side
+            StageTimer st(p, MLFMA_STAGE_M2M, l, NR);
+            for (int r = 0; r < NR; ++r)
+                launch_dense_m2m_tc(p, TC.nbox, (int)Ch.K, (int)F.K, F.DmTc, TC.parent, TC.key, (const float2*)F.Soct,
+                                    (const float2*)Ch.F + r * sF(l + 1), (float2*)F.F + r * sF(l), s);
+            continue;
+        }
         const int Lc = Ch.L;
         const int64_t rows_c = TC.nbox * (int64_t)Ch.nth;
         const int budget = (int)(p.tile_fft / sizeof(C));
@@ -1571,7 +1579,14 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
             StageTimer st(p, MLFMA_STAGE_M2L, l, m2l_launches<C, NR>(F.K, TP.nbox));
             launch_m2l<R, C, NR>(p, l, s);
         }
-        if (l > p.top) {
+        if (l > p.top && p.far[l - 1].dense) {
+            // fine pair on the tensor cores: one dense map per right-hand side, added to G
+            FarLevel& Pf = p.far[l - 1];
+            StageTimer st(p, MLFMA_STAGE_L2L, l, NR);
+            for (int r = 0; r < NR; ++r)
+                launch_dense_l2l_tc(p, T.nbox, (int)Pf.K, (int)F.K, Pf.DlTc, T.parent, T.key, (const float2*)Pf.Soct,
+                                    (const float2*)Pf.G + r * sF(l - 1), (float2*)F.G + r * sF(l), s);
+        } else if (l > p.top) {
             FarLevel& Pf = p.far[l - 1];
             const int Lc = F.L;
             const int CPB =
@@ -1686,7 +1701,10 @@ static void prepare_fft_kernels() {
 void prepare_kernels(Plan& p) {
     if (p.prec == MLFMA_PREC_FP64) prepare_fft_kernels<double2, double>();
     else prepare_fft_kernels<float2, float>();
-    if (p.prec == MLFMA_PREC_FP32_TF32X3 || p.prec == MLFMA_PREC_FP32_BF16X3) prepare_theta_tc();
+    if (p.prec == MLFMA_PREC_FP32_TF32X3 || p.prec == MLFMA_PREC_FP32_BF16X3) {
+        prepare_theta_tc();
+        prepare_dense_tc();
+    }
     if (p.prec == MLFMA_PREC_FP64) {
         allow_max_smem(k_m2l<double, double2, 1, M2LShape<double2, 1>::NW>);
         allow_max_smem(k_m2l<double, double2, kMaxNR, M2LShape<double2, kMaxNR>::NW>);

@@ -28,6 +28,13 @@ __global__ void k_copy_add(int* __restrict__ dst, const int* __restrict__ src, i
     if (i < n) dst[i] = src[i] + add;
 }
 
+// parent indices moved into the forest's parent level (add < 0: the parent level is not in the
+// forest, every box is parentless)
+__global__ void k_copy_parent(int* __restrict__ dst, const int* __restrict__ src, int64_t n, int add) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (add < 0 || src[i] < 0) ? -1 : src[i] + add;
+}
+
 __global__ void k_fill(int* __restrict__ dst, int64_t n, int v) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) dst[i] = v;
@@ -134,6 +141,7 @@ void build_forest(Plan& P) {
         T.end = P.mem.make<int>(std::max<int64_t>(nb, 1));
         T.child_begin = P.mem.make<int>(std::max<int64_t>(nb, 1));
         T.child_end = P.mem.make<int>(std::max<int64_t>(nb, 1));
+        T.parent = P.mem.make<int>(std::max<int64_t>(nb, 1));
         T.center = P.mem.make<double>(3 * std::max<int64_t>(nb, 1));
         T.m2l_off = P.mem.make<int>(nb + 1);
         int64_t n_small = 0, n_big = 0, n_tiles = 0, m2l_n = 0;
@@ -172,6 +180,8 @@ void build_forest(Plan& P) {
                 const int cadd = lg < sp.nlev ? (int)boff[g][l + 1] : 0;
                 k_copy_add<<<nblk(nbs, 256), 256, 0, s>>>(T.child_begin + bo, S.child_begin, nbs, cadd);
                 k_copy_add<<<nblk(nbs, 256), 256, 0, s>>>(T.child_end + bo, S.child_end, nbs, cadd);
+                k_copy_parent<<<nblk(nbs, 256), 256, 0, s>>>(T.parent + bo, S.parent, nbs,
+                                                             l > 1 && inc(g, l - 1) ? (int)boff[g][l - 1] : -1);
                 MLFMA_LAUNCH_CHECK();
                 // M2L lists of this level as parent level (sources are children at level l + 1)
                 if (S.m2l_off && S.m2l_n > 0) {
@@ -335,7 +345,7 @@ void build_forest(Plan& P) {
     std::vector<const void*> keep;
     for (int l = P.top ? P.top : 1; P.top && l <= Lmax; ++l) {
         const FarLevel& F = P.far[l];
-        const void* used[] = {F.x, F.wgl, F.dirs, F.tw, F.T, F.At, F.Bt, F.AtTc, F.BtTc, F.Sz, F.Sxy};
+        const void* used[] = {F.x, F.wgl, F.dirs, F.tw, F.T, F.At, F.Bt, F.AtTc, F.BtTc, F.DmTc, F.DlTc, F.Soct, F.Sz, F.Sxy};
         for (const void* q : used)
             if (q) keep.push_back(q);
     }

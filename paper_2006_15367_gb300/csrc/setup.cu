@@ -313,6 +313,46 @@ __global__ void k_shifts(int nth, int nph, double k, double edge, const double* 
     }
 }
 
+// Dense maps of a level pair (tensor-core precisions, fine levels): the forward phi transform
+// of the child grid, the theta maps of every mode and the inverse phi transform of the parent
+// grid composed into one real matrix each way,
+//   Mp[(i,j)][(i',j')] = (1/n_c) sum_{|m| <= Lc} At[|m|][i][i'] cos(2 pi m (j'/n_p - j/n_c))   (M2M, [Kc][Kp])
+//   Mq[(i',j')][(i,j)] = (1/n_p) sum_{|m| <= Lc} Bt[|m|][i'][i] cos(2 pi m (j'/n_p - j/n_c))   (L2L, [Kp][Kc])
+// the same operators as the FFT path (whose mode m and -m terms are complex conjugates).  The
+// phases are reduced with integer residues m j mod n; FP64 sums.
+__global__ void k_dense_maps(int Lc, int nthc, int nphc, int nthp, int nphp, const float* __restrict__ At,
+                             const float* __restrict__ Bt, float* __restrict__ Mp, float* __restrict__ Mq) {
+    const int64_t Kc = (int64_t)nthc * nphc, Kp = (int64_t)nthp * nphp;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= Kc * Kp) return;
+    const int64_t kc = idx / Kp, sp = idx - kc * Kp;
+    const int i = (int)(kc / nphc), j = (int)(kc % nphc);
+    const int ip = (int)(sp / nphp), jp = (int)(sp % nphp);
+    double sa = 0, sb = 0;
+    for (int m = -Lc; m <= Lc; ++m) {
+        const int am = m < 0 ? -m : m;
+        int rp = (int)(((int64_t)m * jp) % nphp), rc = (int)(((int64_t)m * j) % nphc);
+        if (rp < 0) rp += nphp;
+        if (rc < 0) rc += nphc;
+        const double c = cospi(2.0 * ((double)rp / nphp - (double)rc / nphc));
+        sa += (double)At[((int64_t)am * nthc + i) * nthp + ip] * c;
+        sb += (double)Bt[((int64_t)am * nthp + ip) * nthc + i] * c;
+    }
+    Mp[kc * Kp + sp] = (float)(sa / nphc);
+    Mq[sp * Kc + kc] = (float)(sb / nphp);
+}
+
+// the children's shifts by octant o: So[o][i'][j'] = Sz[o >> 2][i'] Sxy[o & 3][i'][j']
+template <typename C>
+__global__ void k_soct(int nth, int nph, const C* __restrict__ Sz, const C* __restrict__ Sxy, C* __restrict__ So) {
+    const int64_t K = (int64_t)nth * nph;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= 8 * K) return;
+    const int o = (int)(idx / K);
+    const int64_t sp = idx - o * K;
+    So[idx] = cmul(Sz[(o >> 2) * nth + sp / nph], Sxy[(o & 3) * K + sp]);
+}
+
 static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 template <typename R>
@@ -385,6 +425,27 @@ static void build_far_levels_t(Plan& p) {
         P.Sxy = p.mem.make<C>(4 * P.K);
         k_shifts<C><<<nblk(4 * P.K, 256), 256, 0, s>>>(P.nth, P.nph, p.k, p.lev[l].edge, P.x, (C*)P.Sz, (C*)P.Sxy);
         MLFMA_LAUNCH_CHECK();
+        if ((p.prec == MLFMA_PREC_FP32_TF32X3 || p.prec == MLFMA_PREC_FP32_BF16X3) && Ch.K <= p.dense_kc &&
+            dense_tc_fits(p, (int)Ch.K, (int)P.K)) {
+            // fine pair: the whole interpolation and anterpolation as dense tensor-core maps
+            P.dense = 1;
+            const int64_t nKK = Ch.K * P.K;
+            float* Mp = p.mem.make<float>(nKK);
+            float* Mq = p.mem.make<float>(nKK);
+            k_dense_maps<<<nblk(nKK, 128), 128, 0, s>>>(Ch.L, Ch.nth, Ch.nph, P.nth, P.nph, (const float*)P.At,
+                                                          (const float*)P.Bt, Mp, Mq);
+            MLFMA_LAUNCH_CHECK();
+            P.DmTc = p.mem.get(dense_tc_map_bytes(p, true, (int)Ch.K, (int)P.K));
+            P.DlTc = p.mem.get(dense_tc_map_bytes(p, false, (int)P.K, (int)Ch.K));
+            presplit_dense_tc(p, true, (int)Ch.K, (int)P.K, Mp, P.DmTc, s);
+            presplit_dense_tc(p, false, (int)P.K, (int)Ch.K, Mq, P.DlTc, s);
+            P.Soct = p.mem.make<C>(8 * P.K);
+            k_soct<C><<<nblk(8 * P.K, 256), 256, 0, s>>>(P.nth, P.nph, (const C*)P.Sz, (const C*)P.Sxy, (C*)P.Soct);
+            MLFMA_LAUNCH_CHECK();
+            MLFMA_CUDA(cudaStreamSynchronize(s));      // the unsplit maps are temporaries
+            p.mem.drop(Mq);
+            p.mem.drop(Mp);
+        }
     }
     // spectral scratch shared by all level pairs: X [nbox_c][2Lc+1][nth_c], Y [nbox_c][2Lc+1][nth_p]
     size_t xs = 0, ys = 0;

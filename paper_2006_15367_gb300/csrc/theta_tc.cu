@@ -26,11 +26,10 @@
 // through shared memory as whole output rows.  Every wait has an iteration limit after which the
 // kernel raises the plan's error flag, waits (normal limit) for its copies and MMAs in flight,
 // releases its tensor memory and returns.
-#include <cuda_bf16.h>
-
 #include <algorithm>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace mlfma {
 
@@ -45,107 +44,30 @@ constexpr uint32_t kABytes = kTcM * kTcRowBytes;          // one part of the A c
 constexpr uint32_t kBBytesMax = kTcMaxN * kTcRowBytes;    // one part of the widest B chunk (32 KB)
 // two stages of (A hi, A lo, B hi, B lo): 192 KB at the widest B
 constexpr size_t kTcSmemMax = 2 * (2 * (size_t)kABytes + 2 * (size_t)kBBytesMax);
-constexpr long long kWaitLimit = 1ll << 22;
+using tc::mbar_init;
+using tc::mbar_wait;
+using tc::SplitBF16;
+using tc::SplitTF32;
+using tc::smem_u32;
+using tc::st_part;
+using tc::tmem_ld16;
+constexpr long long kWaitLimit = tc::kWaitLimit;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// The two operand forms: element type in shared memory, K elements per chunk, the split of an
-// FP32 value into hi + lo, the instruction descriptor (D = F32, A and B of the same type, both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24) and the MMA kind.
-struct SplitTF32 {
-    using T = float;
-    static constexpr int KC = kTcRowBytes / 4;       // 32
-    __device__ static void split(float x, T& hi, T& lo) {
-        hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-        lo = x - hi;
-    }
-    __device__ static uint32_t idesc(int M, int N) {
-        return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-    }
-    __device__ static void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc)
-            : "memory");
-    }
+// K elements of one staged chunk row (kTcRowBytes)
+template <typename Op> struct Chunk {
+    static constexpr int KC = kTcRowBytes / (int)sizeof(typename Op::T);
 };
 
-struct SplitBF16 {
-    using T = __nv_bfloat16;
-    static constexpr int KC = kTcRowBytes / 2;       // 64
-    __device__ static void split(float x, T& hi, T& lo) {
-        hi = __float2bfloat16_rn(x);
-        lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-    }
-    __device__ static uint32_t idesc(int M, int N) {
-        return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-    }
-    __device__ static void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc)
-            : "memory");
-    }
-};
-
-// Canonical K-major layout without swizzle: core matrices of 8 rows x 16 bytes (EPC = 16 /
-// sizeof(T) elements), core (row / 8, k / EPC) at byte ((row / 8) (KC / EPC) + k / EPC) 128, row
-// r % 8 at 16 (r % 8).  Leading-dimension offset (next core along K) 128 B, stride offset (next
-// 8 rows) KC / EPC * 128 = 1024 B for both forms.
 template <typename Op>
 __device__ __forceinline__ uint32_t core_off(int row, int k) {
-    constexpr int ES = (int)sizeof(typename Op::T), EPC = 16 / ES;
-    return (uint32_t)(((row >> 3) * (Op::KC / EPC) + k / EPC) * 128 + (row & 7) * 16 + (k % EPC) * ES);
+    return tc::core_off_kr<typename Op::T>(row, k, Chunk<Op>::KC);
 }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);                    // start address
-    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;                       // leading-dimension byte offset
-    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;                      // stride-dimension byte offset
-    d |= (uint64_t)1 << 46;                                             // descriptor version of tcgen05
-    return d;                                                           // base offset 0, no swizzle
-}
-
-template <typename T> __device__ __forceinline__ void st_part(unsigned char* base, uint32_t off, T v) {
-    *reinterpret_cast<T*>(base + off) = v;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit = kWaitLimit) {
-    for (long long i = 0; i < limit; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(phase)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) { return tc::smem_desc(addr, 1024u); }
 
 // bulk copy of one pre-split B block (both parts) into shared memory, completing on bar
 __device__ __forceinline__ void bulk_b(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
+    tc::bulk_load(dst, src, bytes, bar);
 }
 
 // Pre-split map blocks: for mode m, output tile t (kTcMaxN rows) and K chunk ch, a block of two
@@ -154,7 +76,7 @@ __device__ __forceinline__ void bulk_b(uint32_t dst, const void* src, uint32_t b
 template <typename Op>
 __global__ void k_presplit_map(int nmaps, int nin, int nout, int Npmax, int ntiles, int nchunks,
                                const float* __restrict__ M, unsigned char* __restrict__ out) {
-    constexpr int KC = Op::KC;
+    constexpr int KC = Chunk<Op>::KC;
     using T = typename Op::T;
     const int64_t per_block = (int64_t)Npmax * KC;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -184,7 +106,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar[4];       // [0, 1]: B block of stage s landed; [2, 3]: MMAs of stage s done
     __shared__ uint32_t s_taddr;
-    constexpr int KC = Op::KC;
+    constexpr int KC = Chunk<Op>::KC;
     using T = typename Op::T;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mi = blockIdx.z, m = abs(mi - Lc);
@@ -272,12 +194,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_map_tc(int nbox, int Lc
             if (t_ok) {
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t a0 = sS(st), b0 = sS(st) + 2 * kABytes;
+                // K-steps of this chunk holding samples (the last chunk's zero tail is skipped)
+                const int ksteps = min(4, (nin - ch * KC + Op::KSTEP - 1) / Op::KSTEP);
 #pragma unroll
                 for (int s4 = 0; s4 < 4; ++s4) {
-                    const uint32_t ko = (uint32_t)s4 * 256;             // one MMA K-step: two 16-byte cores along K
-                    Op::mma(tmem, smem_desc(a0 + ko), smem_desc(b0 + ko), idesc, ch > 0 || s4 > 0);
-                    Op::mma(tmem, smem_desc(a0 + ko), smem_desc(b0 + bbytes + ko), idesc, 1);
-                    Op::mma(tmem, smem_desc(a0 + kABytes + ko), smem_desc(b0 + ko), idesc, 1);
+                    if (s4 < ksteps) {
+                        const uint32_t ko = (uint32_t)s4 * 256;         // one MMA K-step: two 16-byte cores along K
+                        Op::mma(tmem, smem_desc(a0 + ko), smem_desc(b0 + ko), idesc, ch > 0 || s4 > 0);
+                        Op::mma(tmem, smem_desc(a0 + ko), smem_desc(b0 + bbytes + ko), idesc, 1);
+                        Op::mma(tmem, smem_desc(a0 + kABytes + ko), smem_desc(b0 + ko), idesc, 1);
+                    }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                                  bar_m(st))
@@ -348,7 +274,7 @@ TcShape tc_shape(int nin, int nout) {
     TcShape t;
     t.Npmax = ((std::min(nout, kTcMaxN) + 15) / 16) * 16;
     t.ntiles = (nout + kTcMaxN - 1) / kTcMaxN;
-    t.nchunks = (nin + Op::KC - 1) / Op::KC;
+    t.nchunks = (nin + Chunk<Op>::KC - 1) / Chunk<Op>::KC;
     return t;
 }
 
@@ -370,7 +296,7 @@ size_t theta_tc_map_bytes(const Plan& p, int nmaps, int nin, int nout) {
 void presplit_theta_tc(const Plan& p, int nmaps, int nin, int nout, const float* M, void* out, cudaStream_t s) {
     const bool bf = p.prec == MLFMA_PREC_FP32_BF16X3;
     const TcShape t = bf ? tc_shape<SplitBF16>(nin, nout) : tc_shape<SplitTF32>(nin, nout);
-    const int KC = bf ? SplitBF16::KC : SplitTF32::KC;
+    const int KC = bf ? Chunk<SplitBF16>::KC : Chunk<SplitTF32>::KC;
     const int64_t tot = (int64_t)nmaps * t.ntiles * t.nchunks * t.Npmax * KC;
     const unsigned nb = (unsigned)((tot + 255) / 256);
     if (bf)

@@ -103,3 +103,63 @@ def test_bf16x3_matches_fp32_large_sphere():
     assert rel(phibf[tg], direct.direct(pts, q, K, targets=tg)) < 1e-3
     pbf.close()
     p32.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4)])
+@pytest.mark.parametrize("geom", ["sphere", "clusters"])
+def test_dense_pairs_match_fft_path(prec, tol, geom):
+    """The fine level pairs as dense tensor-core maps (opt-in: phi transforms, theta maps and shifts
+    folded into one real matrix per pair and direction) against the same precision on the FFT
+    path, level by level, on a level-uniform sphere and on an adaptive clustered set
+    (parent-level leaves, ragged child counts); and against the direct sum."""
+    if geom == "sphere":
+        pts, leaf_max = synth.sphere(65536, 8.0, seed=91), 0
+    else:
+        pts, leaf_max = synth.cube_surface_clusters(60000, half=3.0, seed=97), 24
+    q = synth.complex_normal(92, pts.shape[0])[0]
+    pd = make_plan(pts, K, 3, prec, leaf_max=leaf_max, dense_samples=400)
+    pf = make_plan(pts, K, 3, prec, leaf_max=leaf_max)
+    info = pd.info()
+    assert any(info["dense"]) and not any(pf.info()["dense"])
+    for l in range(info["top"], info["nlev"]):
+        if info["L"][l + 1] > 0:                                   # (l, l + 1) is a far-field pair
+            assert info["dense"][l] == int(info["K"][l + 1] <= 400), l
+    phid = apply_plan(pd, q, prec)
+    phif = apply_plan(pf, q, prec)
+    for l in range(info["top"], info["nlev"] + 1):
+        if info["nbox"][l] == 0:
+            continue
+        assert rel(pd.export("F", l), pf.export("F", l)) < tol, ("F", l)
+        assert rel(pd.export("G", l), pf.export("G", l)) < tol, ("G", l)
+    assert rel(phid, phif) < tol
+    assert np.array_equal(apply_plan(pd, q, prec), phid)          # graph replay: same bits
+    tg = np.sort(np.random.default_rng(6).choice(pts.shape[0], 500, replace=False))
+    assert rel(phid[tg], direct.direct(pts, q, K, targets=tg)) < 1e-3
+    assert pd.info()["precision"] == {"tf32x3": 3, "bf16x3": 2}[prec]   # no device error flag raised
+    pd.close()
+    pf.close()
+
+
+def test_dense_pairs_in_forest_match_single_plans():
+    """A batched forest plan (tf32x3, dense fine pairs) over ellipsoids and geometries without a
+    far field or without a parent level: every geometry matches its own plan and the direct
+    sum (the dense kernels find parents and children through the forest's merged levels)."""
+    import torch
+    geoms, sizes, axes = synth.ellipsoid_batch(4, seed=4101, nmin=2000, nmax=20000, amin=1.0, amax=3.0)
+    geoms = list(geoms) + [np.array([[0.0, 0.0, 0.0], [0.3, 0.1, -0.2]]), synth.sphere(900, 0.8, seed=4102)]
+    pts = np.concatenate(geoms)
+    off = np.concatenate([[0], np.cumsum([g.shape[0] for g in geoms])])
+    Q = synth.complex_normal(4103, pts.shape[0], nrhs=1)
+    dev = torch.device("cuda", 0)
+    plan = make_plan(pts, K, 3, "tf32x3", offsets=off, dense_samples=400)
+    assert any(plan.info()["dense"])
+    out = plan.apply(torch.as_tensor(Q[0].astype(np.complex64), device=dev)).cpu().numpy()
+    for gi, g in enumerate(geoms):
+        sl = slice(off[gi], off[gi + 1])
+        single = make_plan(g, K, 3, "tf32x3", graphs=False, dense_samples=400)
+        ref = single.apply(torch.as_tensor(Q[0, sl].astype(np.complex64), device=dev)).cpu().numpy()
+        assert rel(out[sl], ref) < 1e-6, gi
+        assert rel(out[sl], direct.direct(g, Q[0, sl], K)) < 1e-3, gi
+        single.close()
+    assert plan.info()["precision"] == 3
+    plan.close()
