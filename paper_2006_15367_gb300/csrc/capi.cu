@@ -397,6 +397,9 @@ static void init_streams(Plan& P, int nsub) {
     MLFMA_CUDA(cudaStreamCreateWithFlags(&P.gstream, cudaStreamNonBlocking));
     MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_fork, cudaEventDisableTiming));
     MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_join, cudaEventDisableTiming));
+    MLFMA_CUDA(cudaStreamCreateWithFlags(&P.nstream, cudaStreamNonBlocking));
+    MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_nfork, cudaEventDisableTiming));
+    MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_near, cudaEventDisableTiming));
     for (int w = 0; w < nsub; ++w) {
         cudaStream_t st;
         cudaEvent_t ev;
@@ -410,6 +413,7 @@ static void init_streams(Plan& P, int nsub) {
 static void release_plan(Plan& P) {
     if (P.stream) cudaStreamSynchronize(P.stream);
     if (P.gstream) cudaStreamSynchronize(P.gstream);
+    if (P.nstream) cudaStreamSynchronize(P.nstream);
     for (auto s : P.sub_streams) cudaStreamSynchronize(s);
     drop_graphs(P);
     for (auto* sp : P.subs) {
@@ -428,8 +432,11 @@ static void release_plan(Plan& P) {
     if (P.ev_fork) cudaEventDestroy(P.ev_fork);
     if (P.ev_join) cudaEventDestroy(P.ev_join);
     if (P.gstream) cudaStreamDestroy(P.gstream);
-    P.ev_fork = P.ev_join = nullptr;
-    P.gstream = nullptr;
+    if (P.ev_nfork) cudaEventDestroy(P.ev_nfork);
+    if (P.ev_near) cudaEventDestroy(P.ev_near);
+    if (P.nstream) cudaStreamDestroy(P.nstream);
+    P.ev_fork = P.ev_join = P.ev_nfork = P.ev_near = nullptr;
+    P.gstream = P.nstream = nullptr;
     P.mem.release_all();
 }
 

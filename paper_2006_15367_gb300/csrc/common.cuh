@@ -225,8 +225,9 @@ struct Plan {
     int64_t nnear = 0, near_pairs = 0;
     // P2P work split: leaves with at most kSmallLeaf points (one warp each) and
     // tiles of kP2PTile targets of the larger leaves (one CTA each)
-    int* p2p_small = nullptr;      // [n_small] leaf-table indices
-    int64_t n_small = 0;
+    int* p2p_small = nullptr;      // [n_small] leaf-table indices: first the n_small32 leaves with at
+    int64_t n_small = 0;           // most 32 points, then those with 33 .. kSmallLeaf
+    int64_t n_small32 = 0;
     int2* p2p_tiles = nullptr;     // [n_tiles] (leaf-table index, first target offset)
     int64_t n_tiles = 0;
     TreeLevel lev[kMaxLev + 1];
@@ -259,6 +260,11 @@ struct Plan {
     int dense_kc = 0;
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // near field beside the far field: P2P runs on nstream from ev_nfork while the far field's
+    // upward and downward passes run on the plan stream, which waits for ev_near before L2O
+    // (single and forest plans; null: one stream)
+    cudaStream_t nstream = nullptr;
+    cudaEvent_t ev_nfork = nullptr, ev_near = nullptr;
     std::map<int64_t, cudaGraphExec_t> graphs;
     // batched plans: independent geometries; level-uniform ones are merged into this plan as a
     // forest (the sub-plans then only hold the shared operators), others run concurrently on
@@ -324,7 +330,7 @@ void presplit_theta_tc(const Plan& p, int nmaps, int nin, int nout, const float*
 // one right-hand side in sorted order; grads_r (nullable): [n][3] complex gradient of phi
 // nr right-hand sides per pass (1, or kMaxNR without gradients): q and phi r n apart
 void apply_pipeline(Plan& p, const void* qs_r, void* phis_r, void* grads_r, int nr);
-void far_apply(Plan& p, const void* qs, void* phis, void* grads, int nr);
+void far_apply(Plan& p, const void* qs, void* phis, void* grads, int nr, cudaEvent_t near_done = nullptr);
 // one apply of a top-level plan on a device vector in caller order; the result stays in P.phiout
 void apply_device(Plan& P, const void* q);
 // restarted GMRES on (sigma I + A) x = b with the plan's matvec (solve.cu)

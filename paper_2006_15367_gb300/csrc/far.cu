@@ -1488,8 +1488,11 @@ static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int n
 // One pass of the far field for NR right-hand sides (charges qs[r n + j], potentials
 // phis[r n + j]; signatures of level l r nbox_l K_l apart).  C2M, M2L and L2O take all NR
 // at once; the interpolation steps run per right-hand side on the shared spectral scratch.
+// Upward pass, then M2L and L2L down the levels, then L2O at every level with leaves (after
+// near_done, when the near field runs on another stream: L2O adds to what it wrote; each
+// level's local signatures stay in place after its L2L, so L2O can come last).
 template <typename R, int NR>
-static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v) {
+static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v, cudaEvent_t near_done) {
     using C = typename Cx<R>::T;
     cudaStream_t s = p.stream;
     const C* qs = (const C*)qs_v;
@@ -1636,6 +1639,12 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v)
                 }
             }
         }
+    }
+    // ---- L2O at every level with leaves (after the near field)
+    if (near_done) MLFMA_CUDA(cudaStreamWaitEvent(s, near_done, 0));
+    for (int l = p.top; l <= p.nlev; ++l) {
+        FarLevel& F = p.far[l];
+        TreeLevel& T = p.lev[l];
         if (T.nleaf > 0) {
             StageTimer st(p, MLFMA_STAGE_L2O, l, (T.n_small_leaves > 0) + (T.n_big_tiles > 0));
             if (T.n_small_leaves > 0) {
@@ -1715,15 +1724,15 @@ void prepare_kernels(Plan& p) {
     }
 }
 
-void far_apply(Plan& p, const void* qs, void* phis, void* grads, int nr) {
+void far_apply(Plan& p, const void* qs, void* phis, void* grads, int nr, cudaEvent_t near_done) {
     if (!p.top) return;
     if (nr != 1 && nr != kMaxNR) fail(MLFMA_ERR_INVALID_ARG, "right-hand sides per pass %d", nr);
     if (p.prec == MLFMA_PREC_FP64) {
-        if (nr == 1) far_pipeline<double, 1>(p, qs, phis, grads);
-        else far_pipeline<double, kMaxNR>(p, qs, phis, nullptr);
+        if (nr == 1) far_pipeline<double, 1>(p, qs, phis, grads, near_done);
+        else far_pipeline<double, kMaxNR>(p, qs, phis, nullptr, near_done);
     } else {
-        if (nr == 1) far_pipeline<float, 1>(p, qs, phis, grads);
-        else far_pipeline<float, kMaxNR>(p, qs, phis, nullptr);
+        if (nr == 1) far_pipeline<float, 1>(p, qs, phis, grads, near_done);
+        else far_pipeline<float, kMaxNR>(p, qs, phis, nullptr, near_done);
     }
 }
 

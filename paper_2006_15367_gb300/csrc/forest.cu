@@ -240,17 +240,19 @@ void build_forest(Plan& P) {
     }
 
     // ---- leaf table, near lists, P2P work
-    int64_t nleaf = 0, nnear = 0, n_small = 0, n_tiles = 0;
+    int64_t nleaf = 0, nnear = 0, n_small = 0, n_small32 = 0, n_tiles = 0;
     for (const Plan* sp : P.subs) {
         nleaf += sp->nleaf_total;
         nnear += sp->nnear;
         n_small += sp->n_small;
+        n_small32 += sp->n_small32;
         n_tiles += sp->n_tiles;
         P.near_pairs += sp->near_pairs;
     }
     P.nleaf_total = nleaf;
     P.nnear = nnear;
     P.n_small = n_small;
+    P.n_small32 = n_small32;
     P.n_tiles = n_tiles;
     P.leaf_level = P.mem.make<int>(std::max<int64_t>(nleaf, 1));
     P.leaf_box = P.mem.make<int>(std::max<int64_t>(nleaf, 1));
@@ -259,7 +261,8 @@ void build_forest(Plan& P) {
     P.near_box = P.mem.make<int>(std::max<int64_t>(nnear, 1));
     P.p2p_small = P.mem.make<int>(std::max<int64_t>(n_small, 1));
     P.p2p_tiles = P.mem.make<int2>(std::max<int64_t>(n_tiles, 1));
-    int64_t o_leaf = 0, o_near = 0, o_small = 0, o_tiles = 0;
+    // small leaves: every geometry's leaves of up to 32 points first, then those of 33 and more
+    int64_t o_leaf = 0, o_near = 0, o_small = 0, o_mid = n_small32, o_tiles = 0;
     for (int g = 0; g < G; ++g) {
         const Plan& sp = *P.subs[g];
         const LevOffsets offs = own_offsets(g);
@@ -273,16 +276,20 @@ void build_forest(Plan& P) {
         if (sp.nnear > 0)
             k_copy_levbox<<<nblk(sp.nnear, 256), 256, 0, s>>>(P.near_lev + o_near, P.near_box + o_near, sp.near_lev,
                                                               sp.near_box, sp.nnear, shift[g], offs);
-        if (sp.n_small > 0)
-            k_copy_add<<<nblk(sp.n_small, 256), 256, 0, s>>>(P.p2p_small + o_small, sp.p2p_small, sp.n_small,
-                                                             (int)o_leaf);
+        if (sp.n_small32 > 0)
+            k_copy_add<<<nblk(sp.n_small32, 256), 256, 0, s>>>(P.p2p_small + o_small, sp.p2p_small, sp.n_small32,
+                                                               (int)o_leaf);
+        if (sp.n_small > sp.n_small32)
+            k_copy_add<<<nblk(sp.n_small - sp.n_small32, 256), 256, 0, s>>>(
+                P.p2p_small + o_mid, sp.p2p_small + sp.n_small32, sp.n_small - sp.n_small32, (int)o_leaf);
         if (sp.n_tiles > 0)
             k_copy_tiles<<<nblk(sp.n_tiles, 256), 256, 0, s>>>(P.p2p_tiles + o_tiles, sp.p2p_tiles, sp.n_tiles,
                                                                (int)o_leaf);
         MLFMA_LAUNCH_CHECK();
         o_leaf += sp.nleaf_total;
         o_near += sp.nnear;
-        o_small += sp.n_small;
+        o_small += sp.n_small32;
+        o_mid += sp.n_small - sp.n_small32;
         o_tiles += sp.n_tiles;
     }
     k_fill<<<1, 1, 0, s>>>(P.near_off + nleaf, 1, (int)nnear);

@@ -4,10 +4,12 @@
 //
 // P2P for a target leaf b sums q_j e^{ikR}/R over the points of its near sources
 // (U list; W and X lists of adaptive trees), skipping R = 0 (the point itself and
-// coincident points).  One warp per target leaf; the source points of its near boxes
-// are staged through shared memory relative to the target leaf centre (FP64
-// difference, then rounded), lanes split (target, source slice) and the slices are
-// combined with warp shuffles.
+// coincident points).  One warp per target leaf of up to 64 points; the source points of its
+// near boxes are staged through shared memory relative to the target leaf centre (FP64
+// difference, then rounded); lanes split (target, source slice) and the slices are combined
+// with warp shuffles, or with 33-64 targets every lane takes two.  Larger leaves take tiles of
+// 128 targets per CTA.  The FP32 kernels evaluate sin and cos of k R on the SFU after reducing
+// k R / pi to [-1, 1] (absolute error about 4e-7).
 #include <cstdio>
 
 #include "common.cuh"
@@ -16,8 +18,6 @@ namespace mlfma {
 
 static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-__device__ __forceinline__ void scpi(float x, float& s, float& c) { sincospif(x, &s, &c); }
-__device__ __forceinline__ void scpi(double x, double& s, double& c) { sincospi(x, &s, &c); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
@@ -45,8 +45,8 @@ struct LevelRanges {
 constexpr int kP2PSlots = 128;
 
 // NR right-hand sides (charges and potentials sn apart) share each kernel value; GRAD only
-// with NR = 1.
-template <typename R, typename C, bool GRAD, int NR>
+// with NR = 1.  TWO: the leaves of the list hold 33 .. 64 points (else at most 32).
+template <typename R, typename C, bool GRAD, int NR, bool TWO>
 __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restrict__ leaves, const int* __restrict__ leaf_level,
                                              const int* __restrict__ leaf_box, const int* __restrict__ near_off,
                                              const int* __restrict__ near_lev, const int* __restrict__ near_box, LevelRanges LR,
@@ -65,121 +65,144 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
     const double* ct = LR.center[l] + 3 * b;
     const double cx = ct[0], cy = ct[1], cz = ct[2];
     const int s_lo = near_off[w], s_hi = near_off[w + 1];
-    for (int j0 = t0; j0 < t1; j0 += 32) {
-        const int np = min(32, t1 - j0);
-        int P = 1;
-        while (P < np) P <<= 1;
-        const int S = 32 / P;
-        const int tp = lane & (P - 1), sl = lane / P;
-        const int i = j0 + tp;
-        R x = 0, y = 0, z = 0;
-        if (tp < np) {
-            x = (R)(pos[3 * (int64_t)i] - cx);
-            y = (R)(pos[3 * (int64_t)i + 1] - cy);
-            z = (R)(pos[3 * (int64_t)i + 2] - cz);
+    // up to 32 targets: P lanes (a power of two) take one target each and the S = 32 / P lane
+    // groups split the sources; 33 .. 64 targets: every lane takes targets tp and tp + 32, so
+    // each staged source feeds two targets and the stream is staged once
+    const int nt = t1 - t0;
+    const int np = TWO ? 32 : nt;
+    int P = 1;
+    while (P < np) P <<= 1;
+    const int S = 32 / P;
+    const int tp = lane & (P - 1), sl = lane / P;
+    const int i = t0 + tp, i2 = i + 32;
+    const bool has1 = tp < np, has2 = TWO && i2 < t1;
+    R x = 0, y = 0, z = 0, x2 = 0, y2 = 0, z2 = 0;
+    if (has1) {
+        x = (R)(pos[3 * (int64_t)i] - cx);
+        y = (R)(pos[3 * (int64_t)i + 1] - cy);
+        z = (R)(pos[3 * (int64_t)i + 2] - cz);
+    }
+    if (has2) {
+        x2 = (R)(pos[3 * (int64_t)i2] - cx);
+        y2 = (R)(pos[3 * (int64_t)i2 + 1] - cy);
+        z2 = (R)(pos[3 * (int64_t)i2 + 2] - cz);
+    }
+    C acc[NR], acc2[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = acc2[r] = cmake<C>(0, 0);
+    C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
+    C gb[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
+    const R kk = kpi * (R)M_PI;
+    // one (target, source) term, branch-free: R = 0 (the point itself, coincident points) gives
+    // inv = 0 and adds nothing
+    auto term = [&](R tx, R ty, R tz, int jj, C (&ac)[NR], C (&gg)[3]) {
+        const R dx = tx - sx[wl][jj], dy = ty - sy[wl][jj], dz = tz - sz[wl][jj];
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        const R inv = r2 > (R)0 ? rsq(r2) : (R)0;
+        const R r = r2 * inv;
+        R s, c;
+        scpi_fast(kpi * r, s, c);
+        if (!GRAD) {
+            const C g = cmake<C>(c * inv, s * inv);
+#pragma unroll
+            for (int q = 0; q < NR; ++q) cfma(ac[q], sq[wl][q][jj], g);
+        } else {
+            const C qe = cmul(sq[wl][0][jj], cmake<C>(c * inv, s * inv));   // q e^{ikR} / R
+            ac[0] = cadd(ac[0], qe);
+            // q e^{ikR} (ikR - 1) / R^3 = qe (ikR - 1) / R^2
+            const R iv2 = inv * inv;
+            const C g = cmul(qe, cmake<C>(-iv2, kk * r * iv2));
+            gg[0] = cadd(gg[0], cmake<C>(g.x * dx, g.y * dx));
+            gg[1] = cadd(gg[1], cmake<C>(g.x * dy, g.y * dy));
+            gg[2] = cadd(gg[2], cmake<C>(g.x * dz, g.y * dz));
         }
-        C acc[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) acc[r] = cmake<C>(0, 0);
-        C ga[3] = {cmake<C>(0, 0), cmake<C>(0, 0), cmake<C>(0, 0)};
-        const R kk = kpi * (R)M_PI;
-        int eb = s_lo, oe = 0;
-        while (eb < s_hi) {
-            const int e = eb + lane;
-            int u0 = 0, cnt = 0;
-            if (e < s_hi) {
-                const int ls = near_lev[e], bs = near_box[e];
-                u0 = LR.begin[ls][bs];
-                cnt = LR.end[ls][bs] - u0;
-            }
-            if (lane == 0) { u0 += oe; cnt -= oe; }
-            int inc = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(FULL, inc, o);
-                if (lane >= o) inc += t;
-            }
-            const int exc = inc - cnt;
-            const int all = __shfl_sync(FULL, inc, 31);
-            const int total = min(all, kP2PSlots);
-            for (int s0 = 0; s0 < total; s0 += 32) {
-                const int sidx = s0 + lane;
-                int q = 0;                       // first lane whose inclusive count exceeds sidx
-#pragma unroll
-                for (int st = 16; st >= 1; st >>= 1) {
-                    const int v = __shfl_sync(FULL, inc, q + st - 1);
-                    if (v <= sidx) q += st;
-                }
-                const int uq = __shfl_sync(FULL, u0, q), xq = __shfl_sync(FULL, exc, q);
-                if (sidx < total) {
-                    const int64_t j = uq + (sidx - xq);
-                    sx[wl][sidx] = (R)(pos[3 * j] - cx);
-                    sy[wl][sidx] = (R)(pos[3 * j + 1] - cy);
-                    sz[wl][sidx] = (R)(pos[3 * j + 2] - cz);
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) sq[wl][r][sidx] = qs[r * sn + j];
-                }
-            }
-            // advance the cursor past the consumed points
-            const int qn = __popc(__ballot_sync(FULL, inc <= total));
-            if (total == all) {
-                eb += 32;
-                oe = 0;
-            } else {
-                const int xn = __shfl_sync(FULL, exc, qn);
-                oe = (qn == 0 ? oe : 0) + (total - xn);
-                eb += qn;
-            }
-            __syncwarp();
-            if (tp < np) {
-                for (int jj = sl; jj < total; jj += S) {
-                    R dx = x - sx[wl][jj], dy = y - sy[wl][jj], dz = z - sz[wl][jj];
-                    R r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 > (R)0) {
-                        R inv = rsq(r2);
-                        R r = r2 * inv;
-                        R s, c;
-                        scpi(kpi * r, s, c);
-                        if (!GRAD) {
-                            const C g = cmake<C>(c * inv, s * inv);
-#pragma unroll
-                            for (int r = 0; r < NR; ++r) cfma(acc[r], sq[wl][r][jj], g);
-                        } else {
-                            const C qe = cmul(sq[wl][0][jj], cmake<C>(c * inv, s * inv));   // q e^{ikR} / R
-                            acc[0] = cadd(acc[0], qe);
-                            // q e^{ikR} (ikR - 1) / R^3 = qe (ikR - 1) / R^2
-                            const R i2 = inv * inv;
-                            const C g = cmul(qe, cmake<C>(-i2, kk * r * i2));
-                            ga[0] = cadd(ga[0], cmake<C>(g.x * dx, g.y * dx));
-                            ga[1] = cadd(ga[1], cmake<C>(g.x * dy, g.y * dy));
-                            ga[2] = cadd(ga[2], cmake<C>(g.x * dz, g.y * dz));
-                        }
-                    }
-                }
-            }
-            __syncwarp();
+    };
+    int eb = s_lo, oe = 0;
+    while (eb < s_hi) {
+        const int e = eb + lane;
+        int u0 = 0, cnt = 0;
+        if (e < s_hi) {
+            const int ls = near_lev[e], bs = near_box[e];
+            u0 = LR.begin[ls][bs];
+            cnt = LR.end[ls][bs] - u0;
         }
-        for (int o = 16; o >= P; o >>= 1) {
+        if (lane == 0) { u0 += oe; cnt -= oe; }
+        int inc = cnt;
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
-                acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += t;
+        }
+        const int exc = inc - cnt;
+        const int all = __shfl_sync(FULL, inc, 31);
+        const int total = min(all, kP2PSlots);
+        for (int s0 = 0; s0 < total; s0 += 32) {
+            const int sidx = s0 + lane;
+            int q = 0;                       // first lane whose inclusive count exceeds sidx
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const int v = __shfl_sync(FULL, inc, q + st - 1);
+                if (v <= sidx) q += st;
             }
-            if (GRAD) {
+            const int uq = __shfl_sync(FULL, u0, q), xq = __shfl_sync(FULL, exc, q);
+            if (sidx < total) {
+                const int64_t j = uq + (sidx - xq);
+                sx[wl][sidx] = (R)(pos[3 * j] - cx);
+                sy[wl][sidx] = (R)(pos[3 * j + 1] - cy);
+                sz[wl][sidx] = (R)(pos[3 * j + 2] - cz);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    ga[a].x += __shfl_xor_sync(0xffffffffu, ga[a].x, o);
-                    ga[a].y += __shfl_xor_sync(0xffffffffu, ga[a].y, o);
-                }
+                for (int r = 0; r < NR; ++r) sq[wl][r][sidx] = qs[r * sn + j];
             }
         }
-        if (sl == 0 && tp < np) {
-#pragma unroll
-            for (int r = 0; r < NR; ++r) phis[r * sn + i] = acc[r];
-            if (GRAD)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) grads[3 * (int64_t)i + a] = ga[a];
+        // advance the cursor past the consumed points
+        const int qn = __popc(__ballot_sync(FULL, inc <= total));
+        if (total == all) {
+            eb += 32;
+            oe = 0;
+        } else {
+            const int xn = __shfl_sync(FULL, exc, qn);
+            oe = (qn == 0 ? oe : 0) + (total - xn);
+            eb += qn;
         }
+        __syncwarp();
+        if constexpr (TWO) {
+            // every lane holds two targets (the second may be absent: its terms are discarded)
+            for (int jj = 0; jj < total; ++jj) {
+                term(x, y, z, jj, acc, ga);
+                term(x2, y2, z2, jj, acc2, gb);
+            }
+        } else if (has1) {
+            for (int jj = sl; jj < total; jj += S) term(x, y, z, jj, acc, ga);
+        }
+        __syncwarp();
+    }
+    for (int o = 16; o >= P && S > 1; o >>= 1) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
+            acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
+        }
+        if (GRAD) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                ga[a].x += __shfl_xor_sync(0xffffffffu, ga[a].x, o);
+                ga[a].y += __shfl_xor_sync(0xffffffffu, ga[a].y, o);
+            }
+        }
+    }
+    if (sl == 0 && has1) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) phis[r * sn + i] = acc[r];
+        if (GRAD)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) grads[3 * (int64_t)i + a] = ga[a];
+    }
+    if (TWO && has2) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) phis[r * sn + i2] = acc2[r];
+        if (GRAD)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) grads[3 * (int64_t)i2 + a] = gb[a];
     }
 }
 
@@ -245,20 +268,18 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ 
                         const C g = cmake<C>(c * inv, s * inv);
 #pragma unroll
                         for (int r = 0; r < NR; ++r) cfma(acc[r], sq[r][m], g);
-                    } else if (r2 > (R)0) {
-                        const R inv = rsq(r2);
+                    } else {
+                        const R inv = r2 > (R)0 ? rsq(r2) : (R)0;
                         const R r = r2 * inv;
                         R s, c;
-                        scpi(kpi * r, s, c);
-                        {
-                            const C qe = cmul(sq[0][m], cmake<C>(c * inv, s * inv));
-                            acc[0] = cadd(acc[0], qe);
-                            const R i2 = inv * inv;
-                            const C g = cmul(qe, cmake<C>(-i2, kk * r * i2));
-                            ga[0] = cadd(ga[0], cmake<C>(g.x * dx, g.y * dx));
-                            ga[1] = cadd(ga[1], cmake<C>(g.x * dy, g.y * dy));
-                            ga[2] = cadd(ga[2], cmake<C>(g.x * dz, g.y * dz));
-                        }
+                        scpi_fast(kpi * r, s, c);
+                        const C qe = cmul(sq[0][m], cmake<C>(c * inv, s * inv));
+                        acc[0] = cadd(acc[0], qe);
+                        const R i2 = inv * inv;
+                        const C g = cmul(qe, cmake<C>(-i2, kk * r * i2));
+                        ga[0] = cadd(ga[0], cmake<C>(g.x * dx, g.y * dx));
+                        ga[1] = cadd(ga[1], cmake<C>(g.x * dy, g.y * dy));
+                        ga[2] = cadd(ga[2], cmake<C>(g.x * dz, g.y * dz));
                     }
                 }
             }
@@ -327,18 +348,30 @@ static void near_apply(Plan& p, const void* qs, void* phis, void* grads, bool ti
         LR.end[l] = l <= p.nlev ? p.lev[l].end : nullptr;
         LR.center[l] = l <= p.nlev ? p.lev[l].center : nullptr;
     }
-    const int64_t nl = p.n_small, sn = p.n;
+    const int64_t n32 = p.n_small32, nmid = p.n_small - p.n_small32, sn = p.n;
     const R kpi = (R)(p.k / M_PI);
-    StageTimer st(p, MLFMA_STAGE_P2P, 0, (nl > 0) + (p.n_tiles > 0), timed);
-    if (nl > 0) {
+    StageTimer st(p, MLFMA_STAGE_P2P, 0, (n32 > 0) + (nmid > 0) + (p.n_tiles > 0), timed);
+    if (n32 > 0) {
         if (grads)
-            k_p2p<R, C, true, 1><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off,
-                                                                    p.near_lev, p.near_box, LR, p.pos, (const C*)qs, sn,
-                                                                    kpi, (C*)phis, (C*)grads);
+            k_p2p<R, C, true, 1, false><<<nblk(n32, 4), 128, 0, p.stream>>>(
+                n32, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos,
+                (const C*)qs, sn, kpi, (C*)phis, (C*)grads);
         else
-            k_p2p<R, C, false, NR><<<nblk(nl, 4), 128, 0, p.stream>>>(nl, p.p2p_small, p.leaf_level, p.leaf_box,
-                                                                      p.near_off, p.near_lev, p.near_box, LR, p.pos,
-                                                                      (const C*)qs, sn, kpi, (C*)phis, nullptr);
+            k_p2p<R, C, false, NR, false><<<nblk(n32, 4), 128, 0, p.stream>>>(
+                n32, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos,
+                (const C*)qs, sn, kpi, (C*)phis, nullptr);
+        MLFMA_LAUNCH_CHECK();
+    }
+    if (nmid > 0) {
+        const int* mid = p.p2p_small + n32;
+        if (grads)
+            k_p2p<R, C, true, 1, true><<<nblk(nmid, 4), 128, 0, p.stream>>>(
+                nmid, mid, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, sn,
+                kpi, (C*)phis, (C*)grads);
+        else
+            k_p2p<R, C, false, NR, true><<<nblk(nmid, 4), 128, 0, p.stream>>>(
+                nmid, mid, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, sn,
+                kpi, (C*)phis, nullptr);
         MLFMA_LAUNCH_CHECK();
     }
     if (p.n_tiles > 0) {
@@ -360,17 +393,38 @@ void near_only(Plan& p, const void* qs, void* phis, bool timed) {
 }
 
 // nr right-hand sides (q and phi n apart): 1, or kMaxNR without gradients
+// One pass of nr right-hand sides: the near field writes phis (and grads), the far field's L2O
+// adds to them.  The two are independent until then, so unless stage timings are being taken
+// the near field runs on its own stream beside the far field's upward and downward passes and
+// the plan stream waits for it before the first L2O (the fork and the join are events, so a
+// captured apply keeps them as graph edges).
 void apply_pipeline(Plan& p, const void* qs, void* phis, void* grads, int nr) {
-    if (nr == kMaxNR && !grads) {
-        if (p.prec == MLFMA_PREC_FP64) near_apply<double, kMaxNR>(p, qs, phis, nullptr);
-        else near_apply<float, kMaxNR>(p, qs, phis, nullptr);
-    } else {
-        if (nr != 1) fail(MLFMA_ERR_INVALID_ARG, "right-hand sides per pass %d", nr);
-        if (p.prec == MLFMA_PREC_FP64) near_apply<double, 1>(p, qs, phis, grads);
-        else near_apply<float, 1>(p, qs, phis, grads);
+    if (nr != 1 && !(nr == kMaxNR && !grads)) fail(MLFMA_ERR_INVALID_ARG, "right-hand sides per pass %d", nr);
+    const bool fork = p.nstream && !p.profiling;
+    const cudaStream_t main = p.stream;
+    if (fork) {
+        MLFMA_CUDA(cudaEventRecord(p.ev_nfork, main));
+        MLFMA_CUDA(cudaStreamWaitEvent(p.nstream, p.ev_nfork, 0));
+        p.stream = p.nstream;
     }
-    if (p.near_dump) MLFMA_CUDA(cudaMemcpyAsync(p.near_dump, phis, p.n * csize(p), cudaMemcpyDeviceToDevice, p.stream));
-    far_apply(p, qs, phis, grads, nr);
+    try {
+        if (nr == kMaxNR) {
+            if (p.prec == MLFMA_PREC_FP64) near_apply<double, kMaxNR>(p, qs, phis, nullptr);
+            else near_apply<float, kMaxNR>(p, qs, phis, nullptr);
+        } else {
+            if (p.prec == MLFMA_PREC_FP64) near_apply<double, 1>(p, qs, phis, grads);
+            else near_apply<float, 1>(p, qs, phis, grads);
+        }
+        if (p.near_dump)
+            MLFMA_CUDA(cudaMemcpyAsync(p.near_dump, phis, p.n * csize(p), cudaMemcpyDeviceToDevice, p.stream));
+        if (fork) MLFMA_CUDA(cudaEventRecord(p.ev_near, p.nstream));
+    } catch (...) {
+        p.stream = main;
+        throw;
+    }
+    p.stream = main;
+    far_apply(p, qs, phis, grads, nr, fork ? p.ev_near : nullptr);
+    if (fork) MLFMA_CUDA(cudaStreamWaitEvent(main, p.ev_near, 0));   // no far field: join here
 }
 
 template <typename C>

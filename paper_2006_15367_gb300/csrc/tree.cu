@@ -840,6 +840,36 @@ __global__ void k_leaf_sizes(int64_t nleaf, const int* __restrict__ leaf_level, 
     out[t] = end[l][b] - beg[l][b];
 }
 
+// near-field source points of each leaf (sum of its near boxes' point counts)
+__global__ void k_leaf_sources(int64_t nleaf, const int* __restrict__ near_off, const int* __restrict__ near_lev,
+                               const int* __restrict__ near_box, const int* const* __restrict__ beg,
+                               const int* const* __restrict__ end, long long* __restrict__ out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nleaf) return;
+    long long n = 0;
+    for (int e = near_off[t]; e < near_off[t + 1]; ++e) {
+        const int l = near_lev[e], b = near_box[e];
+        n += end[l][b] - beg[l][b];
+    }
+    out[t] = n;
+}
+
+// Heavy leaves first: the entries whose work is above four times the list's mean, by decreasing
+// work, then the others in their (Morton) order.  The near field's launches then end with short
+// warps instead of waiting on one with thousands of sources.
+template <typename T, typename W>
+static void heavy_first(std::vector<T>& v, W work) {
+    if (v.size() < 2) return;
+    double mean = 0;
+    for (const T& x : v) mean += (double)work(x);
+    mean /= (double)v.size();
+    std::vector<T> heavy, rest;
+    for (const T& x : v) ((double)work(x) > 4.0 * mean ? heavy : rest).push_back(x);
+    std::stable_sort(heavy.begin(), heavy.end(), [&](const T& a, const T& b) { return work(a) > work(b); });
+    heavy.insert(heavy.end(), rest.begin(), rest.end());
+    v.swap(heavy);
+}
+
 void build_p2p_work(Plan& p) {
     cudaStream_t s = p.stream;
     const int64_t nl = p.nleaf_total;
@@ -853,14 +883,24 @@ void build_p2p_work(Plan& p) {
     MLFMA_CUDA(cudaMemcpyAsync(de, he, sizeof(he), cudaMemcpyHostToDevice, s));
     k_leaf_sizes<<<nblk(nl, 256), 256, 0, s>>>(nl, p.leaf_level, p.leaf_box, db, de, sizes);
     MLFMA_LAUNCH_CHECK();
+    long long* srcs = p.mem.make<long long>(std::max<int64_t>(nl, 1));
+    if (nl > 0) {
+        k_leaf_sources<<<nblk(nl, 256), 256, 0, s>>>(nl, p.near_off, p.near_lev, p.near_box, db, de, srcs);
+        MLFMA_LAUNCH_CHECK();
+    }
     std::vector<int> hs(nl);
+    std::vector<long long> hsrc(nl);
     MLFMA_CUDA(cudaMemcpyAsync(hs.data(), sizes, nl * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MLFMA_CUDA(cudaMemcpyAsync(hsrc.data(), srcs, nl * sizeof(long long), cudaMemcpyDeviceToHost, s));
     MLFMA_CUDA(cudaStreamSynchronize(s));
-    std::vector<int> small;
+    p.mem.drop(srcs);
+    std::vector<int> small, small_mid;        // up to 32 points; 33 .. kSmallLeaf (two targets per lane)
     std::vector<int2> tiles;
     for (int64_t t = 0; t < nl; ++t) {
-        if (hs[t] <= kSmallLeaf) {
+        if (hs[t] <= 32) {
             small.push_back((int)t);
+        } else if (hs[t] <= kSmallLeaf) {
+            small_mid.push_back((int)t);
         } else {
             for (int o = 0; o < hs[t]; o += kP2PTile) tiles.push_back(make_int2((int)t, o));
         }
@@ -893,6 +933,12 @@ void build_p2p_work(Plan& p) {
         if (!bt.empty()) MLFMA_CUDA(cudaMemcpyAsync(L.big_tiles, bt.data(), bt.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
         MLFMA_CUDA(cudaStreamSynchronize(s));
     }
+    auto leaf_work = [&](int t) { return (long long)hs[t] * hsrc[t]; };
+    heavy_first(small, leaf_work);
+    heavy_first(small_mid, leaf_work);
+    heavy_first(tiles, [&](const int2& tl) { return (long long)std::min(kP2PTile, hs[tl.x] - tl.y) * hsrc[tl.x]; });
+    p.n_small32 = (int64_t)small.size();
+    small.insert(small.end(), small_mid.begin(), small_mid.end());
     p.n_small = (int64_t)small.size();
     p.n_tiles = (int64_t)tiles.size();
     p.p2p_small = p.mem.make<int>(std::max<int64_t>(p.n_small, 1));

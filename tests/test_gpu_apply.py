@@ -81,13 +81,17 @@ def test_six_digits_fp64_half_wavelength_leaves(sphere4k):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_adaptive_tree_matches_oracle(prec):
+@pytest.mark.parametrize("leaf_max", [24, 64])
+def test_adaptive_tree_matches_oracle(prec, leaf_max):
+    """A sphere with a dense cluster, adaptive tree: every stage against the oracle.  With
+    leaf_max 64 the cluster's leaves hold 33-64 points (the near-field warp takes two targets
+    per lane) and the deepest leaves more (tiles of 128 targets)."""
     pts = np.concatenate([synth.sphere(3000, 1.5, seed=71),
                           synth.normal(72, 3 * 1200).reshape(1200, 3) * 0.05 + np.array([0.9, 0.2, -0.3])])
     q = synth.complex_normal(73, pts.shape[0])[0]
-    o = om.OracleMLFMA(pts, K, 3, leaf_max=24, margin=MARGIN[prec])
+    o = om.OracleMLFMA(pts, K, 3, leaf_max=leaf_max, margin=MARGIN[prec])
     phio, dump = o.apply(q, dump=True)
-    plan = make_plan(pts, K, 3, prec, leaf_max=24)
+    plan = make_plan(pts, K, 3, prec, leaf_max=leaf_max)
     phi = apply_plan(plan, q, prec)
     for l in range(o.top, o.tree.nlev + 1):
         nb = o.tree.levels[l].nbox

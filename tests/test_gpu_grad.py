@@ -47,6 +47,25 @@ def test_apply_grad_vs_direct_grad(ellipsoid_case, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_grad_clustered_leaves(prec):
+    """Adaptive tree with leaf_max 64 over a sphere and a dense cluster: near-field gradients of
+    leaves with 33-64 points (two targets per lane) and of the tiled large leaves, against the
+    direct-sum gradient at sampled targets, most of them in the cluster."""
+    import torch
+    pts = np.concatenate([synth.sphere(3000, 1.5, seed=5111),
+                          synth.normal(5112, 3 * 2000).reshape(2000, 3) * 0.04 + np.array([0.2, -0.8, 0.4])])
+    q = synth.complex_normal(5113, pts.shape[0])[0]
+    plan = make_plan(pts, K, 3, prec, leaf_max=64)
+    phi, grad = plan.apply_grad(torch.as_tensor(q.astype(cdtype(prec)), device="cuda:0"))
+    phi, grad = phi.cpu().numpy(), grad.cpu().numpy()
+    rng = np.random.default_rng(8)
+    tg = np.sort(np.concatenate([rng.choice(3000, 100, replace=False), 3000 + rng.choice(2000, 412, replace=False)]))
+    assert rel(grad[tg], direct.direct_grad(pts, q, K, targets=tg)) < 3e-3
+    assert rel(phi[tg], direct.direct(pts, q, K, targets=tg)) < 1e-3
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_autograd_loss_gradients(ellipsoid_case, prec):
     import torch
 
