@@ -230,6 +230,19 @@ struct Plan {
     int64_t n_small32 = 0;
     int2* p2p_tiles = nullptr;     // [n_tiles] (leaf-table index, first target offset)
     int64_t n_tiles = 0;
+    // symmetric near field of the large leaves (one right-hand side, no gradient): each pair of
+    // mutually near large leaves (A, B), A < B in the leaf table, is evaluated once by
+    // k_p2p_sym, whose work items (A, target offset in A, B, scratch offset) write both
+    // directions' partial sums to sym_buf; k_p2p_sym_reduce adds them to the potentials in a fixed
+    // order.  The tiled kernel then takes the large leaves' remaining near boxes (asym_*).
+    int64_t n_sym_items = 0;
+    int4* sym_items = nullptr;     // [n_sym_items]
+    void* sym_buf = nullptr;       // complex [sum over items of kP2PTile + |B|]
+    int* asym_off = nullptr;       // [nleaf_total+1] CSR over the leaf table (large leaves only)
+    int* asym_lev = nullptr;
+    int* asym_box = nullptr;
+    int* sym_red_off = nullptr;    // [nleaf_total+1] per large leaf: its blocks in sym_buf
+    int2* sym_red = nullptr;       // (item scratch offset, target offset of the item in this leaf, or -1: B side)
     TreeLevel lev[kMaxLev + 1];
     FarLevel far[kMaxLev + 1];
     // apply buffers

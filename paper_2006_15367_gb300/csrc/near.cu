@@ -294,6 +294,113 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ 
     }
 }
 
+// Symmetric near field of two mutually near large leaves A and B (the kernel e^{ikR}/R is
+// symmetric in its two points): one CTA per work item (A, target offset o in A, B, scratch
+// offset); thread t holds target o + t of A, and each warp meets 32 sources of B at a time in
+// 32 rotation steps (lane l takes source (l + s) mod 32 at step s): the forward term q_j K_ij
+// goes to the lane's target sum, the reverse term q_i K_ij to an accumulator that moves to the
+// next lower lane after every step, so after the 32 steps lane l holds the warp's sum for source
+// l.  The four warps' sums are added in a fixed order.  Writes the forward sums of the item's
+// targets to scratch[off .. off + kP2PTile) and the reverse sums of all of B to
+// scratch[off + kP2PTile ..); k_p2p_sym_reduce adds them to the potentials.
+template <typename R, typename C>
+__global__ void __launch_bounds__(kP2PTile) k_p2p_sym(const int4* __restrict__ items, const int* __restrict__ leaf_level,
+                                                      const int* __restrict__ leaf_box, LevelRanges LR,
+                                                      const double* __restrict__ pos, const C* __restrict__ qs, R kpi,
+                                                      C* __restrict__ scratch) {
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ R sx[32], sy[32], sz[32];
+    __shared__ C sq[32];
+    __shared__ C red[kP2PTile / 32][32];
+    const int4 it = items[blockIdx.x];
+    const int la = leaf_level[it.x], ba = leaf_box[it.x];
+    const int lb = leaf_level[it.z], bb = leaf_box[it.z];
+    const int t0 = LR.begin[la][ba], t1 = LR.end[la][ba];
+    const int u0 = LR.begin[lb][bb], nb = LR.end[lb][bb] - u0;
+    const double* ct = LR.center[la] + 3 * ba;
+    const double cx = ct[0], cy = ct[1], cz = ct[2];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int i = t0 + it.y + threadIdx.x;
+    const bool valid = i < t1;
+    R x = 0, y = 0, z = 0;
+    C qi = cmake<C>(0, 0);                       // an absent target contributes nothing in reverse
+    if (valid) {
+        x = (R)(pos[3 * (int64_t)i] - cx);
+        y = (R)(pos[3 * (int64_t)i + 1] - cy);
+        z = (R)(pos[3 * (int64_t)i + 2] - cz);
+        qi = qs[i];
+    }
+    C fwd = cmake<C>(0, 0);
+    C* out = scratch + (unsigned)it.w;
+    for (int k0 = 0; k0 < nb; k0 += 32) {
+        __syncthreads();                         // the previous chunk's sources and sums are consumed
+        if (threadIdx.x < 32) {
+            const int j = k0 + (int)threadIdx.x;
+            R px = 0, py = 0, pz = 0;
+            C qj = cmake<C>(0, 0);               // past the end of B: a zero charge
+            if (j < nb) {
+                const int64_t jj = u0 + j;
+                px = (R)(pos[3 * jj] - cx);
+                py = (R)(pos[3 * jj + 1] - cy);
+                pz = (R)(pos[3 * jj + 2] - cz);
+                qj = qs[jj];
+            }
+            sx[threadIdx.x] = px;
+            sy[threadIdx.x] = py;
+            sz[threadIdx.x] = pz;
+            sq[threadIdx.x] = qj;
+        }
+        __syncthreads();
+        C rev = cmake<C>(0, 0);
+#pragma unroll 4
+        for (int st = 0; st < 32; ++st) {
+            const int js = (lane + st) & 31;
+            const R dx = x - sx[js], dy = y - sy[js], dz = z - sz[js];
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            const R inv = r2 > (R)0 ? rsq(r2) : (R)0;
+            R sn, cs;
+            scpi_fast(kpi * (r2 * inv), sn, cs);
+            const C g = cmake<C>(cs * inv, sn * inv);
+            cfma(fwd, sq[js], g);
+            cfma(rev, qi, g);
+            rev.x = __shfl_sync(FULL, rev.x, (lane + 1) & 31);
+            rev.y = __shfl_sync(FULL, rev.y, (lane + 1) & 31);
+        }
+        red[wl][lane] = rev;
+        __syncthreads();
+        if (threadIdx.x < 32 && k0 + (int)threadIdx.x < nb) {
+            C sum = red[0][threadIdx.x];
+#pragma unroll
+            for (int w = 1; w < kP2PTile / 32; ++w) sum = cadd(sum, red[w][threadIdx.x]);
+            out[kP2PTile + k0 + threadIdx.x] = sum;
+        }
+    }
+    out[threadIdx.x] = valid ? fwd : cmake<C>(0, 0);
+}
+
+// Adds the symmetric pass's partial sums to the potentials of the large leaves' points, one CTA
+// per target tile, each point's blocks in the leaf's fixed order (deterministic).
+template <typename C>
+__global__ void __launch_bounds__(kP2PTile) k_p2p_sym_reduce(const int2* __restrict__ tiles, const int* __restrict__ leaf_level,
+                                                             const int* __restrict__ leaf_box, LevelRanges LR,
+                                                             const int* __restrict__ red_off, const int2* __restrict__ red,
+                                                             const C* __restrict__ scratch, C* __restrict__ phis) {
+    const int2 tile = tiles[blockIdx.x];
+    const int w = tile.x;
+    const int l = leaf_level[w], b = leaf_box[w];
+    const int t0 = LR.begin[l][b], t1 = LR.end[l][b];
+    const int u = tile.y + threadIdx.x;
+    if (t0 + u >= t1) return;
+    C acc = cmake<C>(0, 0);
+    for (int e = red_off[w]; e < red_off[w + 1]; ++e) {
+        const int2 r = red[e];
+        const C* blk = scratch + (unsigned)r.x;
+        if (r.y < 0) acc = cadd(acc, blk[kP2PTile + u]);
+        else if (u >= r.y && u < r.y + kP2PTile) acc = cadd(acc, blk[u - r.y]);
+    }
+    phis[t0 + u] = cadd(phis[t0 + u], acc);
+}
+
 // caller order (rows of stride ld) <-> Morton order (rows of stride n)
 template <typename C>
 __global__ void k_permute_in(int64_t n, int nrhs, int64_t ld, const int* __restrict__ perm, const C* __restrict__ q,
@@ -350,7 +457,8 @@ static void near_apply(Plan& p, const void* qs, void* phis, void* grads, bool ti
     }
     const int64_t n32 = p.n_small32, nmid = p.n_small - p.n_small32, sn = p.n;
     const R kpi = (R)(p.k / M_PI);
-    StageTimer st(p, MLFMA_STAGE_P2P, 0, (n32 > 0) + (nmid > 0) + (p.n_tiles > 0), timed);
+    const bool sym_pass = NR == 1 && !grads && p.n_tiles > 0 && p.n_sym_items > 0;
+    StageTimer st(p, MLFMA_STAGE_P2P, 0, (n32 > 0) + (nmid > 0) + (p.n_tiles > 0) + 2 * sym_pass, timed);
     if (n32 > 0) {
         if (grads)
             k_p2p<R, C, true, 1, false><<<nblk(n32, 4), 128, 0, p.stream>>>(
@@ -375,15 +483,28 @@ static void near_apply(Plan& p, const void* qs, void* phis, void* grads, bool ti
         MLFMA_LAUNCH_CHECK();
     }
     if (p.n_tiles > 0) {
+        // one right-hand side without gradients: pairs of mutually near large leaves go through the
+        // symmetric pass, the tiled kernel takes the rest of their near boxes
+        const bool sym = NR == 1 && !grads && p.n_sym_items > 0;
+        const int* off = sym ? p.asym_off : p.near_off;
+        const int* nlv = sym ? p.asym_lev : p.near_lev;
+        const int* nbx = sym ? p.asym_box : p.near_box;
         if (grads)
             k_p2p_tile<R, C, true, 1><<<(unsigned)p.n_tiles, kP2PTile, 0, p.stream>>>(
-                p.p2p_tiles, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, sn, kpi,
-                (C*)phis, (C*)grads);
+                p.p2p_tiles, p.leaf_level, p.leaf_box, off, nlv, nbx, LR, p.pos, (const C*)qs, sn, kpi, (C*)phis,
+                (C*)grads);
         else
             k_p2p_tile<R, C, false, NR><<<(unsigned)p.n_tiles, kP2PTile, 0, p.stream>>>(
-                p.p2p_tiles, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, sn, kpi,
-                (C*)phis, nullptr);
+                p.p2p_tiles, p.leaf_level, p.leaf_box, off, nlv, nbx, LR, p.pos, (const C*)qs, sn, kpi, (C*)phis, nullptr);
         MLFMA_LAUNCH_CHECK();
+        if (sym) {
+            k_p2p_sym<R, C><<<(unsigned)p.n_sym_items, kP2PTile, 0, p.stream>>>(p.sym_items, p.leaf_level, p.leaf_box, LR,
+                                                                               p.pos, (const C*)qs, kpi, (C*)p.sym_buf);
+            MLFMA_LAUNCH_CHECK();
+            k_p2p_sym_reduce<C><<<(unsigned)p.n_tiles, kP2PTile, 0, p.stream>>>(
+                p.p2p_tiles, p.leaf_level, p.leaf_box, LR, p.sym_red_off, p.sym_red, (const C*)p.sym_buf, (C*)phis);
+            MLFMA_LAUNCH_CHECK();
+        }
     }
 }
 

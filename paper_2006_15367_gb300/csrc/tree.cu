@@ -8,6 +8,9 @@
 #include <cstdio>
 #include <cstring>
 
+#include <set>
+#include <unordered_map>
+
 #include "common.cuh"
 
 namespace mlfma {
@@ -932,6 +935,91 @@ void build_p2p_work(Plan& p) {
         if (!bg.empty()) MLFMA_CUDA(cudaMemcpyAsync(L.big_leaves, bg.data(), bg.size() * sizeof(int), cudaMemcpyHostToDevice, s));
         if (!bt.empty()) MLFMA_CUDA(cudaMemcpyAsync(L.big_tiles, bt.data(), bt.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
         MLFMA_CUDA(cudaStreamSynchronize(s));
+    }
+    // ---- symmetric pairs of large leaves: both near to each other, each evaluated once
+    if (!tiles.empty()) {
+        std::vector<int> noff(nl + 1), nlev, nbox;
+        MLFMA_CUDA(cudaMemcpyAsync(noff.data(), p.near_off, (nl + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+        MLFMA_CUDA(cudaStreamSynchronize(s));
+        nlev.resize(noff[nl]);
+        nbox.resize(noff[nl]);
+        if (noff[nl] > 0) {
+            MLFMA_CUDA(cudaMemcpyAsync(nlev.data(), p.near_lev, noff[nl] * sizeof(int), cudaMemcpyDeviceToHost, s));
+            MLFMA_CUDA(cudaMemcpyAsync(nbox.data(), p.near_box, noff[nl] * sizeof(int), cudaMemcpyDeviceToHost, s));
+            MLFMA_CUDA(cudaStreamSynchronize(s));
+        }
+        std::unordered_map<long long, int> leaf_at;   // (level, box) -> leaf-table index of large leaves
+        for (int64_t t = 0; t < nl; ++t)
+            if (hs[t] > kSmallLeaf) leaf_at[((long long)lev_of[t] << 32) | (unsigned)box_of[t]] = (int)t;
+        auto big_of = [&](int e) {
+            auto f = leaf_at.find(((long long)nlev[e] << 32) | (unsigned)nbox[e]);
+            return f == leaf_at.end() ? -1 : f->second;
+        };
+        std::set<std::pair<int, int>> nearbig;     // (A, B): B a large near box of large leaf A, A != B
+        for (int64_t t = 0; t < nl; ++t) {
+            if (hs[t] <= kSmallLeaf) continue;
+            for (int e = noff[t]; e < noff[t + 1]; ++e) {
+                const int b = big_of(e);
+                if (b >= 0 && b != (int)t) nearbig.insert({(int)t, b});
+            }
+        }
+        auto mutual = [&](int a, int b) { return nearbig.count({a, b}) && nearbig.count({b, a}); };
+        std::vector<int> aoff(nl + 1, 0), alev, abox;
+        struct Item { int a, o, b; long long work; };
+        std::vector<Item> items;
+        for (int64_t t = 0; t < nl; ++t) {
+            aoff[t] = (int)alev.size();
+            if (hs[t] <= kSmallLeaf) continue;
+            for (int e = noff[t]; e < noff[t + 1]; ++e) {
+                const int b = big_of(e);
+                if (b >= 0 && b != (int)t && mutual((int)t, b)) {
+                    if (b > (int)t)
+                        for (int o = 0; o < hs[t]; o += kP2PTile)
+                            items.push_back({(int)t, o, b, (long long)std::min(kP2PTile, hs[t] - o) * hs[b]});
+                    continue;
+                }
+                alev.push_back(nlev[e]);
+                abox.push_back(nbox[e]);
+            }
+        }
+        aoff[nl] = (int)alev.size();
+        // scratch offsets, then heavy items first
+        std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.work > y.work; });
+        long long scratch = 0;
+        std::vector<int4> hitems;
+        std::vector<std::vector<int2>> red(nl);
+        for (const Item& it : items) {
+            hitems.push_back(make_int4(it.a, it.o, it.b, (int)scratch));
+            red[it.a].push_back(make_int2((int)scratch, it.o));
+            red[it.b].push_back(make_int2((int)scratch, -1));
+            scratch += kP2PTile + hs[it.b];
+        }
+        if (!items.empty() && scratch < (1ll << 31)) {
+            std::vector<int> roff(nl + 1, 0);
+            std::vector<int2> rflat;
+            for (int64_t t = 0; t < nl; ++t) {
+                roff[t] = (int)rflat.size();
+                rflat.insert(rflat.end(), red[t].begin(), red[t].end());
+            }
+            roff[nl] = (int)rflat.size();
+            p.n_sym_items = (int64_t)hitems.size();
+            p.sym_items = p.mem.make<int4>(hitems.size());
+            p.sym_buf = p.mem.get((size_t)scratch * csize(p));
+            p.asym_off = p.mem.make<int>(nl + 1);
+            p.asym_lev = p.mem.make<int>(std::max<size_t>(alev.size(), 1));
+            p.asym_box = p.mem.make<int>(std::max<size_t>(abox.size(), 1));
+            p.sym_red_off = p.mem.make<int>(nl + 1);
+            p.sym_red = p.mem.make<int2>(std::max<size_t>(rflat.size(), 1));
+            MLFMA_CUDA(cudaMemcpyAsync(p.sym_items, hitems.data(), hitems.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+            MLFMA_CUDA(cudaMemcpyAsync(p.asym_off, aoff.data(), (nl + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+            if (!alev.empty()) {
+                MLFMA_CUDA(cudaMemcpyAsync(p.asym_lev, alev.data(), alev.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+                MLFMA_CUDA(cudaMemcpyAsync(p.asym_box, abox.data(), abox.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+            }
+            MLFMA_CUDA(cudaMemcpyAsync(p.sym_red_off, roff.data(), (nl + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+            MLFMA_CUDA(cudaMemcpyAsync(p.sym_red, rflat.data(), rflat.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+            MLFMA_CUDA(cudaStreamSynchronize(s));
+        }
     }
     auto leaf_work = [&](int t) { return (long long)hs[t] * hsrc[t]; };
     heavy_first(small, leaf_work);

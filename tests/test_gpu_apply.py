@@ -81,11 +81,12 @@ def test_six_digits_fp64_half_wavelength_leaves(sphere4k):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("leaf_max", [24, 64])
+@pytest.mark.parametrize("leaf_max", [24, 64, 200])
 def test_adaptive_tree_matches_oracle(prec, leaf_max):
     """A sphere with a dense cluster, adaptive tree: every stage against the oracle.  With
     leaf_max 64 the cluster's leaves hold 33-64 points (the near-field warp takes two targets
-    per lane) and the deepest leaves more (tiles of 128 targets)."""
+    per lane); with 200 they hold up to 200 (tiles of 128 targets, and the pairs of mutually near
+    large leaves evaluated once by the symmetric pass)."""
     pts = np.concatenate([synth.sphere(3000, 1.5, seed=71),
                           synth.normal(72, 3 * 1200).reshape(1200, 3) * 0.05 + np.array([0.9, 0.2, -0.3])])
     q = synth.complex_normal(73, pts.shape[0])[0]
