@@ -30,6 +30,12 @@ __device__ __forceinline__ void scpi_fast(float x, float& s, float& c) {
 }
 __device__ __forceinline__ void scpi_fast(double x, double& s, double& c) { sincospi(x, &s, &c); }
 
+// a staged source: position relative to the target leaf centre and one more value
+template <typename R>
+struct __align__(4 * sizeof(R) > 16 ? 16 : 4 * sizeof(R)) SrcPos {
+    R x, y, z, w;
+};
+
 struct LevelRanges {
     const int* begin[kMaxLev + 1];
     const int* end[kMaxLev + 1];
@@ -297,7 +303,8 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ 
 // Symmetric near field of two mutually near large leaves A and B (the kernel e^{ikR}/R is
 // symmetric in its two points): one CTA per work item (A, target offset o in A, B, scratch
 // offset); thread t holds target o + t of A, and each warp meets 32 sources of B at a time in
-// 32 rotation steps (lane l takes source (l + s) mod 32 at step s): the forward term q_j K_ij
+// 32 rotation steps (lane l takes source (l + s) mod 32 at step s; the chunk is staged twice in a
+// row, so that source is entry l + s): the forward term q_j K_ij
 // goes to the lane's target sum, the reverse term q_i K_ij to an accumulator that moves to the
 // next lower lane after every step, so after the 32 steps lane l holds the warp's sum for source
 // l.  The four warps' sums are added in a fixed order.  Writes the forward sums of the item's
@@ -309,8 +316,10 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_sym(const int4* __restrict__ i
                                                       const double* __restrict__ pos, const C* __restrict__ qs, R kpi,
                                                       C* __restrict__ scratch) {
     constexpr unsigned FULL = 0xffffffffu;
-    __shared__ R sx[32], sy[32], sz[32];
-    __shared__ C sq[32];
+    // the chunk's 32 sources twice in a row, so lane l's source at step s is entry l + s: position
+    // and real part of the charge in one record, imaginary part beside it
+    __shared__ SrcPos<R> sp[64];
+    __shared__ R sqi[64];
     __shared__ C red[kP2PTile / 32][32];
     const int4 it = items[blockIdx.x];
     const int la = leaf_level[it.x], ba = leaf_box[it.x];
@@ -336,32 +345,34 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_sym(const int4* __restrict__ i
         __syncthreads();                         // the previous chunk's sources and sums are consumed
         if (threadIdx.x < 32) {
             const int j = k0 + (int)threadIdx.x;
-            R px = 0, py = 0, pz = 0;
-            C qj = cmake<C>(0, 0);               // past the end of B: a zero charge
+            SrcPos<R> v{(R)0, (R)0, (R)0, (R)0}; // past the end of B: a zero charge
+            R vi = 0;
             if (j < nb) {
                 const int64_t jj = u0 + j;
-                px = (R)(pos[3 * jj] - cx);
-                py = (R)(pos[3 * jj + 1] - cy);
-                pz = (R)(pos[3 * jj + 2] - cz);
-                qj = qs[jj];
+                const C qj = qs[jj];
+                v = SrcPos<R>{(R)(pos[3 * jj] - cx), (R)(pos[3 * jj + 1] - cy), (R)(pos[3 * jj + 2] - cz), qj.x};
+                vi = qj.y;
             }
-            sx[threadIdx.x] = px;
-            sy[threadIdx.x] = py;
-            sz[threadIdx.x] = pz;
-            sq[threadIdx.x] = qj;
+            sp[threadIdx.x] = v;
+            sp[threadIdx.x + 32] = v;
+            sqi[threadIdx.x] = vi;
+            sqi[threadIdx.x + 32] = vi;
         }
         __syncthreads();
         C rev = cmake<C>(0, 0);
+        const SrcPos<R>* pl = sp + lane;
+        const R* ql = sqi + lane;
 #pragma unroll 4
         for (int st = 0; st < 32; ++st) {
-            const int js = (lane + st) & 31;
-            const R dx = x - sx[js], dy = y - sy[js], dz = z - sz[js];
+            const SrcPos<R> ps = pl[st];
+            const R qjy = ql[st];
+            const R dx = x - ps.x, dy = y - ps.y, dz = z - ps.z;
             const R r2 = dx * dx + dy * dy + dz * dz;
             const R inv = r2 > (R)0 ? rsq(r2) : (R)0;
             R sn, cs;
             scpi_fast(kpi * (r2 * inv), sn, cs);
             const C g = cmake<C>(cs * inv, sn * inv);
-            cfma(fwd, sq[js], g);
+            cfma(fwd, cmake<C>(ps.w, qjy), g);
             cfma(rev, qi, g);
             rev.x = __shfl_sync(FULL, rev.x, (lane + 1) & 31);
             rev.y = __shfl_sync(FULL, rev.y, (lane + 1) & 31);
