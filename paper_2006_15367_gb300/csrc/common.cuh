@@ -231,10 +231,11 @@ struct Plan {
     int2* p2p_tiles = nullptr;     // [n_tiles] (leaf-table index, first target offset)
     int64_t n_tiles = 0;
     // symmetric near field of the large leaves (one right-hand side, no gradient): each pair of
-    // mutually near large leaves (A, B), A < B in the leaf table, is evaluated once by
-    // k_p2p_sym, whose work items (A, target offset in A, B, scratch offset) write both
-    // directions' partial sums to sym_buf; k_p2p_sym_reduce adds them to the potentials in a fixed
-    // order.  The tiled kernel then takes the large leaves' remaining near boxes (asym_*).
+    // mutually near large leaves (A, B), A < B in the leaf table, and each large leaf with itself
+    // (pairs j > i) is evaluated once by k_p2p_sym, whose work items (A, target offset in A, B,
+    // scratch offset) write both directions' partial sums to sym_buf; k_p2p_sym_reduce adds them
+    // to the potentials in a fixed order.  The tiled kernel then takes the large leaves' remaining
+    // near boxes (asym_*).
     int64_t n_sym_items = 0;
     int4* sym_items = nullptr;     // [n_sym_items]
     void* sym_buf = nullptr;       // complex [sum over items of kP2PTile + |B|]

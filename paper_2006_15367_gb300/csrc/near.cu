@@ -301,8 +301,9 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ 
 }
 
 // Symmetric near field of two mutually near large leaves A and B (the kernel e^{ikR}/R is
-// symmetric in its two points): one CTA per work item (A, target offset o in A, B, scratch
-// offset); thread t holds target o + t of A, and each warp meets 32 sources of B at a time in
+// symmetric in its two points), and of a large leaf with itself (B = A: the sources from the
+// tile's first point on, pairs j > i only; the reverse sums below o are zero): one CTA per work
+// item (A, target offset o in A, B, scratch offset); thread t holds target o + t of A, and each warp meets 32 sources of B at a time in
 // 32 rotation steps (lane l takes source (l + s) mod 32 at step s; the chunk is staged twice in a
 // row, so that source is entry l + s): the forward term q_j K_ij
 // goes to the lane's target sum, the reverse term q_i K_ij to an accumulator that moves to the
@@ -329,7 +330,9 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_sym(const int4* __restrict__ i
     const double* ct = LR.center[la] + 3 * ba;
     const double cx = ct[0], cy = ct[1], cz = ct[2];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int i = t0 + it.y + threadIdx.x;
+    const bool self = it.x == it.z;             // B = A: pairs j > i only
+    const int iu = it.y + (int)threadIdx.x;      // target index within A
+    const int i = t0 + iu;
     const bool valid = i < t1;
     R x = 0, y = 0, z = 0;
     C qi = cmake<C>(0, 0);                       // an absent target contributes nothing in reverse
@@ -341,7 +344,9 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_sym(const int4* __restrict__ i
     }
     C fwd = cmake<C>(0, 0);
     C* out = scratch + (unsigned)it.w;
-    for (int k0 = 0; k0 < nb; k0 += 32) {
+    const int kstart = self ? it.y : 0;          // B = A: sources from the tile's first point on
+    for (int j = threadIdx.x; j < kstart; j += blockDim.x) out[kP2PTile + j] = cmake<C>(0, 0);
+    for (int k0 = kstart; k0 < nb; k0 += 32) {
         __syncthreads();                         // the previous chunk's sources and sums are consumed
         if (threadIdx.x < 32) {
             const int j = k0 + (int)threadIdx.x;
@@ -362,13 +367,16 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_sym(const int4* __restrict__ i
         C rev = cmake<C>(0, 0);
         const SrcPos<R>* pl = sp + lane;
         const R* ql = sqi + lane;
+        // B = A: the chunks that overlap the tile keep only j > i (the chunks above it need no mask)
+        const bool mask = self && k0 < it.y + kP2PTile;
 #pragma unroll 4
         for (int st = 0; st < 32; ++st) {
             const SrcPos<R> ps = pl[st];
             const R qjy = ql[st];
             const R dx = x - ps.x, dy = y - ps.y, dz = z - ps.z;
             const R r2 = dx * dx + dy * dy + dz * dz;
-            const R inv = r2 > (R)0 ? rsq(r2) : (R)0;
+            R inv = r2 > (R)0 ? rsq(r2) : (R)0;
+            if (mask && k0 + ((lane + st) & 31) <= iu) inv = (R)0;
             R sn, cs;
             scpi_fast(kpi * (r2 * inv), sn, cs);
             const C g = cmake<C>(cs * inv, sn * inv);

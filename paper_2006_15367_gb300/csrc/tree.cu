@@ -936,7 +936,8 @@ void build_p2p_work(Plan& p) {
         if (!bt.empty()) MLFMA_CUDA(cudaMemcpyAsync(L.big_tiles, bt.data(), bt.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
         MLFMA_CUDA(cudaStreamSynchronize(s));
     }
-    // ---- symmetric pairs of large leaves: both near to each other, each evaluated once
+    // ---- symmetric pairs of large leaves: both near to each other (or a leaf with itself),
+    // each pair of points evaluated once
     if (!tiles.empty()) {
         std::vector<int> noff(nl + 1), nlev, nbox;
         MLFMA_CUDA(cudaMemcpyAsync(noff.data(), p.near_off, (nl + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -972,6 +973,11 @@ void build_p2p_work(Plan& p) {
             if (hs[t] <= kSmallLeaf) continue;
             for (int e = noff[t]; e < noff[t + 1]; ++e) {
                 const int b = big_of(e);
+                if (b == (int)t) {                     // the leaf with itself: pairs j > i, once
+                    for (int o = 0; o < hs[t]; o += kP2PTile)
+                        items.push_back({(int)t, o, b, (long long)std::min(kP2PTile, hs[t] - o) * (hs[t] - o)});
+                    continue;
+                }
                 if (b >= 0 && b != (int)t && mutual((int)t, b)) {
                     if (b > (int)t)
                         for (int o = 0; o < hs[t]; o += kP2PTile)
