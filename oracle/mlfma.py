@@ -31,6 +31,9 @@ projection per Fourier mode (the 'global interpolation' the paper insists on,
 Sec. 2 Related Work); truncation L = ceil(kD + 1.8 d0^(2/3) (kD)^(1/3)) with
 D = sqrt(3) * edge, d0 = digits + DIGIT_MARGIN (excess-bandwidth rule, not
 printed in the paper); M2L starts at the highest level with a non-empty V list.
+Optional sampled translation operators (Sec. 3.2.3, "Translation Operators"): T tabulated in
+the angle psi between khat and X and interpolated by P-point Lagrange weights
+(sampled_translation_operator), at the levels with boxes of a wavelength or more.
 """
 from __future__ import annotations
 
@@ -102,6 +105,71 @@ def translation_operator(grid: Grid, k: float, X: np.ndarray) -> np.ndarray:
     return coef @ P
 
 
+# Sampled translation operators (Sec. 3.2.3, "Translation Operators": where the operators do
+# not fit in memory they are sampled and interpolated).  T_X(khat) depends on khat only through
+# the angle psi between khat and Xhat: T = sum_n i^n (2n+1) h_n(k|X|) P_n(cos psi).  Each
+# P_n(cos psi) is a cosine polynomial of degree n, so T is an even, 2 pi-periodic trigonometric
+# polynomial of degree L in psi.  Reading (the paper defers the technique to its reference):
+# tabulate T at the equispaced angles psi_i = i pi / S, S = s L (s: oversampling over the
+# Nyquist spacing pi / L), for i = -P .. S + P, and evaluate it at each sample's psi with the
+# P-point Lagrange interpolant whose nodes straddle psi (P even, psi in the middle interval).
+# The padded entries are T at cos(psi_i): by evenness and periodicity they are the reflections
+# across psi = 0 and psi = pi.  Only levels whose boxes are at least one wavelength wide
+# (k edge >= 2 pi) are sampled: their tables are the large ones, while at sub-wavelength boxes
+# |T| grows far above the signatures it produces (low-frequency growth of h_n), which would
+# magnify the interpolation error; those levels keep their exact operators.
+SAMPLED_ORDER = 10
+
+
+def level_is_sampled(k: float, edge: float, s: int) -> bool:
+    """Sampled operators apply at levels with k edge >= 2 pi (relative slack 1e-9)."""
+    return s > 0 and k * edge >= 2.0 * math.pi * (1.0 - 1e-9)
+
+
+def lagrange_weights(t, P: int) -> np.ndarray:
+    """l_j(t) = prod_{m != j} (t - m) / (j - m), j = 0..P-1: the P-point Lagrange basis on the
+    nodes 0..P-1 evaluated at t (any shape); returns [P, *shape(t)]."""
+    t = np.asarray(t, dtype=np.float64)
+    w = np.ones((P,) + t.shape)
+    for j in range(P):
+        for m in range(P):
+            if m != j:
+                w[j] *= (t - m) / (j - m)
+    return w
+
+
+def operator_samples(L: int, k: float, r: float, s: int, P: int = SAMPLED_ORDER) -> np.ndarray:
+    """T at psi_i = i pi / (s L), i = -P .. s L + P, for |X| = r: [s L + 2 P + 1] complex."""
+    S = s * L
+    h = special.spherical_hn_all(L, k * r)
+    n = np.arange(L + 1)
+    coef = (1j ** n) * (2 * n + 1) * h
+    psi = np.arange(-P, S + P + 1) * (math.pi / S)
+    return coef @ special.legendre_all(L, np.cos(psi))
+
+
+def sampled_translation_operator(grid: Grid, k: float, X: np.ndarray, s: int, P: int = SAMPLED_ORDER) -> np.ndarray:
+    """T_X(khat_p) interpolated from operator_samples at psi_p = angle(khat_p, Xhat)."""
+    X = np.asarray(X, dtype=np.float64)
+    r = float(np.linalg.norm(X))
+    tab = operator_samples(grid.L, k, r, s, P)
+    xh = X / r
+    psi = np.arctan2(np.linalg.norm(np.cross(grid.dirs, xh), axis=1), grid.dirs @ xh)
+    return interpolate_samples(tab, psi, s * grid.L, P)
+
+
+def interpolate_samples(tab: np.ndarray, psi: np.ndarray, S: int, P: int = SAMPLED_ORDER) -> np.ndarray:
+    """sum_j l_j(t) tab[psi_{i0 + j}]: nodes i0 .. i0 + P - 1, i0 = floor(psi / h) - P/2 + 1,
+    t = psi / h - i0 (the middle interval), h = pi / S; tab[i + P] holds the value at psi_i."""
+    u = np.asarray(psi, dtype=np.float64) / (math.pi / S)
+    i0 = np.floor(u).astype(np.int64) - (P // 2 - 1)         # first node: psi_{i0}
+    w = lagrange_weights(u - i0, P)
+    out = np.zeros(u.shape, dtype=np.result_type(tab.dtype, np.float64))
+    for j in range(P):
+        out += w[j] * tab[i0 + j + P]
+    return out
+
+
 def theta_maps(gc: Grid, gp: Grid):
     """A_m[i', i] = sum_{n=|m|}^{L_c} Pbar_n^m(x'_i') Pbar_n^m(x_i) w_i, m = 0..L_c."""
     out = []
@@ -163,7 +231,10 @@ class OracleMLFMA:
     """Plain FP64 MLFMA with per-stage dumps.  Level-uniform or adaptive tree."""
 
     def __init__(self, points, k: float, digits: int, leaf_max: int = 0, leaf_edge: float | None = None,
-                 max_depth: int = 12, margin: int = DIGIT_MARGIN):
+                 max_depth: int = 12, margin: int = DIGIT_MARGIN, sampled_operators: int = 0):
+        # sampled_operators = s > 0: M2L of the levels with k edge >= 2 pi uses
+        # sampled_translation_operator with oversampling s
+        self.sampled = int(sampled_operators)
         self.k = float(k)
         self.digits = int(digits)
         self.points = np.asarray(points, dtype=np.float64)
@@ -202,7 +273,10 @@ class OracleMLFMA:
         key = (l, tuple(int(v) for v in off))
         if key not in self._T:
             X = np.asarray(off, dtype=np.float64) * self.tree.levels[l].edge
-            self._T[key] = translation_operator(self.grid[l], self.k, X)
+            if level_is_sampled(self.k, self.tree.levels[l].edge, self.sampled):
+                self._T[key] = sampled_translation_operator(self.grid[l], self.k, X, self.sampled)
+            else:
+                self._T[key] = translation_operator(self.grid[l], self.k, X)
         return self._T[key]
 
     def shift_m2m(self, l: int, dc: np.ndarray) -> np.ndarray:

@@ -305,3 +305,115 @@ def test_grid_quadrature_exact_and_antipodally_symmetric(L):
     anti = ((L - i) * g.nph + (j + g.nph // 2) % g.nph).reshape(-1)
     assert np.allclose(g.dirs[anti], -g.dirs, atol=1e-14)
     assert np.allclose(g.w[anti], g.w, rtol=1e-14)
+
+
+# --------------------------------------------------------------------------- sampled operators
+@pytest.mark.parametrize("P", [4, 10])
+def test_lagrange_weights_reproduce_polynomials(P):
+    """The P-point interpolant is exact on polynomials of degree < P and is a delta at the nodes."""
+    rng = np.random.default_rng(5)
+    c = rng.standard_normal(P)                          # degree P - 1
+    t = rng.uniform(P // 2 - 1, P // 2, 7)
+    w = mlfma.lagrange_weights(t, P)
+    vals = np.polyval(c, np.arange(P, dtype=float))
+    assert np.allclose(vals @ w, np.polyval(c, t), rtol=1e-11, atol=1e-11 * np.max(np.abs(vals)))
+    for j in range(P):
+        assert np.array_equal(mlfma.lagrange_weights(float(j), P), np.eye(P)[j])
+
+
+def test_interpolation_stencil_is_centred():
+    """On u^P (u = psi / h) the P-point interpolant errs by exactly prod_j (t - j) (the P-th
+    derivative over P! is 1), with t = u - i0 in the middle interval [P/2 - 1, P/2): this fixes
+    where the stencil sits around each angle."""
+    P, S = mlfma.SAMPLED_ORDER, 40
+    i = np.arange(-P, S + P + 1, dtype=float)
+    for u in (0.3, 5.5, 17.25, 39.9):
+        c = math.floor(u) + 0.5                        # (u - c)^P: same P-th derivative, no cancellation
+        got = mlfma.interpolate_samples((i - c) ** P, np.array([u * math.pi / S]), S, P)[0]
+        t = u - math.floor(u) + (P // 2 - 1)
+        omega = np.prod([t - j for j in range(P)])
+        assert abs((u - c) ** P - got - omega) < 1e-9 * abs(omega), u
+
+
+class _Dirs:
+    """A sampling 'grid' of given directions (translation_operator reads L, K and dirs)."""
+
+    def __init__(self, L, dirs):
+        self.L, self.dirs, self.K = L, dirs, dirs.shape[0]
+
+
+def _bound(s, P):
+    """sqrt(2) (pi / s)^P max_{t in middle interval} prod_j |t - j| / P!: the Lagrange remainder
+    with Bernstein's inequality |f^(P)| <= L^P |f| for a trigonometric polynomial of degree L
+    (node spacing pi / (s L)), real and imaginary parts apart."""
+    t = np.linspace(P // 2 - 1, P // 2, 2001)
+    om_max = np.max(np.abs(np.prod([t - j for j in range(P)], axis=0)))
+    return math.sqrt(2.0) * (math.pi / s) ** P * om_max / math.factorial(P)
+
+
+@pytest.mark.parametrize("edge,digits", [(0.25, 3), (2.0, 3), (1.0, 6)])
+def test_sampled_operator_within_interpolation_bound(edge, digits):
+    """Sampled-and-interpolated operators against the exact (Gegenbauer-pinned) ones: within the
+    Lagrange-Bernstein bound relative to max |T|, and converging at order P in the oversampling.
+    The axis offsets put samples next to psi = 0 and psi = pi, where the stencil reads the
+    reflected entries of the table."""
+    L = mlfma.truncation_L(edge, K, digits)
+    g = mlfma.Grid(L)
+    P = mlfma.SAMPLED_ORDER
+    errs = {}
+    for s in (3, 4, 6):
+        worst = 0.0
+        for off in ((0, 0, 2), (0, 0, -3), (2, 1, 3), (3, 3, 3), (-2, 2, 1)):
+            X = np.array(off, float) * edge
+            T = mlfma.translation_operator(g, K, X)
+            Ts = mlfma.sampled_translation_operator(g, K, X, s)
+            tmax = np.max(np.abs(mlfma.operator_samples(L, K, np.linalg.norm(X), 16)))
+            e = np.max(np.abs(Ts - T)) / tmax
+            assert e <= _bound(s, P), (s, off, e)
+            worst = max(worst, e)
+        errs[s] = worst
+    assert errs[3] / errs[6] > 2.0 ** (P - 3)
+
+
+def test_sampled_operator_exact_at_table_angles():
+    """Directions at the tabulated angles psi_i (both ends included) reproduce T exactly."""
+    L, s, edge = 12, 4, 0.5
+    S = s * L
+    i = np.array([0, 1, 7, S // 2, S - 1, S])
+    psi = i * math.pi / S
+    X = np.array([0.0, 0.0, 2.0]) * edge                 # Xhat = z: psi is the polar angle
+    d = np.stack([np.sin(psi), np.zeros_like(psi), np.cos(psi)], axis=1)
+    g = _Dirs(L, d)
+    Ts = mlfma.sampled_translation_operator(g, K, X, s)
+    T = mlfma.translation_operator(g, K, X)
+    assert np.max(np.abs(Ts - T)) < 1e-12 * np.max(np.abs(T))
+
+
+def test_operator_samples_hold_the_reflections():
+    """Padding entries: T(-psi) = T(psi) and T(pi + psi) = T(pi - psi)."""
+    L, s, P = 9, 3, mlfma.SAMPLED_ORDER
+    S = s * L
+    tab = mlfma.operator_samples(L, K, 1.3, s)
+    assert tab.shape == (S + 2 * P + 1,)
+    for m in range(1, P + 1):
+        assert abs(tab[P - m] - tab[P + m]) < 1e-12 * np.max(np.abs(tab))
+        assert abs(tab[P + S + m] - tab[P + S - m]) < 1e-12 * np.max(np.abs(tab))
+
+
+def test_sampled_levels_are_the_wavelength_sized_boxes():
+    assert mlfma.level_is_sampled(K, 1.0, 6) and mlfma.level_is_sampled(K, 1.0 - 1e-12, 6)
+    assert not mlfma.level_is_sampled(K, 0.5, 6) and not mlfma.level_is_sampled(K, 4.0, 0)
+
+
+def test_mlfma_with_sampled_operators_vs_direct(sphere4k):
+    """The far field with sampled operators (oversampling 6; on this sphere level 3, edge one
+    wavelength, is sampled) meets 3 digits and stays within the operator interpolation error
+    of the full-table MLFMA."""
+    pts, q, prm = sphere4k
+    o = mlfma.OracleMLFMA(pts, prm["k"], 3, sampled_operators=6)
+    assert [l for l in o.L if mlfma.level_is_sampled(o.k, o.tree.levels[l].edge, 6)] == [3]
+    phi_s = o.apply(q[0])
+    phi = mlfma.OracleMLFMA(pts, prm["k"], 3).apply(q[0])
+    ref = direct.direct(pts, q[0], prm["k"])
+    assert np.linalg.norm(phi_s - ref) / np.linalg.norm(ref) < 1e-3
+    assert 0 < np.linalg.norm(phi_s - phi) / np.linalg.norm(phi) < 1e-4
