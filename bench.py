@@ -289,15 +289,17 @@ def measure_forms(dev, pts, q, prm, fp32_ms):
             out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
         torch.cuda.empty_cache()
 
-    def precision(prec):
+    def precision(prec, sampled=0):
         cdt = np.complex128 if prec == "fp64" else np.complex64
         qd = torch.as_tensor(q[0].astype(cdt), device=dev)
         res = torch.empty_like(qd)
-        plan = mf.Plan(ptd, prm["k"], prm["digits"], precision=prec)
+        plan = mf.Plan(ptd, prm["k"], prm["digits"], precision=prec, sampled_operators=sampled)
         t = _time_ms(lambda: plan.apply(qd, res), plan.stream, 3)
         err = _rel_err(mf, torch, ptd, q[0], prm["k"], res, n)
+        info = plan.info()
         plan.close()
-        return {"ms": t, "rel_err_vs_fp64_direct": err}
+        return {"ms": t, "rel_err_vs_fp64_direct": err, "device_bytes": info["device_bytes"],
+                "setup_ms": info["setup_ms"], "sampled_levels": [l for l, v in enumerate(info["sampled"]) if v]}
 
     guarded("fp64", lambda: precision("fp64"))
     guarded("tf32x3", lambda: precision("tf32x3"))
@@ -310,6 +312,21 @@ def measure_forms(dev, pts, q, prm, fp32_ms):
             out["tf32x3_speedup_vs_fp32"] = fp32_ms / out["tf32x3"]["ms"]
         if "ms" in out.get("bf16x3", {}):
             out["bf16x3_speedup_vs_fp32"] = fp32_ms / out["bf16x3"]["ms"]
+
+    # sampled translation operators (Sec. 3.2.3) at the levels with boxes of a wavelength or
+    # more, against the full operator tables: time, accuracy, plan memory and creation time
+    def sampled(prec, s):
+        full = out["fp64"] if prec == "fp64" else precision(prec)
+        smp = precision(prec, s)
+        if "ms" not in full:
+            return smp
+        smp.update({"oversampling": s, "full_ms": full["ms"], "full_rel_err": full["rel_err_vs_fp64_direct"],
+                    "full_device_bytes": full["device_bytes"], "full_setup_ms": full["setup_ms"],
+                    "bytes_saved": full["device_bytes"] - smp["device_bytes"], "time_ratio": smp["ms"] / full["ms"]})
+        return smp
+
+    guarded("sampled_operators_fp32", lambda: sampled("fp32", 6))
+    guarded("sampled_operators_fp64", lambda: sampled("fp64", 8))
 
     def nrhs64():
         Q = synth.complex_normal(2003, n, nrhs=64).astype(np.complex64)

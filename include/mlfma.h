@@ -116,6 +116,23 @@ typedef struct mlfma_options {
                                      a slice of the map in shared memory.  0 (default) or -1: never (the
                                      FFT path with tensor-core theta maps runs everywhere).  Ignored by
                                      FP32 and FP64 plans */
+    int sampled_operators;        /* sampled translation operators (Sec. 3.2.3, "Translation Operators":
+                                     where the operators do not fit, they are sampled and interpolated).
+                                     0 (default): every far level keeps its full table T[316][K].
+                                     s in [3, 32]: a level whose boxes are at least one wavelength wide
+                                     (k edge >= 2 pi) keeps instead, per squared offset length |X/edge|^2,
+                                     T as a function of the angle psi between khat and X, tabulated at
+                                     psi_i = i pi / (s L), i = -10 .. s L + 10 (the padding holds the
+                                     reflections at psi = 0 and pi); M2L interpolates each (offset,
+                                     sample) entry with 10-point Lagrange weights as it stages an
+                                     operator slice in shared memory.  Finer levels keep full tables
+                                     (small, and their large |T| would magnify the interpolation
+                                     error).  Error of the interpolated operators relative to max |T|:
+                                     about 1e-5 (s = 4), 2e-7 (s = 6), 1e-8 (s = 8), 1e-11 (s = 16).
+                                     max |T| exceeds the sums M2L forms by a factor that grows with L
+                                     at small boxes: at 3 digits s = 6 keeps the potentials within
+                                     1e-5 of the full tables' (s = 4: 1e-4); 6 digits (L = 26 at
+                                     one-wavelength boxes, factor ~10^4) need s >= 16 */
 } mlfma_options;
 
 /* Summary of a plan (levels are numbered from the root, level 1). */
@@ -142,6 +159,8 @@ typedef struct mlfma_info {
     int recompute_signatures;                /* the plan's mlfma_options.recompute_signatures */
     int dense[MLFMA_MAX_LEVELS + 1];         /* 1 where the level pair (l, l + 1) runs as dense tensor-core
                                                 maps (mlfma_options.dense_samples) */
+    int sampled_operators;                   /* the plan's mlfma_options.sampled_operators */
+    int sampled[MLFMA_MAX_LEVELS + 1];       /* 1 where the level's M2L interpolates sampled operators */
 } mlfma_info;
 
 /* Tree and list arrays that mlfma_plan_export can copy out (for verification). */
@@ -160,7 +179,11 @@ typedef enum {
     MLFMA_EXPORT_F = 11,          /* complex [nbox(level)][K(level)]: last apply's multipole signatures */
     MLFMA_EXPORT_G = 12,          /* complex [nbox(level)][K(level)]: last apply's local signatures */
     MLFMA_EXPORT_NEAR_PHI = 13,   /* complex [n] sorted order: last apply's near-field part (last rhs) */
-    MLFMA_EXPORT_TRANSLATION = 14 /* complex [316][K(level)]: translation operators of a level */
+    MLFMA_EXPORT_TRANSLATION = 14,/* complex [316][K(level)]: translation operators of a level
+                                     (MLFMA_ERR_UNSUPPORTED at a level with sampled operators) */
+    MLFMA_EXPORT_OPERATOR_SAMPLES = 15 /* complex [28][s L + 21]: a sampled level's table, row |X/edge|^2
+                                     (rows that no far offset has are zero), entry i + 10 = T at
+                                     psi_i = i pi / (s L) (MLFMA_ERR_UNSUPPORTED at other levels) */
 } mlfma_export_item;
 
 /* Stages timed by mlfma_plan_profile / mlfma_plan_timings. */

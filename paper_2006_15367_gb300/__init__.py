@@ -28,7 +28,8 @@ _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "bf16x3": PREC_FP32_BF16X3, "tf32
 MAX_LEVELS = 22
 
 EXPORT = dict(PERM=0, KEYS=1, BOX_KEY=2, BOX_BEGIN=3, BOX_END=4, BOX_PARENT=5, BOX_LEAF=6, V_OFFSETS=7,
-              V_SOURCES=8, NEAR_OFFSETS=9, NEAR_SOURCES=10, F=11, G=12, NEAR_PHI=13, TRANSLATION=14)
+              V_SOURCES=8, NEAR_OFFSETS=9, NEAR_SOURCES=10, F=11, G=12, NEAR_PHI=13, TRANSLATION=14,
+              OPERATOR_SAMPLES=15)
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "TIMEOUT", 5: "UNSUPPORTED"}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -40,7 +41,7 @@ class Options(ctypes.Structure):
                 ("max_depth", ctypes.c_int), ("digit_margin", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("disable_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("recompute_signatures", ctypes.c_int), ("test_fail_waits", ctypes.c_int),
-                ("dense_samples", ctypes.c_int)]
+                ("dense_samples", ctypes.c_int), ("sampled_operators", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -51,7 +52,8 @@ class Info(ctypes.Structure):
                 ("K", ctypes.c_int64 * (MAX_LEVELS + 1)), ("nv", ctypes.c_int64 * (MAX_LEVELS + 1)),
                 ("near_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
                 ("n_geom", ctypes.c_int), ("tile_bytes", ctypes.c_int * 3), ("recompute_signatures", ctypes.c_int),
-                ("dense", ctypes.c_int * (MAX_LEVELS + 1))]
+                ("dense", ctypes.c_int * (MAX_LEVELS + 1)), ("sampled_operators", ctypes.c_int),
+                ("sampled", ctypes.c_int * (MAX_LEVELS + 1))]
 
 
 STAGES = ["PERMUTE", "P2P", "C2M", "M2M", "M2L", "L2L", "L2O"]
@@ -280,6 +282,8 @@ class Plan:
               split-BF16 GEMMs)
     dense_samples  tensor-core precisions, opt-in: level pairs whose child grid has at most this many
               samples run as dense maps (0: never; mlfma_options.dense_samples)
+    sampled_operators  oversampling s (3-32) of the sampled translation operators at levels with boxes
+              of a wavelength or more, interpolated in M2L (0: full tables; mlfma_options.sampled_operators)
     offsets   concatenated geometries: offsets[g] .. offsets[g + 1] are geometry g's points (one
               batched plan; the matrix is block diagonal)
     graphs    replay the apply as a captured CUDA graph (default) or launch the kernels each time
@@ -297,7 +301,8 @@ class Plan:
 
     def __init__(self, points, k, digits=3, leaf_max=0, precision="fp32", leaf_edge=0.0, max_depth=12,
                  digit_margin=-1, stream=None, use_torch_allocator=True, offsets=None, graphs=True, autotune=False,
-                 recompute_signatures=False, test_fail_waits=False, allocator=None, dense_samples=0):
+                 recompute_signatures=False, test_fail_waits=False, allocator=None, dense_samples=0,
+                 sampled_operators=0):
         import torch
         self.torch = torch
         load()
@@ -326,6 +331,7 @@ class Plan:
             o.recompute_signatures = 1 if recompute_signatures else 0
             o.test_fail_waits = 1 if test_fail_waits else 0
             o.dense_samples = int(dense_samples)
+            o.sampled_operators = int(sampled_operators)
             self._alloc = None
             if allocator is not None:
                 self._alloc = allocator
@@ -416,7 +422,8 @@ class Plan:
                     K=list(i.K[:nl + 1]), nv=list(i.nv[:nl + 1]), near_pairs=i.near_pairs,
                     device_bytes=i.device_bytes, setup_ms=i.setup_ms, n_geom=i.n_geom,
                     tile_bytes=list(i.tile_bytes), recompute_signatures=bool(i.recompute_signatures),
-                    dense=list(i.dense[:nl + 1]))
+                    dense=list(i.dense[:nl + 1]), sampled_operators=i.sampled_operators,
+                    sampled=list(i.sampled[:nl + 1]))
 
     def export(self, item, level=0):
         """Copies a tree/list/signature array to a host numpy array."""
@@ -429,7 +436,7 @@ class Plan:
             return buf.view(np.uint64)
         if name == "BOX_LEAF":
             return buf.view(np.uint8)
-        if name in ("F", "G", "NEAR_PHI", "TRANSLATION"):
+        if name in ("F", "G", "NEAR_PHI", "TRANSLATION", "OPERATOR_SAMPLES"):
             return buf.view(np.complex128 if self.precision == "fp64" else np.complex64)
         return buf.view(np.int32)
 

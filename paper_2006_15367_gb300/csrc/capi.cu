@@ -495,6 +495,8 @@ static mlfma_options checked_options(const mlfma_options* opt, double k, int dig
         fail(MLFMA_ERR_INVALID_ARG, "recompute_signatures must be 0 or 1");
     if (o.test_fail_waits != 0 && o.test_fail_waits != 1) fail(MLFMA_ERR_INVALID_ARG, "test_fail_waits must be 0 or 1");
     if (o.dense_samples < -1) fail(MLFMA_ERR_INVALID_ARG, "dense_samples must be >= -1");
+    if (o.sampled_operators != 0 && (o.sampled_operators < 3 || o.sampled_operators > 32))
+        fail(MLFMA_ERR_INVALID_ARG, "sampled_operators must be 0 or in [3, 32] (got %d)", o.sampled_operators);
     return o;
 }
 
@@ -517,6 +519,7 @@ static void configure(Plan& p, int64_t n, double k, int digits, int leaf_max, co
     p.wait_first = o.test_fail_waits ? 0 : (1ll << 22);
     p.recompute = o.recompute_signatures ? 1 : 0;
     p.dense_kc = o.dense_samples > 0 ? o.dense_samples : 0;
+    p.op_s = o.sampled_operators;
 }
 
 // tree, lists, grids and operators of one point set (device points)
@@ -689,6 +692,8 @@ mlfma_status mlfma_plan_info(const mlfma_plan* plan, mlfma_info* info) {
         info->n_geom = p.subs.empty() ? 1 : (int)p.subs.size();
         info->recompute_signatures = p.recompute;
         for (int l = 0; l <= kMaxLev; ++l) info->dense[l] = p.far[l].dense;
+        info->sampled_operators = p.op_s;
+        for (int l = 0; l <= kMaxLev; ++l) info->sampled[l] = p.far[l].T1 != nullptr;
         if (p.forest) {                                // the merged levels (height above the leaves)
             for (const Plan* sp : p.subs) info->device_bytes += (int64_t)sp->mem.bytes;
         } else if (!p.subs.empty()) {
@@ -720,7 +725,8 @@ mlfma_status mlfma_plan_export(const mlfma_plan* plan, int item, int level, void
                                item != MLFMA_EXPORT_NEAR_SOURCES && item != MLFMA_EXPORT_NEAR_PHI;
         if (per_level && (level < 1 || level > p.nlev)) fail(MLFMA_ERR_INVALID_ARG, "level %d outside 1..%d", level, p.nlev);
         const TreeLevel* L = per_level ? &p.lev[level] : nullptr;
-        const bool far_item = item == MLFMA_EXPORT_F || item == MLFMA_EXPORT_G || item == MLFMA_EXPORT_TRANSLATION;
+        const bool far_item = item == MLFMA_EXPORT_F || item == MLFMA_EXPORT_G || item == MLFMA_EXPORT_TRANSLATION ||
+                              item == MLFMA_EXPORT_OPERATOR_SAMPLES;
         if (far_item && (!p.top || level < p.top)) fail(MLFMA_ERR_INVALID_ARG, "level %d has no far-field data", level);
         std::vector<std::pair<const void*, size_t>> parts;
         switch (item) {
@@ -748,6 +754,7 @@ mlfma_status mlfma_plan_export(const mlfma_plan* plan, int item, int level, void
             case MLFMA_EXPORT_G: parts.push_back({p.far[level].G, L->nbox * p.far[level].K * csize(p)}); break;
             case MLFMA_EXPORT_NEAR_PHI: parts.push_back({p.near_dump, p.n * csize(p)}); break;
             case MLFMA_EXPORT_TRANSLATION: {   // the 316 far rows of the 7^3 cube in raster order
+                if (!p.far[level].T) fail(MLFMA_ERR_UNSUPPORTED, "level %d keeps sampled operators", level);
                 const size_t row = p.far[level].K * csize(p);
                 for (int dz = -3; dz <= 3; ++dz)
                     for (int dy = -3; dy <= 3; ++dy)
@@ -758,6 +765,10 @@ mlfma_status mlfma_plan_export(const mlfma_plan* plan, int item, int level, void
                         }
                 break;
             }
+            case MLFMA_EXPORT_OPERATOR_SAMPLES:
+                if (!p.far[level].T1) fail(MLFMA_ERR_UNSUPPORTED, "level %d keeps full operator tables", level);
+                parts.push_back({p.far[level].T1, (size_t)kOpRows * p.far[level].T1n * csize(p)});
+                break;
             default: fail(MLFMA_ERR_INVALID_ARG, "unknown export item %d", item);
         }
         size_t tot = 0;

@@ -158,6 +158,9 @@ FftPlan make_fft_plan(int n);
 int smooth_even(int m);
 
 constexpr int kTBoxRows = 172;     // rows of one TMA box of T (two boxes cover the 343 rows)
+// sampled operators: Lagrange points per interpolated entry, and table rows (|X/edge|^2 = 0..27)
+constexpr int kOpOrder = 10;
+constexpr int kOpRows = 28;
 
 struct FarLevel {                  // sampling grid, operators and signatures of one far-field level
     int L = 0, nth = 0, nph = 0;
@@ -170,6 +173,12 @@ struct FarLevel {                  // sampling grid, operators and signatures of
     void* T = nullptr;             // [343][K] complex translation operators by offset raster index
                                    // (dx+3) + 7 (dy+3) + 49 (dz+3); the 27 near rows are zero
     CUtensorMap tmT;               // TMA descriptor of T (boxes of 32 samples x kTBoxRows rows)
+    // sampled operators (instead of T, at levels with k edge >= 2 pi when the plan asks for them):
+    // T1[d2][i + kOpOrder] = T at angle psi_i = i pi / S between khat and X, |X/edge|^2 = d2,
+    // i = -kOpOrder .. S + kOpOrder, S = s L; T1n = S + 2 kOpOrder + 1 entries per row
+    void* T1 = nullptr;
+    int T1n = 0;
+    double T1inv_h = 0;            // S / pi
     void* F = nullptr;             // [nbox][K] complex multipole signatures
     void* G = nullptr;             // [nbox][K] complex local signatures
     // interpolation from level l+1 (child) to this level (parent); set when l+1 is far-field
@@ -198,6 +207,7 @@ struct Plan {
     int* dev_err = nullptr;        // raised by kernels whose bounded waits ran out
     long long wait_first = 1ll << 22;   // polls of a kernel's first try of a bounded wait (0: test hook)
     int recompute = 0;             // mlfma_options.recompute_signatures
+    int op_s = 0;                  // mlfma_options.sampled_operators (oversampling s; 0 = full tables)
     void* vjp_buf = nullptr;       // [nrhs_vjp][n][3] complex: grad psi kept while grad phi is recomputed
     int nrhs_vjp = 0;
     int far_nr = 1;                // right-hand sides the far-level signatures F, G have room for

@@ -413,10 +413,63 @@ __device__ __forceinline__ bool m2l_bar_wait(uint32_t bar, uint32_t phase, long 
     return false;
 }
 
-template <typename R, typename C, int NR, int NW>
+// Lagrange weight of node J among the nodes 0 .. kOpOrder - 1: 1 / prod_{m != J} (J - m)
+template <int J> __host__ __device__ constexpr double lagrange_c() {
+    double d = 1.0;
+    for (int m = 0; m < kOpOrder; ++m)
+        if (m != J) d *= (double)(J - m);
+    return 1.0 / d;
+}
+
+// acc += sum_{j <= J} l_j(t) b[j], l_j(t) = c_j prod_{m < j} (t - m) prod_{m > j} (t - m):
+// pre[j] holds the first product, suf the second (built from the top node down)
+template <typename R, typename C, int J>
+__device__ __forceinline__ void lagrange_terms(C& acc, const C* __restrict__ b, const R (&pre)[kOpOrder], R suf, R t) {
+    constexpr double c = lagrange_c<J>();
+    const R w = pre[J] * suf * (R)c;
+    const C v = __ldg(b + J);
+    acc.x = fma(w, v.x, acc.x);
+    acc.y = fma(w, v.y, acc.y);
+    if constexpr (J > 0) lagrange_terms<R, C, J - 1>(acc, b, pre, suf * (t - (R)J), t);
+}
+
+// Sampled operators (Sec. 3.2.3, "Translation Operators": sample the operators, interpolate
+// them): T of the offset d (box units) at the sample direction khat, from the row of |d|^2 of
+// the level's table (entry i + kOpOrder: T at psi_i = i pi / S), by the kOpOrder-point Lagrange
+// interpolant on the nodes floor(u) - kOpOrder/2 + 1 .. floor(u) + kOpOrder/2, u = psi S / pi,
+// psi = atan2(|d x khat|, d . khat) (accurate at every angle, unlike acos of the dot product).
+// S / pi = inv_h + inv_lo (inv_lo: what rounding inv_h dropped), and the position within the
+// stencil is fma(psi, inv_h, -i) + psi inv_lo, so it keeps the accuracy of psi instead of that
+// of u (whose rounding at u ~ 10^3 would move the node by 1e-4 spacings in FP32).  The node
+// index is clamped to [0, S], the range psi in [0, pi] gives, so every read stays in the row
+// whatever the arithmetic returns.
+template <typename R, typename C>
+__device__ __forceinline__ C sampled_operator(const C* __restrict__ row, int S, R inv_h, R inv_lo, R dx, R dy, R dz,
+                                              R kx, R ky, R kz) {
+    const R cx = dy * kz - dz * ky, cy = dz * kx - dx * kz, cz = dx * ky - dy * kx;
+    R psi;
+    if constexpr (sizeof(R) == 4) psi = atan2f(sqrtf(cx * cx + cy * cy + cz * cz), dx * kx + dy * ky + dz * kz);
+    else psi = atan2(sqrt(cx * cx + cy * cy + cz * cz), dx * kx + dy * ky + dz * kz);
+    const int i = min(max((int)floor(psi * inv_h), 0), S);
+    const R t = fma(psi, inv_h, -(R)i) + psi * inv_lo + (R)(kOpOrder / 2 - 1);   // among the nodes 0 .. kOpOrder - 1
+    R pre[kOpOrder];
+    pre[0] = 1;
+#pragma unroll
+    for (int j = 1; j < kOpOrder; ++j) pre[j] = pre[j - 1] * (t - (R)(j - 1));
+    C acc = cmake<C>(0, 0);
+    lagrange_terms<R, C, kOpOrder - 1>(acc, row + (i - (kOpOrder / 2 - 1) + kOpOrder), pre, (R)1, t);
+    return acc;
+}
+
+// SMP: the level keeps sampled operators (T1, T1n entries per row, inv_h + inv_lo = S / pi,
+// sample directions dirs [K][4]); the CTA computes its operator slice from them instead of
+// copying it.
+template <typename R, typename C, int NR, int NW, bool SMP>
 __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __restrict__ pcb, const int* __restrict__ pce,
                                                    const int* __restrict__ loff, const unsigned long long* __restrict__ lsrc,
                                                    const uint64_t* __restrict__ ckey, const __grid_constant__ CUtensorMap tmT,
+                                                   const C* __restrict__ T1, int T1n, R inv_h, R inv_lo,
+                                                   const R* __restrict__ dirs,
                                                    const C* __restrict__ F, int64_t K, int64_t sF, C* __restrict__ G,
                                                    int Q, int* __restrict__ err, long long wait_first) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -430,32 +483,54 @@ __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __r
     // memory after the operator slice, and the first of them adds the Q partial sums.
     const int PPC = Q > 1 ? NW / Q : NW * kM2LParentsPerWarp;    // parents per CTA
     const int64_t P0 = (int64_t)blockIdx.x * PPC;
-    // stage the slice with two TMA boxes of kTBoxRows rows (rows 343 and samples past K read as
-    // zero) completing on one mbarrier
-    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&tbar);
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        constexpr uint32_t box = kTBoxRows * 32 * sizeof(C);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(2 * box) : "memory");
-        const int x = (int)(p0 * (int64_t)(sizeof(C) / 8));
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Ts + b * kTBoxRows * 32);
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                "[%4];\n" ::"r"(dst),
-                "l"(reinterpret_cast<uint64_t>(&tmT)), "r"(x), "r"(b * kTBoxRows), "r"(bar)
-                : "memory");
+    if constexpr (SMP) {
+        // row r of the slice = offset (r % 7 - 3, r / 7 % 7 - 3, r / 49 - 3), lane = sample p0 + lane;
+        // near rows (|d|^2 <= 3), row 343 and samples past K stay zero
+        const int64_t ps = p0 + lane;
+        R kx = 0, ky = 0, kz = 0;
+        if (ps < K) {
+            kx = dirs[4 * ps];
+            ky = dirs[4 * ps + 1];
+            kz = dirs[4 * ps + 2];
         }
-    }
-    if (!__syncthreads_and(m2l_bar_wait(bar, 0, wait_first))) {
-        if (threadIdx.x == 0) atomicExch(err, 2);
-        m2l_bar_wait(bar, 0);                     // normal limit: let the copies in flight land
-        return;
+        const int S = T1n - 2 * kOpOrder - 1;
+        for (int r = warp; r < 2 * kTBoxRows; r += NW) {
+            const int dx = r % 7 - 3, dy = r / 7 % 7 - 3, dz = r / 49 - 3;
+            const int d2 = dx * dx + dy * dy + dz * dz;
+            C v = cmake<C>(0, 0);
+            if (r < 343 && d2 >= 4 && ps < K)
+                v = sampled_operator<R, C>(T1 + (size_t)d2 * T1n, S, inv_h, inv_lo, (R)dx, (R)dy, (R)dz, kx, ky, kz);
+            Ts[r * 32 + lane] = v;
+        }
+        __syncthreads();
+    } else {
+        // stage the slice with two TMA boxes of kTBoxRows rows (rows 343 and samples past K read as
+        // zero) completing on one mbarrier
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&tbar);
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            constexpr uint32_t box = kTBoxRows * 32 * sizeof(C);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(2 * box) : "memory");
+            const int x = (int)(p0 * (int64_t)(sizeof(C) / 8));
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Ts + b * kTBoxRows * 32);
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                    "[%4];\n" ::"r"(dst),
+                    "l"(reinterpret_cast<uint64_t>(&tmT)), "r"(x), "r"(b * kTBoxRows), "r"(bar)
+                    : "memory");
+            }
+        }
+        if (!__syncthreads_and(m2l_bar_wait(bar, 0, wait_first))) {
+            if (threadIdx.x == 0) atomicExch(err, 2);
+            m2l_bar_wait(bar, 0);                     // normal limit: let the copies in flight land
+            return;
+        }
     }
     const bool ok = p0 + lane < K;
     const C* Fp = F + (ok ? p0 + lane : K - 1);       // lane's sample; + (src * K) per source
@@ -588,9 +663,9 @@ __global__ void __launch_bounds__(32 * kM2LTailWarps) k_m2l_tail(int64_t npar, c
 // w = 2, 69,745 parents: 0.925 -> 0.850 ms; w = 8 levels and the 56-parent level 4 lost 20-50 us
 // each).  Both kernels compute the same values, so the choice does not change results.
 template <typename C, int NR>
-static int m2l_tail(int64_t K, int64_t npar) {
+static int m2l_tail(int64_t K, int64_t npar, bool sampled) {
     const int w = (int)(K % 32);
-    return NR == 1 && m2l_split<C, NR>(K) == 1 && w <= 4 && npar >= 16384 ? w : 0;
+    return NR == 1 && !sampled && m2l_split<C, NR>(K) == 1 && w <= 4 && npar >= 16384 ? w : 0;
 }
 
 template <typename C>
@@ -598,8 +673,8 @@ static size_t m2l_tail_smem(int W) { return (size_t)343 * W * sizeof(C); }
 
 // kernel launches of one level's M2L
 template <typename C, int NR>
-static int m2l_launches(int64_t K, int64_t npar) {
-    const int w = m2l_tail<C, NR>(K, npar);
+static int m2l_launches(int64_t K, int64_t npar, bool sampled) {
+    const int w = m2l_tail<C, NR>(K, npar, sampled);
     return (K >= 32 || !w ? 1 : 0) + (w ? 1 : 0);
 }
 
@@ -610,15 +685,22 @@ static void launch_m2l(const Plan& p, int l, cudaStream_t s) {
     const TreeLevel& T = p.lev[l];
     const TreeLevel& TP = p.lev[l - 1];
     const int Q = m2l_split<C, NR>(F.K);
-    const int w = m2l_tail<C, NR>(F.K, TP.nbox);
+    const bool smp = F.T1 != nullptr;
+    const int w = m2l_tail<C, NR>(F.K, TP.nbox, smp);
     const int64_t nslices = w ? F.K / 32 : (F.K + 31) / 32;
     if (nslices > 0) {
         const int ppc = Q > 1 ? NW / Q : NW * kM2LParentsPerWarp;
         const size_t sm = m2l_smem<R, C>() + (Q > 1 ? (size_t)NW * 8 * NR * 32 * sizeof(C) : 0);
         const dim3 grid(nblk(TP.nbox, ppc), (unsigned)nslices);
-        k_m2l<R, C, NR, NW><<<grid, 32 * NW, sm, s>>>(TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off, TP.m2l_src,
-                                                      T.key, F.tmT, (const C*)F.F, F.K, T.nbox * F.K, (C*)F.G, Q,
-                                                      p.dev_err, std::min(p.wait_first, kM2LWaitLimit));
+        if (smp)
+            k_m2l<R, C, NR, NW, true><<<grid, 32 * NW, sm, s>>>(
+                TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off, TP.m2l_src, T.key, F.tmT, (const C*)F.T1, F.T1n,
+                (R)F.T1inv_h, (R)(F.T1inv_h - (double)(R)F.T1inv_h), (const R*)F.dirs, (const C*)F.F, F.K, T.nbox * F.K,
+                (C*)F.G, Q, p.dev_err, 0);
+        else
+            k_m2l<R, C, NR, NW, false><<<grid, 32 * NW, sm, s>>>(
+                TP.nbox, TP.child_begin, TP.child_end, TP.m2l_off, TP.m2l_src, T.key, F.tmT, nullptr, 0, (R)0, (R)0, nullptr,
+                (const C*)F.F, F.K, T.nbox * F.K, (C*)F.G, Q, p.dev_err, std::min(p.wait_first, kM2LWaitLimit));
         MLFMA_LAUNCH_CHECK();
     }
     if (w) {
@@ -1579,7 +1661,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v,
         TreeLevel& T = p.lev[l];
         TreeLevel& TP = p.lev[l - 1];
         {
-            StageTimer st(p, MLFMA_STAGE_M2L, l, m2l_launches<C, NR>(F.K, TP.nbox));
+            StageTimer st(p, MLFMA_STAGE_M2L, l, m2l_launches<C, NR>(F.K, TP.nbox, F.T1 != nullptr));
             launch_m2l<R, C, NR>(p, l, s);
         }
         if (l > p.top && p.far[l - 1].dense) {
@@ -1715,12 +1797,16 @@ void prepare_kernels(Plan& p) {
         prepare_dense_tc();
     }
     if (p.prec == MLFMA_PREC_FP64) {
-        allow_max_smem(k_m2l<double, double2, 1, M2LShape<double2, 1>::NW>);
-        allow_max_smem(k_m2l<double, double2, kMaxNR, M2LShape<double2, kMaxNR>::NW>);
+        allow_max_smem(k_m2l<double, double2, 1, M2LShape<double2, 1>::NW, false>);
+        allow_max_smem(k_m2l<double, double2, kMaxNR, M2LShape<double2, kMaxNR>::NW, false>);
+        allow_max_smem(k_m2l<double, double2, 1, M2LShape<double2, 1>::NW, true>);
+        allow_max_smem(k_m2l<double, double2, kMaxNR, M2LShape<double2, kMaxNR>::NW, true>);
         allow_max_smem(k_m2l_tail<double2, 16>);
     } else {
-        allow_max_smem(k_m2l<float, float2, 1, M2LShape<float2, 1>::NW>);
-        allow_max_smem(k_m2l<float, float2, kMaxNR, M2LShape<float2, kMaxNR>::NW>);
+        allow_max_smem(k_m2l<float, float2, 1, M2LShape<float2, 1>::NW, false>);
+        allow_max_smem(k_m2l<float, float2, kMaxNR, M2LShape<float2, kMaxNR>::NW, false>);
+        allow_max_smem(k_m2l<float, float2, 1, M2LShape<float2, 1>::NW, true>);
+        allow_max_smem(k_m2l<float, float2, kMaxNR, M2LShape<float2, kMaxNR>::NW, true>);
     }
 }
 

@@ -15,6 +15,7 @@
 //   B_m[i][i'] = A_m[i'][i] w'_i' / w_i.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -159,10 +160,10 @@ __global__ void k_twiddle(int nph, C* __restrict__ tw) {
 // sum_n (2n+1) j_n^2 = 1.
 constexpr int kMillerMax = 2048;
 
-__global__ void k_hankel(int L, double k, double edge, const int* __restrict__ dxyz, double2* __restrict__ hn,
+__global__ void k_hankel(int noff, int L, double k, double edge, const int* __restrict__ dxyz, double2* __restrict__ hn,
                          double* __restrict__ work) {
     int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= kNumOffsets) return;
+    if (o >= noff) return;
     double X[3] = {dxyz[3 * o] * edge, dxyz[3 * o + 1] * edge, dxyz[3 * o + 2] * edge};
     double x = k * sqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
     double2* h = hn + (size_t)o * (L + 1);
@@ -246,6 +247,41 @@ __global__ void k_translation(int L, int nth, int nph, double edge, const double
     // row of the offset in the 7^3 cube (the 27 near rows stay zero)
     const int row = (dxyz[3 * o] + 3) + 7 * (dxyz[3 * o + 1] + 3) + 49 * (dxyz[3 * o + 2] + 3);
     T[(int64_t)row * K + p] = cmake<C>(re, im);
+}
+
+// ---------------------------------------------------------------- sampled translation operators
+// Sec. 3.2.3 ("Translation Operators"): operators that would not fit are sampled and
+// interpolated.  T_X(khat) = sum_n i^n (2n+1) h_n(k|X|) P_n(cos psi) depends on khat only through
+// the angle psi between khat and X, and is an even, 2 pi-periodic cosine polynomial of degree L
+// in psi.  One thread per (class c, entry i): T at psi_i = (i - kOpOrder) pi / S into row d2[c]
+// (|X/edge|^2 of the class) of the level's table.  Entries with psi_i < 0 or > pi are the
+// reflections the interpolation stencil reads next to psi = 0 and pi; cos(psi_i) yields them.
+// hn: [ncls][L+1] spherical Hankel functions of the classes' k|X|.
+template <typename C>
+__global__ void k_op_samples(int L, int S, int ncls, int T1n, const int* __restrict__ d2, const double2* __restrict__ hn,
+                             C* __restrict__ T1) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)ncls * T1n) return;
+    const int c = (int)(idx / T1n), i = (int)(idx % T1n);
+    const double t = cospi((double)(i - kOpOrder) / S);
+    const double2* h = hn + (size_t)c * (L + 1);
+    double re = h[0].x, im = h[0].y, pm1 = 1.0, p0 = t;
+    for (int n = 1; n <= L; ++n) {
+        double Pn = t;
+        if (n >= 2) {
+            Pn = ((2 * n - 1) * t * p0 - (n - 1) * pm1) / n;
+            pm1 = p0;
+            p0 = Pn;
+        }
+        const double a = (2 * n + 1) * Pn, hr = h[n].x, hi = h[n].y;
+        switch (n & 3) {                            // i^n h_n
+            case 0: re += a * hr; im += a * hi; break;
+            case 1: re -= a * hi; im += a * hr; break;
+            case 2: re -= a * hr; im -= a * hi; break;
+            default: re += a * hi; im -= a * hr; break;
+        }
+    }
+    T1[(int64_t)d2[c] * T1n + i] = cmake<C>(re, im);
 }
 
 // ---------------------------------------------------------------- interpolation matrices
@@ -365,6 +401,25 @@ static void build_far_levels_t(Plan& p) {
     MLFMA_CUDA(cudaMemcpyAsync(p.off343, off343, sizeof(off343), cudaMemcpyHostToDevice, s));
     int* d_dxyz = p.mem.make<int>(3 * kNumOffsets);
     MLFMA_CUDA(cudaMemcpyAsync(d_dxyz, dxyz, sizeof(dxyz), cudaMemcpyHostToDevice, s));
+    // sampled operators: one representative offset per squared length |X/edge|^2 that far
+    // offsets take (every d2 >= 4 that is a sum of three squares of at most 3)
+    int rep[3 * kOpRows], cls_d2[kOpRows], ncls = 0;
+    for (int d2 = 4; d2 < kOpRows; ++d2)
+        for (int o = 0; o < kNumOffsets; ++o) {
+            const int* d = dxyz + 3 * o;
+            if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] != d2) continue;
+            rep[3 * ncls] = d[0]; rep[3 * ncls + 1] = d[1]; rep[3 * ncls + 2] = d[2];
+            cls_d2[ncls++] = d2;
+            break;
+        }
+    int* d_rep = nullptr;
+    int* d_cls = nullptr;
+    if (p.op_s > 0) {
+        d_rep = p.mem.make<int>(3 * kOpRows);
+        d_cls = p.mem.make<int>(kOpRows);
+        MLFMA_CUDA(cudaMemcpyAsync(d_rep, rep, sizeof(rep), cudaMemcpyHostToDevice, s));
+        MLFMA_CUDA(cudaMemcpyAsync(d_cls, cls_d2, sizeof(cls_d2), cudaMemcpyHostToDevice, s));
+    }
 
     // top: highest level with a non-empty V list
     p.top = 0;
@@ -395,14 +450,28 @@ static void build_far_levels_t(Plan& p) {
         F.tw = p.mem.make<C>(F.nph);
         k_twiddle<C><<<nblk(F.nph, 256), 256, 0, s>>>(F.nph, (C*)F.tw);
         MLFMA_LAUNCH_CHECK();
-        k_hankel<<<nblk(kNumOffsets, 32), 32, 0, s>>>(F.L, p.k, p.lev[l].edge, d_dxyz, hn, work);
-        MLFMA_LAUNCH_CHECK();
-        F.T = p.mem.make<C>((size_t)343 * F.K);
-        MLFMA_CUDA(cudaMemsetAsync(F.T, 0, (size_t)343 * F.K * sizeof(C), s));
-        k_translation<C><<<nblk(F.K * kNumOffsets, 128), 128, 0, s>>>(F.L, F.nth, F.nph, p.lev[l].edge, F.x, d_dxyz, hn,
-                                                                      (C*)F.T);
-        MLFMA_LAUNCH_CHECK();
-        encode_translation_map(F, sizeof(C));
+        if (p.op_s > 0 && p.k * p.lev[l].edge >= 2.0 * M_PI * (1.0 - 1e-9)) {
+            // boxes of a wavelength or more: sampled operators, interpolated in M2L
+            const int S = p.op_s * F.L;
+            F.T1n = S + 2 * kOpOrder + 1;
+            F.T1inv_h = S / M_PI;
+            k_hankel<<<nblk(ncls, 32), 32, 0, s>>>(ncls, F.L, p.k, p.lev[l].edge, d_rep, hn, work);
+            MLFMA_LAUNCH_CHECK();
+            F.T1 = p.mem.make<C>((size_t)kOpRows * F.T1n);
+            MLFMA_CUDA(cudaMemsetAsync(F.T1, 0, (size_t)kOpRows * F.T1n * sizeof(C), s));
+            k_op_samples<C><<<nblk((int64_t)ncls * F.T1n, 128), 128, 0, s>>>(F.L, S, ncls, F.T1n, d_cls, hn, (C*)F.T1);
+            MLFMA_LAUNCH_CHECK();
+            memset(&F.tmT, 0, sizeof(F.tmT));
+        } else {
+            k_hankel<<<nblk(kNumOffsets, 32), 32, 0, s>>>(kNumOffsets, F.L, p.k, p.lev[l].edge, d_dxyz, hn, work);
+            MLFMA_LAUNCH_CHECK();
+            F.T = p.mem.make<C>((size_t)343 * F.K);
+            MLFMA_CUDA(cudaMemsetAsync(F.T, 0, (size_t)343 * F.K * sizeof(C), s));
+            k_translation<C><<<nblk(F.K * kNumOffsets, 128), 128, 0, s>>>(F.L, F.nth, F.nph, p.lev[l].edge, F.x, d_dxyz,
+                                                                          hn, (C*)F.T);
+            MLFMA_LAUNCH_CHECK();
+            encode_translation_map(F, sizeof(C));
+        }
         F.F = p.mem.make<C>((size_t)p.lev[l].nbox * F.K);
         F.G = p.mem.make<C>((size_t)p.lev[l].nbox * F.K);
     }

@@ -10,6 +10,9 @@ workloads use:
   norm-relative per level.
 * the same sphere with the FP64 path at 6 digits (half-wavelength leaves): 1e-6 against the
   oracle's FP64 direct sum (Eq. (1)) on 2,000 sampled targets.
+* the same sphere with sampled translation operators at the levels of wavelength-sized boxes
+  and above (Sec. 3.2.3): the top level's M2L against the oracle's, 1e-4 (FP32); the
+  potentials against the direct sum, 1e-3 (FP32) and 1e-6 (FP64, 6 digits, oversampling 16).
 * the same sphere with split-TF32 tensor-core theta maps: 1e-3 against the direct sum and
   1e-5 per level (F and G) against the FP32 plan.
 * 4,194,304 points on a cube surface with 64 dense clusters (adaptive tree, leaf_max 64,
@@ -95,6 +98,36 @@ def test_sphere1m_fp64_six_digits(sphere1m):
     plan.close()
     tg = _targets(pts.shape[0], 2000, 2001)
     assert rel(phi[tg], direct.direct(pts, q[0], prm["k"], targets=tg)) < 1e-6
+
+
+def test_sphere1m_sampled_operators(sphere1m):
+    """Sampled translation operators (Sec. 3.2.3) on the 2^20 sphere: the levels with boxes of
+    16 down to 1 wavelength keep angle tables instead of T[316][K].  FP32 (oversampling 6): the
+    top level's M2L (list-split kernel) against the oracle's m2l with sampled operators on the
+    exported F_3, 1e-4 (FP32 angles good to ~2e-7 and dT/dpsi up to L |T|, L ~ 200 there); the
+    potentials within 1e-3 of the direct sum.  FP64 at 6 digits (oversampling 16): 1e-6 against
+    the direct sum.  At 6 digits the one-wavelength level has L = 26 and max |T| some 10^4 times
+    the sums it produces, so the interpolation error relative to max |T| must stay near 1e-11:
+    with oversampling 8 (1e-8) the potentials are off by 1.5e-4 (the oracle with the same
+    sampled operators gives 1.7e-4 on the 4,096-point sphere; 6.6e-8 at oversampling 16)."""
+    pts, q, prm = sphere1m
+    plan = make_plan(pts, prm["k"], 3, "fp32", sampled_operators=6)
+    phi = apply_plan(plan, q[0], "fp32")
+    o = om.OracleMLFMA(pts, prm["k"], 3, margin=0, sampled_operators=6)
+    info = plan.info()
+    assert [l for l, v in enumerate(info["sampled"]) if v] == \
+        [l for l in sorted(o.L) if om.level_is_sampled(o.k, o.tree.levels[l].edge, 6)] == [3, 4, 5, 6, 7]
+    F3 = plan.export("F", 3).reshape(o.tree.levels[3].nbox, -1).astype(np.complex128)
+    G3 = plan.export("G", 3).reshape(o.tree.levels[3].nbox, -1).astype(np.complex128)
+    assert rel(G3, o.m2l(3, F3)) < 1e-4
+    plan.close()
+    tg = _targets(pts.shape[0], 2000, 2004)
+    assert rel(phi[tg], direct.direct(pts, q[0], prm["k"], targets=tg)) < 1e-3
+    p64 = make_plan(pts, prm["k"], 6, "fp64", sampled_operators=16)
+    assert sum(p64.info()["sampled"]) >= 3
+    phi64 = apply_plan(p64, q[0], "fp64")
+    p64.close()
+    assert rel(phi64[tg], direct.direct(pts, q[0], prm["k"], targets=tg)) < 1e-6
 
 
 def test_sphere1m_tf32x3(sphere1m):
