@@ -421,31 +421,37 @@ template <int J> __host__ __device__ constexpr double lagrange_c() {
     return 1.0 / d;
 }
 
-// acc += sum_{j <= J} l_j(t) b[j], l_j(t) = c_j prod_{m < j} (t - m) prod_{m > j} (t - m):
-// pre[j] holds the first product, suf the second (built from the top node down)
+// acc += sum_{j <= J} l_j(t) b[j] and acm += sum_{j <= J} l_j(t) bm[-j], l_j(t) = c_j
+// prod_{m < j} (t - m) prod_{m > j} (t - m): pre[j] holds the first product, suf the second
+// (built from the top node down)
 template <typename R, typename C, int J>
-__device__ __forceinline__ void lagrange_terms(C& acc, const C* __restrict__ b, const R (&pre)[kOpOrder], R suf, R t) {
+__device__ __forceinline__ void lagrange_terms(C& acc, C& acm, const C* __restrict__ b, const C* __restrict__ bm,
+                                               const R (&pre)[kOpOrder], R suf, R t) {
     constexpr double c = lagrange_c<J>();
     const R w = pre[J] * suf * (R)c;
-    const C v = __ldg(b + J);
+    const C v = __ldg(b + J), vm = __ldg(bm - J);
     acc.x = fma(w, v.x, acc.x);
     acc.y = fma(w, v.y, acc.y);
-    if constexpr (J > 0) lagrange_terms<R, C, J - 1>(acc, b, pre, suf * (t - (R)J), t);
+    acm.x = fma(w, vm.x, acm.x);
+    acm.y = fma(w, vm.y, acm.y);
+    if constexpr (J > 0) lagrange_terms<R, C, J - 1>(acc, acm, b, bm, pre, suf * (t - (R)J), t);
 }
 
 // Sampled operators (Sec. 3.2.3, "Translation Operators": sample the operators, interpolate
-// them): T of the offset d (box units) at the sample direction khat, from the row of |d|^2 of
-// the level's table (entry i + kOpOrder: T at psi_i = i pi / S), by the kOpOrder-point Lagrange
-// interpolant on the nodes floor(u) - kOpOrder/2 + 1 .. floor(u) + kOpOrder/2, u = psi S / pi,
-// psi = atan2(|d x khat|, d . khat) (accurate at every angle, unlike acos of the dot product).
-// S / pi = inv_h + inv_lo (inv_lo: what rounding inv_h dropped), and the position within the
-// stencil is fma(psi, inv_h, -i) + psi inv_lo, so it keeps the accuracy of psi instead of that
-// of u (whose rounding at u ~ 10^3 would move the node by 1e-4 spacings in FP32).  The node
-// index is clamped to [0, S], the range psi in [0, pi] gives, so every read stays in the row
-// whatever the arithmetic returns.
+// them): T of the offset d (box units) and of its antipode -d at the sample direction khat,
+// from the row of |d|^2 of the level's table (entry i + kOpOrder: T at psi_i = i pi / S), by the
+// kOpOrder-point Lagrange interpolant on the nodes n_j = floor(u) - kOpOrder/2 + 1 + j,
+// u = psi S / pi, psi = atan2(|d x khat|, d . khat) (accurate at every angle, unlike acos of the
+// dot product).  The antipode's angle is pi - psi: its stencil is the mirror image, nodes S - n_j
+// with the same weights, so the angle and the weights serve both.  S / pi = inv_h + inv_lo
+// (inv_lo: what rounding inv_h dropped), and the position within the stencil is
+// fma(psi, inv_h, -i) + psi inv_lo, so it keeps the accuracy of psi instead of that of u (whose
+// rounding at u ~ 10^3 would move the node by 1e-4 spacings in FP32).  The node index is
+// clamped to [0, S], the range psi in [0, pi] gives, so every read stays in the row whatever
+// the arithmetic returns.
 template <typename R, typename C>
-__device__ __forceinline__ C sampled_operator(const C* __restrict__ row, int S, R inv_h, R inv_lo, R dx, R dy, R dz,
-                                              R kx, R ky, R kz) {
+__device__ __forceinline__ void sampled_operator_pair(const C* __restrict__ row, int S, R inv_h, R inv_lo, R dx, R dy,
+                                                      R dz, R kx, R ky, R kz, C& v, C& vm) {
     const R cx = dy * kz - dz * ky, cy = dz * kx - dx * kz, cz = dx * ky - dy * kx;
     R psi;
     if constexpr (sizeof(R) == 4) psi = atan2f(sqrtf(cx * cx + cy * cy + cz * cz), dx * kx + dy * ky + dz * kz);
@@ -456,9 +462,10 @@ __device__ __forceinline__ C sampled_operator(const C* __restrict__ row, int S, 
     pre[0] = 1;
 #pragma unroll
     for (int j = 1; j < kOpOrder; ++j) pre[j] = pre[j - 1] * (t - (R)(j - 1));
-    C acc = cmake<C>(0, 0);
-    lagrange_terms<R, C, kOpOrder - 1>(acc, row + (i - (kOpOrder / 2 - 1) + kOpOrder), pre, (R)1, t);
-    return acc;
+    v = cmake<C>(0, 0);
+    vm = cmake<C>(0, 0);
+    const int n0 = i - (kOpOrder / 2 - 1);              // node 0; entry n + kOpOrder holds psi_n
+    lagrange_terms<R, C, kOpOrder - 1>(v, vm, row + n0 + kOpOrder, row + (S - n0) + kOpOrder, pre, (R)1, t);
 }
 
 // SMP: the level keeps sampled operators (T1, T1n entries per row, inv_h + inv_lo = S / pi,
@@ -493,15 +500,20 @@ __global__ void __launch_bounds__(32 * NW, 1) k_m2l(int64_t npar, const int* __r
             ky = dirs[4 * ps + 1];
             kz = dirs[4 * ps + 2];
         }
+        // rows r and 342 - r hold the offsets d and -d (one interpolation stencil); row 171 is
+        // the zero offset
         const int S = T1n - 2 * kOpOrder - 1;
-        for (int r = warp; r < 2 * kTBoxRows; r += NW) {
+        for (int r = warp; r <= 171; r += NW) {
             const int dx = r % 7 - 3, dy = r / 7 % 7 - 3, dz = r / 49 - 3;
             const int d2 = dx * dx + dy * dy + dz * dz;
-            C v = cmake<C>(0, 0);
-            if (r < 343 && d2 >= 4 && ps < K)
-                v = sampled_operator<R, C>(T1 + (size_t)d2 * T1n, S, inv_h, inv_lo, (R)dx, (R)dy, (R)dz, kx, ky, kz);
+            C v = cmake<C>(0, 0), vm = cmake<C>(0, 0);
+            if (d2 >= 4 && ps < K)
+                sampled_operator_pair<R, C>(T1 + (size_t)d2 * T1n, S, inv_h, inv_lo, (R)dx, (R)dy, (R)dz, kx, ky, kz, v,
+                                            vm);
             Ts[r * 32 + lane] = v;
+            Ts[(342 - r) * 32 + lane] = vm;
         }
+        if (warp == 0) Ts[343 * 32 + lane] = cmake<C>(0, 0);
         __syncthreads();
     } else {
         // stage the slice with two TMA boxes of kTBoxRows rows (rows 343 and samples past K read as

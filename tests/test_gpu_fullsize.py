@@ -4,7 +4,7 @@ Each test compares the CUDA path with the oracle at the size the benchmark and t
 workloads use:
 
 * 2^20-point sphere (radius 32, 9 levels), FP32: the two top levels' M2L (level 3 has
-  K = 77,618 samples per box and runs the list-split M2L kernel, four warps per parent),
+  K = 78,800 samples per box and runs the list-split M2L kernel, four warps per parent),
   the M2M pair 4 -> 3 and the L2L pair 3 -> 4, each against the oracle's own stage
   function applied to the signatures the GPU exported (Sec. 3.2.2-3.2.4, Alg. 1-2), 1e-5
   norm-relative per level.
