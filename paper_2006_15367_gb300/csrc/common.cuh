@@ -184,6 +184,15 @@ struct FarLevel {                  // sampling grid, operators and signatures of
     // interpolation from level l+1 (child) to this level (parent); set when l+1 is far-field
     void* At = nullptr;            // [Lc+1][nth_c][nth_p] real: At[m][i][i'] = A_m[i'][i]
     void* Bt = nullptr;            // [Lc+1][nth_p][nth_c] real: Bt[m][i'][i] = A_m[i'][i] w'_i' / w_i
+    // the same maps split by parity (Gauss-Legendre nodes come in pairs x, -x, and
+    // Pbar_n^m(-x) = (-1)^(n+m) Pbar_n^m(x), so each map is centrosymmetric): for input index
+    // i < ceil(nin/2) and output index o < ceil(nout/2), E = the terms n + m even, D = n + m odd,
+    // times the map's weights; E's middle input row (odd nin) is halved, D's middle row and
+    // column are zero.  Layout [Lc+1][ceil(nin/2)][ceil(nout/2)] real.
+    void* AtE = nullptr;           // M2M (nin = nth_c, nout = nth_p)
+    void* AtD = nullptr;
+    void* BtE = nullptr;           // L2L (nin = nth_p, nout = nth_c)
+    void* BtD = nullptr;
     void* AtTc = nullptr;          // tensor-core precisions: At and Bt split into hi + lo parts, in the
     void* BtTc = nullptr;          // blocks the MMA reads (one per mode, output tile and K chunk)
     // tensor-core precisions, fine level pairs: the whole interpolation (anterpolation) of the

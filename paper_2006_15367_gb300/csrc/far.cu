@@ -1554,10 +1554,132 @@ __global__ void __launch_bounds__(256) k_theta_map(int nbox, int Lc, int nin, in
     }
 }
 
-// Mtc: the pre-split form of M for the tensor-core precisions
+// The same GEMM by parity.  Gauss-Legendre nodes come in pairs (x, -x) and every map is
+// centrosymmetric, M[n-1-i][n'-1-o] = M[i][o], so with e_i = in[i] + in[n-1-i] and
+// d_i = in[i] - in[n-1-i] (i < ceil(n/2)) the halves
+//   oe[o] = sum_i ME[i][o] e_i,   od[o] = sum_i MD[i][o] d_i   (o < ceil(n'/2))
+// give out[o] = oe + od and out[n'-1-o] = oe - od: two GEMMs of a quarter of the size, half the
+// multiply-adds of the full map.  ME and MD are built at plan creation from the even and odd
+// terms of the Legendre sums (k_interp_par; ME's middle row halved, because e takes the middle
+// sample twice).  The CTA stages the rows in[i] and in[n-1-i] of its chunk (cp.async, double-
+// buffered like k_theta_map) and forms e and d in registers as it multiplies.
+template <typename R, typename C, int BN>
+struct MapParShape {
+    static constexpr int BM = 4096 / BN, BK = sizeof(C) == 8 ? 16 : 8, AP = BM + 2;
+    static constexpr size_t smem = 2 * (2 * (size_t)BK * AP * sizeof(C) + 2 * (size_t)BK * BN * sizeof(R));
+};
+
+template <typename R, typename C, int BN>
+__global__ void __launch_bounds__(256) k_theta_map_par(int nbox, int Lc, int nin, int nout, const R* __restrict__ ME,
+                                                       const R* __restrict__ MD, const C* __restrict__ in,
+                                                       C* __restrict__ out) {
+    using S = MapParShape<R, C, BN>;
+    constexpr int BM = S::BM, BK = S::BK, AP = S::AP;
+    constexpr int TX = BN / 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* Al = reinterpret_cast<C*>(smem_raw);                    // [2][BK][AP] in[i]
+    C* Ah = Al + 2 * BK * AP;                                  // [2][BK][AP] in[nin-1-i]
+    R* Be = reinterpret_cast<R*>(Ah + 2 * BK * AP);            // [2][BK][BN]
+    R* Bd = Be + 2 * BK * BN;                                  // [2][BK][BN]
+    const int hin = (nin + 1) / 2, hout = (nout + 1) / 2;
+    const int mi = blockIdx.z;
+    const int m = abs(mi - Lc);
+    const int c0 = blockIdx.x * BM, o0 = blockIdx.y * BN;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const C* inm = in + (int64_t)mi * nbox * nin;
+    const R* Em = ME + (int64_t)m * hin * hout;
+    const R* Dm = MD + (int64_t)m * hin * hout;
+    auto stage = [&](int buf, int k0) {
+        C* al = Al + buf * BK * AP;
+        C* ah = Ah + buf * BK * AP;
+        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
+            const int cl = idx / BK, kk = idx % BK;
+            const int c = c0 + cl, i = k0 + kk;
+            const bool v = c < nbox && i < hin;
+            const C* row = inm + (int64_t)c * nin;
+            cp_async_zfill<sizeof(C)>(al + kk * AP + cl, v ? row + i : inm, v);
+            cp_async_zfill<sizeof(C)>(ah + kk * AP + cl, v ? row + (nin - 1 - i) : inm, v);
+        }
+        R* be = Be + buf * BK * BN;
+        R* bd = Bd + buf * BK * BN;
+        for (int idx = threadIdx.x; idx < BK * BN; idx += 256) {
+            const int kk = idx / BN, ol = idx % BN;
+            const int i = k0 + kk, o = o0 + ol;
+            const bool v = i < hin && o < hout;
+            const int64_t e = (int64_t)i * hout + o;
+            cp_async_zfill<sizeof(R)>(be + kk * BN + ol, v ? Em + e : Em, v);
+            cp_async_zfill<sizeof(R)>(bd + kk * BN + ol, v ? Dm + e : Dm, v);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    C ae[4][4], ad[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ae[a][b] = ad[a][b] = cmake<C>(0, 0);
+    const int nch = (hin + BK - 1) / BK;
+    stage(0, 0);
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) {
+            stage((ch + 1) & 1, (ch + 1) * BK);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+        const C* al = Al + (ch & 1) * BK * AP;
+        const C* ah = Ah + (ch & 1) * BK * AP;
+        const R* be = Be + (ch & 1) * BK * BN;
+        const R* bd = Bd + (ch & 1) * BK * BN;
+        auto mac = [&](int kk) {
+            C lo[4], hi[4];
+            R ev[4], dv[4];
+            ld4c(al + kk * AP + ty * 4, lo);
+            ld4c(ah + kk * AP + ty * 4, hi);
+            ld4r(be + kk * BN + tx * 4, ev);
+            ld4r(bd + kk * BN + tx * 4, dv);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const C e = cmake<C>(lo[i].x + hi[i].x, lo[i].y + hi[i].y);
+                const C d = cmake<C>(lo[i].x - hi[i].x, lo[i].y - hi[i].y);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    crfma(ae[i][j], ev[j], e);
+                    crfma(ad[i][j], dv[j], d);
+                }
+            }
+        };
+        const int kc = hin - ch * BK;
+        if (kc >= BK) {
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) mac(kk);
+        } else {                                  // the last, partial chunk: skip its zero fill
+#pragma unroll 2
+            for (int kk = 0; kk < kc; ++kk) mac(kk);
+        }
+        __syncthreads();                          // the buffer is restaged two chunks later
+    }
+    C* outm = out + (int64_t)mi * nbox * nout;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int c = c0 + ty * 4 + i;
+        if (c >= nbox) continue;
+        C* row = outm + (int64_t)c * nout;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int o = o0 + tx * 4 + j;
+            if (o >= hout) continue;
+            const C e = ae[i][j], d = ad[i][j];
+            row[o] = cmake<C>(e.x + d.x, e.y + d.y);
+            if (nout - 1 - o != o) row[nout - 1 - o] = cmake<C>(e.x - d.x, e.y - d.y);
+        }
+    }
+}
+
+// Mtc: the pre-split form of M for the tensor-core precisions; ME, MD: its parity halves
 template <typename R, typename C>
 static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int nout, const R* M, const void* Mtc,
-                             const C* in, C* out, cudaStream_t s) {
+                             const R* ME, const R* MD, const C* in, C* out, cudaStream_t s) {
     if constexpr (sizeof(C) == 8) {
         if (p.prec == MLFMA_PREC_FP32_TF32X3 || p.prec == MLFMA_PREC_FP32_BF16X3) {
             launch_theta_map_tc(p, nbox, Lc, nin, nout, Mtc, (const float2*)in, (float2*)out, s);
@@ -1565,6 +1687,18 @@ static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int n
         }
     }
     const int nm = 2 * Lc + 1;
+    if (ME && MD) {
+        const int hout = (nout + 1) / 2;
+        if (hout <= 32) {
+            k_theta_map_par<R, C, 32><<<dim3(nblk(nbox, 128), nblk(hout, 32), nm), 256, MapParShape<R, C, 32>::smem, s>>>(
+                (int)nbox, Lc, nin, nout, ME, MD, in, out);
+        } else {
+            k_theta_map_par<R, C, 64><<<dim3(nblk(nbox, 64), nblk(hout, 64), nm), 256, MapParShape<R, C, 64>::smem, s>>>(
+                (int)nbox, Lc, nin, nout, ME, MD, in, out);
+        }
+        MLFMA_LAUNCH_CHECK();
+        return;
+    }
     if (nout <= 16) {
         k_theta_map<R, C, 16><<<dim3(nblk(nbox, 256), nblk(nout, 16), nm), 256, MapShape<R, C, 16>::smem, s>>>(
             (int)nbox, Lc, nin, nout, M, in, out);
@@ -1645,8 +1779,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v,
                                                                           (C*)F.X);
                 MLFMA_LAUNCH_CHECK();
                 // B: theta maps per mode
-                launch_theta_map<R, C>(p, TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, F.AtTc, (const C*)F.X, (C*)F.Y,
-                                       s);
+                launch_theta_map<R, C>(p, TC.nbox, Lc, Ch.nth, F.nth, (const R*)F.At, F.AtTc, (const R*)F.AtE,
+                                       (const R*)F.AtD, (const C*)F.X, (C*)F.Y, s);
             }
             // C: z-shift per mode, inverse FFT, xy-shift, sum over children
             const int pbudget = (int)(p.tile_parent / sizeof(C));
@@ -1722,8 +1856,8 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v,
                     launch_l2l_out<C, R>(CPB, (int)T.nbox, (const C*)Pf.Y, Lc, F.nth, Pf.nth, F.fft, (const C*)F.tw,
                                          (const R*)Pf.Bt, Gc, s);
                 } else {
-                    launch_theta_map<R, C>(p, T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, Pf.BtTc, (const C*)Pf.Y,
-                                           (C*)Pf.X, s);
+                    launch_theta_map<R, C>(p, T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, Pf.BtTc, (const R*)Pf.BtE,
+                                           (const R*)Pf.BtD, (const C*)Pf.Y, (C*)Pf.X, s);
                     const int64_t rows_c = T.nbox * (int64_t)F.nth;
                     int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - F.nph, 2 * (F.nph + 1));
                     sm = ((size_t)2 * RB * (F.nph + 1) + F.nph) * sizeof(C);
@@ -1799,6 +1933,8 @@ static void prepare_fft_kernels() {
     allow_max_smem(k_theta_map<R, C, 16>);
     allow_max_smem(k_theta_map<R, C, 32>);
     allow_max_smem(k_theta_map<R, C, 64>);
+    allow_max_smem(k_theta_map_par<R, C, 32>);
+    allow_max_smem(k_theta_map_par<R, C, 64>);
 }
 
 void prepare_kernels(Plan& p) {

@@ -352,8 +352,8 @@ void build_forest(Plan& P) {
     std::vector<const void*> keep;
     for (int l = P.top ? P.top : 1; P.top && l <= Lmax; ++l) {
         const FarLevel& F = P.far[l];
-        const void* used[] = {F.x,  F.wgl,  F.dirs, F.tw,   F.T,    F.T1,   F.At, F.Bt,
-                              F.AtTc, F.BtTc, F.DmTc, F.DlTc, F.Soct, F.Sz, F.Sxy};
+        const void* used[] = {F.x,    F.wgl,  F.dirs, F.tw,   F.T,    F.T1,   F.At,   F.Bt, F.AtE,
+                              F.AtD,  F.BtE,  F.BtD,  F.AtTc, F.BtTc, F.DmTc, F.DlTc, F.Soct, F.Sz, F.Sxy};
         for (const void* q : used)
             if (q) keep.push_back(q);
     }

@@ -378,6 +378,46 @@ __global__ void k_dense_maps(int Lc, int nthc, int nphc, int nthp, int nphp, con
     Mq[sp * Kc + kc] = (float)(sb / nphp);
 }
 
+// Parity split of the theta maps (the GEMM form of the unfused level pairs evaluates the
+// even and odd parts at half the size each).  One thread per (m, i, i') over the half ranges
+// i < ceil(nth_c/2), i' < ceil(nth_p/2): the sums over n of Pbar_n^m(x_i) Pbar_n^m(x'_i') split
+// by the parity of n + m, times w_i (M2M map, input i) or w'_i' (L2L map, input i').  A row
+// for the middle input node of an odd grid (x = 0: only even terms) is halved, since the GEMM
+// forms its input as in[i] + in[n-1-i], twice the middle value; odd entries at a middle node
+// are zero.
+template <typename R>
+__global__ void k_interp_par(int Lc, const double* __restrict__ xc, const double* __restrict__ wc, int nthp,
+                             const double* __restrict__ xp, const double* __restrict__ wp, R* __restrict__ AtE,
+                             R* __restrict__ AtD, R* __restrict__ BtE, R* __restrict__ BtD) {
+    const int nthc = Lc + 1, hc = (nthc + 1) / 2, hp = (nthp + 1) / 2;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)(Lc + 1) * hc * hp) return;
+    const int ip = (int)(idx % hp);
+    const int i = (int)((idx / hp) % hc);
+    const int m = (int)(idx / ((int64_t)hp * hc));
+    const double a = xc[i], b = xp[ip];
+    double pa = pbar_mm(m, a), pb = pbar_mm(m, b);
+    double se = pa * pb, so = 0;                 // n = m: n + m even
+    if (m + 1 <= Lc) {
+        double qa = a * sqrt(2.0 * m + 3.0) * pa, qb = b * sqrt(2.0 * m + 3.0) * pb;
+        so += qa * qb;
+        for (int n = m + 2; n <= Lc; ++n) {
+            double an = sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+            double bn = sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+            double ra = an * (a * qa - bn * pa), rb = an * (b * qb - bn * pb);
+            pa = qa; qa = ra; pb = qb; qb = rb;
+            if (((n + m) & 1) == 0) se += ra * rb;
+            else so += ra * rb;
+        }
+    }
+    const bool midc = (nthc & 1) && i == hc - 1, midp = (nthp & 1) && ip == hp - 1;
+    const double sd = (midc || midp) ? 0.0 : so;
+    AtE[((int64_t)m * hc + i) * hp + ip] = (R)(se * wc[i] * (midc ? 0.5 : 1.0));
+    AtD[((int64_t)m * hc + i) * hp + ip] = (R)(sd * wc[i]);
+    BtE[((int64_t)m * hp + ip) * hc + i] = (R)(se * wp[ip] * (midp ? 0.5 : 1.0));
+    BtD[((int64_t)m * hp + ip) * hc + i] = (R)(sd * wp[ip]);
+}
+
 // the children's shifts by octant o: So[o][i'][j'] = Sz[o >> 2][i'] Sxy[o & 3][i'][j']
 template <typename C>
 __global__ void k_soct(int nth, int nph, const C* __restrict__ Sz, const C* __restrict__ Sxy, C* __restrict__ So) {
@@ -482,6 +522,14 @@ static void build_far_levels_t(Plan& p) {
         P.At = p.mem.make<R>(nA);
         P.Bt = p.mem.make<R>(nA);
         k_interp<R><<<nblk(nA, 128), 128, 0, s>>>(Ch.L, Ch.x, Ch.wgl, P.nth, P.x, P.wgl, (R*)P.At, (R*)P.Bt);
+        MLFMA_LAUNCH_CHECK();
+        const int64_t nH = (int64_t)(Ch.L + 1) * ((Ch.nth + 1) / 2) * ((P.nth + 1) / 2);
+        P.AtE = p.mem.make<R>(nH);
+        P.AtD = p.mem.make<R>(nH);
+        P.BtE = p.mem.make<R>(nH);
+        P.BtD = p.mem.make<R>(nH);
+        k_interp_par<R><<<nblk(nH, 128), 128, 0, s>>>(Ch.L, Ch.x, Ch.wgl, P.nth, P.x, P.wgl, (R*)P.AtE, (R*)P.AtD,
+                                                       (R*)P.BtE, (R*)P.BtD);
         MLFMA_LAUNCH_CHECK();
         if (p.prec == MLFMA_PREC_FP32_TF32X3 || p.prec == MLFMA_PREC_FP32_BF16X3) {
             // the maps split once into the tensor-core operand blocks (At: nth_c -> nth_p, Bt: nth_p -> nth_c)
