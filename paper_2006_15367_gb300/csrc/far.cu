@@ -1248,16 +1248,19 @@ __global__ void k_l2l_fft_out(int nrows_tot, const C* __restrict__ H, int Lc, Ff
 // ============================================================== fused phi transform + theta map (fine levels)
 // For level pairs whose child rows fit in shared memory a CTA takes CPB (2 ... 16, a power
 // of two) consecutive child boxes and keeps the spectral rows on chip between the phi transform and
-// the theta map.  The theta map is register-blocked over the CTA's children: a thread owns
-// one (mode, output row) pair and one accumulator per child, so each map entry is loaded
+// the theta map.  The theta map is register-blocked over the CTA's children and split by
+// parity like k_theta_map_par: a thread owns one mode, one output row o and its mirror n'-1-o,
+// with an even and an odd accumulator per child, so each entry of the map's halves is loaded
 // once per CTA and the spectral samples are shared-memory broadcasts.
 constexpr int kMaxCPB = 16;
 
-// M2M first two steps:  Y[mi][c][i'] = scale sum_i At[|m|][i][i'] sum_j F[c][i][j] e^{-i m phi_j}.
+// M2M first two steps:  Y[mi][c][i'] = scale sum_i At[|m|][i][i'] sum_j F[c][i][j] e^{-i m phi_j}
+// (At applied as its parity halves AtE, AtD).
 // dnh divides by (nthp + 1) / 2.
 template <typename C, typename R, int CPB>
 __global__ void k_m2m_in(int nbox_c, const C* __restrict__ F, int Lc, int nthc, int nthp, FftPlan fp,
-                         const C* __restrict__ tw, R scale, const R* __restrict__ At, FastDiv dnh, C* __restrict__ Y) {
+                         const C* __restrict__ tw, R scale, const R* __restrict__ AtE, const R* __restrict__ AtD,
+                         FastDiv dnh, C* __restrict__ Y) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
     // unpadded rows: no loop here walks across rows with consecutive threads
@@ -1274,45 +1277,49 @@ __global__ void k_m2m_in(int nbox_c, const C* __restrict__ F, int Lc, int nthc, 
     __syncthreads();
     const C* res = fft_rows(buf0, buf1, nr, fp, stw, false, n);
     const int rowc = nthc * n;                     // stride between children in res
-    // a thread takes output rows o and o + 1 of one mode: each spectral sample it reads from
-    // shared memory feeds both (the accumulation order of every output is unchanged)
-    const int nh = (nthp + 1) >> 1;
+    // a thread takes output row o and its mirror nthp - 1 - o of one mode, from the parity
+    // halves of the map (even part on e_i = x_i + x_{n-1-i}, odd part on d_i = x_i - x_{n-1-i})
+    const int nh = (nthp + 1) >> 1, hin = (nthc + 1) >> 1;
     for (int idx = threadIdx.x; idx < nm * nh; idx += blockDim.x) {
-        const int mi = (int)dnh.div((unsigned)idx), o = 2 * (idx - mi * nh);
-        const bool two = o + 1 < nthp;
+        const int mi = (int)dnh.div((unsigned)idx), o = idx - mi * nh;
         const int m = abs(mi - Lc);
-        const R* Am = At + (int64_t)m * nthc * nthp + o;
+        const R* Em = AtE + (int64_t)m * hin * nh + o;
+        const R* Dm = AtD + (int64_t)m * hin * nh + o;
         const C* xr = res + wrap(mi - Lc, n);
-        C acc0[CPB], acc1[CPB];
+        C ae[CPB], ad[CPB];
 #pragma unroll
-        for (int c = 0; c < CPB; ++c) acc0[c] = acc1[c] = cmake<C>(0, 0);
-        for (int i = 0; i < nthc; ++i) {
-            const R a0 = Am[i * nthp], a1 = two ? Am[i * nthp + 1] : (R)0;
-            const C* xi = xr + i * n;
+        for (int c = 0; c < CPB; ++c) ae[c] = ad[c] = cmake<C>(0, 0);
+        for (int i = 0; i < hin; ++i) {
+            const R e = Em[i * nh], d = Dm[i * nh];
+            const C* xl = xr + i * n;
+            const C* xh = xr + (nthc - 1 - i) * n;
 #pragma unroll
             for (int c = 0; c < CPB; ++c)
                 if (c < ncb) {
-                    const C x = xi[c * rowc];
-                    crfma(acc0[c], a0, x);
-                    crfma(acc1[c], a1, x);
+                    const C lo = xl[c * rowc], hi = xh[c * rowc];
+                    crfma(ae[c], e, cmake<C>(lo.x + hi.x, lo.y + hi.y));
+                    crfma(ad[c], d, cmake<C>(lo.x - hi.x, lo.y - hi.y));
                 }
         }
-        C* yo = Y + ((int64_t)mi * nbox_c + c0) * nthp + o;
+        C* yo = Y + ((int64_t)mi * nbox_c + c0) * nthp;
+        const bool mirror = nthp - 1 - o != o;
 #pragma unroll
         for (int c = 0; c < CPB; ++c)
             if (c < ncb) {
-                yo[c * nthp] = cmake<C>(acc0[c].x * scale, acc0[c].y * scale);
-                if (two) yo[c * nthp + 1] = cmake<C>(acc1[c].x * scale, acc1[c].y * scale);
+                yo[c * nthp + o] = cmake<C>((ae[c].x + ad[c].x) * scale, (ae[c].y + ad[c].y) * scale);
+                if (mirror) yo[c * nthp + nthp - 1 - o] = cmake<C>((ae[c].x - ad[c].x) * scale, (ae[c].y - ad[c].y) * scale);
             }
     }
 }
 
-// L2L last two steps:  G[c][i][j] += sum_m e^{-i m phi_j} sum_i' Bt[|m|][i'][i] H[mi][c][i'].
+// L2L last two steps:  G[c][i][j] += sum_m e^{-i m phi_j} sum_i' Bt[|m|][i'][i] H[mi][c][i']
+// (Bt applied as its parity halves BtE, BtD).
 // The CTA's slice of H is staged in shared memory first.  dnh divides by (nthc + 1) / 2, dhrow
 // by ncb nthp (dhfull: CPB nthp, the value for every CTA but the last).
 template <typename C, typename R, int CPB>
 __global__ void k_l2l_out(int nbox_c, const C* __restrict__ H, int Lc, int nthc, int nthp, FftPlan fp,
-                          const C* __restrict__ tw, const R* __restrict__ Bt, FastDiv dnh, FastDiv dhrow,
+                          const C* __restrict__ tw, const R* __restrict__ BtE, const R* __restrict__ BtD, FastDiv dnh,
+                          FastDiv dhrow,
                           FastDiv dhfull, C* __restrict__ G) {
     extern __shared__ unsigned char smem_raw[];
     const int n = fp.n, nm = 2 * Lc + 1;
@@ -1334,33 +1341,34 @@ __global__ void k_l2l_out(int nbox_c, const C* __restrict__ H, int Lc, int nthc,
     for (int idx = threadIdx.x; idx < nr * pn; idx += blockDim.x) buf0[idx] = cmake<C>(0, 0);
     cp_async_wait_all();
     __syncthreads();
-    // a thread takes child rows i and i + 1 of one mode: each staged sample feeds both
-    const int nh = (nthc + 1) >> 1;
+    // a thread takes child row i and its mirror nthc - 1 - i of one mode, from the parity halves
+    const int nh = (nthc + 1) >> 1, hin = (nthp + 1) >> 1;
     for (int idx = threadIdx.x; idx < nm * nh; idx += blockDim.x) {
-        const int mi = (int)dnh.div((unsigned)idx), i = 2 * (idx - mi * nh);
-        const bool two = i + 1 < nthc;
+        const int mi = (int)dnh.div((unsigned)idx), i = idx - mi * nh;
         const int m = abs(mi - Lc);
-        const R* Bm = Bt + (int64_t)m * nthp * nthc + i;
+        const R* Em = BtE + (int64_t)m * hin * nh + i;
+        const R* Dm = BtD + (int64_t)m * hin * nh + i;
         const C* hm = hs + mi * hp;
-        C acc0[CPB], acc1[CPB];
+        C ae[CPB], ad[CPB];
 #pragma unroll
-        for (int c = 0; c < CPB; ++c) acc0[c] = acc1[c] = cmake<C>(0, 0);
-        for (int ip = 0; ip < nthp; ++ip) {
-            const R b0 = Bm[ip * nthc], b1 = two ? Bm[ip * nthc + 1] : (R)0;
+        for (int c = 0; c < CPB; ++c) ae[c] = ad[c] = cmake<C>(0, 0);
+        for (int ip = 0; ip < hin; ++ip) {
+            const R e = Em[ip * nh], d = Dm[ip * nh];
 #pragma unroll
             for (int c = 0; c < CPB; ++c)
                 if (c < ncb) {
-                    const C h = hm[c * nthp + ip];
-                    crfma(acc0[c], b0, h);
-                    crfma(acc1[c], b1, h);
+                    const C lo = hm[c * nthp + ip], hi = hm[c * nthp + nthp - 1 - ip];
+                    crfma(ae[c], e, cmake<C>(lo.x + hi.x, lo.y + hi.y));
+                    crfma(ad[c], d, cmake<C>(lo.x - hi.x, lo.y - hi.y));
                 }
         }
         const int col = wrap(mi - Lc, n);
+        const bool mirror = nthc - 1 - i != i;
 #pragma unroll
         for (int c = 0; c < CPB; ++c)
             if (c < ncb) {
-                buf0[(c * nthc + i) * pn + col] = acc0[c];
-                if (two) buf0[(c * nthc + i + 1) * pn + col] = acc1[c];
+                buf0[(c * nthc + i) * pn + col] = cmake<C>(ae[c].x + ad[c].x, ae[c].y + ad[c].y);
+                if (mirror) buf0[(c * nthc + nthc - 1 - i) * pn + col] = cmake<C>(ae[c].x - ad[c].x, ae[c].y - ad[c].y);
             }
     }
     __syncthreads();
@@ -1411,11 +1419,11 @@ static int fused_children(size_t budget, int nthc, int n, int pitch, int extra, 
 
 template <typename C, typename R>
 static void launch_m2m_in(int CPB, int nbox_c, const C* F, int Lc, int nthc, int nthp, const FftPlan& fp, const C* tw,
-                          R scale, const R* At, C* Y, cudaStream_t s) {
+                          R scale, const R* AtE, const R* AtD, C* Y, cudaStream_t s) {
     const size_t sm = ((size_t)2 * CPB * nthc * fp.n + fp.n) * sizeof(C);
     const FastDiv d = FastDiv::make((nthp + 1) / 2);
     switch (CPB) {
-#define M2M_IN(c) case c: k_m2m_in<C, R, c><<<nblk(nbox_c, c), 128, sm, s>>>(nbox_c, F, Lc, nthc, nthp, fp, tw, scale, At, d, Y); break;
+#define M2M_IN(c) case c: k_m2m_in<C, R, c><<<nblk(nbox_c, c), 128, sm, s>>>(nbox_c, F, Lc, nthc, nthp, fp, tw, scale, AtE, AtD, d, Y); break;
         M2M_IN(2) M2M_IN(4) M2M_IN(8) M2M_IN(16)
 #undef M2M_IN
         default: fail(MLFMA_ERR_INVALID_ARG, "children per CTA %d", CPB);
@@ -1425,14 +1433,14 @@ static void launch_m2m_in(int CPB, int nbox_c, const C* F, int Lc, int nthc, int
 
 template <typename C, typename R>
 static void launch_l2l_out(int CPB, int nbox_c, const C* H, int Lc, int nthc, int nthp, const FftPlan& fp, const C* tw,
-                           const R* Bt, C* G, cudaStream_t s) {
+                           const R* BtE, const R* BtD, C* G, cudaStream_t s) {
     const size_t rows = (size_t)CPB * nthc * (fp.n + 1), hsz = (size_t)(2 * Lc + 1) * (CPB * nthp + 1);
     const size_t sm = (rows + fp.n + std::max(rows, hsz)) * sizeof(C);
     const FastDiv d = FastDiv::make((nthc + 1) / 2);
     const int tail = nbox_c % CPB ? nbox_c % CPB : CPB;      // children of the last CTA
     const FastDiv dt = FastDiv::make(tail * nthp), df = FastDiv::make(CPB * nthp);
     switch (CPB) {
-#define L2L_OUT(c) case c: k_l2l_out<C, R, c><<<nblk(nbox_c, c), 128, sm, s>>>(nbox_c, H, Lc, nthc, nthp, fp, tw, Bt, d, dt, df, G); break;
+#define L2L_OUT(c) case c: k_l2l_out<C, R, c><<<nblk(nbox_c, c), 128, sm, s>>>(nbox_c, H, Lc, nthc, nthp, fp, tw, BtE, BtD, d, dt, df, G); break;
         L2L_OUT(2) L2L_OUT(4) L2L_OUT(8) L2L_OUT(16)
 #undef L2L_OUT
         default: fail(MLFMA_ERR_INVALID_ARG, "children per CTA %d", CPB);
@@ -1446,7 +1454,7 @@ static void launch_l2l_out(int CPB, int nbox_c, const C* H, int Lc, int nthc, in
 // Tile BM boxes x BN outputs per CTA (BM * BN = 4096), 256 threads, 4 x 4 per thread; the
 // reduction runs in chunks of BK (16 complex64, 8 complex128) staged in shared memory by
 // cp.async, double-buffered so that the next chunk loads while this one is multiplied (three
-// stages measured no better: 9.33 vs 9.28 ms per matvec).
+// stages measured no better than two).
 template <typename C> __device__ __forceinline__ void ld4c(const C* p, C (&v)[4]) {
     if constexpr (sizeof(C) == 8) {            // two 16-byte loads
         const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 2);
@@ -1466,94 +1474,6 @@ template <typename R> __device__ __forceinline__ void ld4r(const R* p, R (&v)[4]
     }
 }
 
-template <typename R, typename C, int BN>
-struct MapShape {
-    static constexpr int BM = 4096 / BN, BK = sizeof(C) == 8 ? 16 : 8, AP = BM + 2;   // AP: padded row of As
-    static constexpr size_t smem = 2 * ((size_t)BK * AP * sizeof(C) + (size_t)BK * BN * sizeof(R));
-};
-
-template <typename R, typename C, int BN>
-__global__ void __launch_bounds__(256) k_theta_map(int nbox, int Lc, int nin, int nout, const R* __restrict__ M,
-                                                   const C* __restrict__ in, C* __restrict__ out) {
-    using S = MapShape<R, C, BN>;
-    constexpr int BM = S::BM, BK = S::BK, AP = S::AP;
-    constexpr int TX = BN / 4;            // threads along outputs
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* As = reinterpret_cast<C*>(smem_raw);                    // [2][BK][AP]
-    R* Bs = reinterpret_cast<R*>(As + 2 * BK * AP);            // [2][BK][BN]
-    const int mi = blockIdx.z;
-    const int m = abs(mi - Lc);
-    const int c0 = blockIdx.x * BM, o0 = blockIdx.y * BN;
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const C* inm = in + (int64_t)mi * nbox * nin;
-    const R* Mm = M + (int64_t)m * nin * nout;
-    auto stage = [&](int buf, int k0) {
-        C* a = As + buf * BK * AP;
-        R* bb = Bs + buf * BK * BN;
-        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
-            const int cl = idx / BK, kk = idx % BK;
-            const int c = c0 + cl, i = k0 + kk;
-            const bool v = c < nbox && i < nin;
-            cp_async_zfill<sizeof(C)>(a + kk * AP + cl, v ? inm + (int64_t)c * nin + i : inm, v);
-        }
-        for (int idx = threadIdx.x; idx < BK * BN; idx += 256) {
-            const int kk = idx / BN, ol = idx % BN;
-            const int i = k0 + kk, o = o0 + ol;
-            const bool v = i < nin && o < nout;
-            cp_async_zfill<sizeof(R)>(bb + kk * BN + ol, v ? Mm + (int64_t)i * nout + o : Mm, v);
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
-    C acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = cmake<C>(0, 0);
-    const int nch = (nin + BK - 1) / BK;
-    stage(0, 0);
-    for (int ch = 0; ch < nch; ++ch) {
-        if (ch + 1 < nch) {
-            stage((ch + 1) & 1, (ch + 1) * BK);
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        }
-        __syncthreads();
-        const C* a = As + (ch & 1) * BK * AP;
-        const R* bb = Bs + (ch & 1) * BK * BN;
-        auto mac = [&](int kk) {
-            C av[4];
-            R bv[4];
-            ld4c(a + kk * AP + ty * 4, av);
-            ld4r(bb + kk * BN + tx * 4, bv);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) crfma(acc[i][j], bv[j], av[i]);
-        };
-        const int kc = nin - ch * BK;
-        if (kc >= BK) {
-#pragma unroll
-            for (int kk = 0; kk < BK; ++kk) mac(kk);
-        } else {                                  // the last, partial chunk: skip its zero fill
-#pragma unroll 4
-            for (int kk = 0; kk < kc; ++kk) mac(kk);
-        }
-        __syncthreads();                          // the buffer is restaged two chunks later
-    }
-    C* outm = out + (int64_t)mi * nbox * nout;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int c = c0 + ty * 4 + i;
-        if (c >= nbox) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int o = o0 + tx * 4 + j;
-            if (o < nout) outm[(int64_t)c * nout + o] = acc[i][j];
-        }
-    }
-}
-
 // The same GEMM by parity.  Gauss-Legendre nodes come in pairs (x, -x) and every map is
 // centrosymmetric, M[n-1-i][n'-1-o] = M[i][o], so with e_i = in[i] + in[n-1-i] and
 // d_i = in[i] - in[n-1-i] (i < ceil(n/2)) the halves
@@ -1561,8 +1481,8 @@ __global__ void __launch_bounds__(256) k_theta_map(int nbox, int Lc, int nin, in
 // give out[o] = oe + od and out[n'-1-o] = oe - od: two GEMMs of a quarter of the size, half the
 // multiply-adds of the full map.  ME and MD are built at plan creation from the even and odd
 // terms of the Legendre sums (k_interp_par; ME's middle row halved, because e takes the middle
-// sample twice).  The CTA stages the rows in[i] and in[n-1-i] of its chunk (cp.async, double-
-// buffered like k_theta_map) and forms e and d in registers as it multiplies.
+// sample twice).  The CTA stages the rows in[i] and in[n-1-i] of its chunk and forms e and d
+// in registers as it multiplies.
 template <typename R, typename C, int BN>
 struct MapParShape {
     static constexpr int BM = 4096 / BN, BK = sizeof(C) == 8 ? 16 : 8, AP = BM + 2;
@@ -1687,27 +1607,13 @@ static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int n
         }
     }
     const int nm = 2 * Lc + 1;
-    if (ME && MD) {
-        const int hout = (nout + 1) / 2;
-        if (hout <= 32) {
-            k_theta_map_par<R, C, 32><<<dim3(nblk(nbox, 128), nblk(hout, 32), nm), 256, MapParShape<R, C, 32>::smem, s>>>(
-                (int)nbox, Lc, nin, nout, ME, MD, in, out);
-        } else {
-            k_theta_map_par<R, C, 64><<<dim3(nblk(nbox, 64), nblk(hout, 64), nm), 256, MapParShape<R, C, 64>::smem, s>>>(
-                (int)nbox, Lc, nin, nout, ME, MD, in, out);
-        }
-        MLFMA_LAUNCH_CHECK();
-        return;
-    }
-    if (nout <= 16) {
-        k_theta_map<R, C, 16><<<dim3(nblk(nbox, 256), nblk(nout, 16), nm), 256, MapShape<R, C, 16>::smem, s>>>(
-            (int)nbox, Lc, nin, nout, M, in, out);
-    } else if (nout <= 32) {
-        k_theta_map<R, C, 32><<<dim3(nblk(nbox, 128), nblk(nout, 32), nm), 256, MapShape<R, C, 32>::smem, s>>>(
-            (int)nbox, Lc, nin, nout, M, in, out);
+    const int hout = (nout + 1) / 2;
+    if (hout <= 32) {
+        k_theta_map_par<R, C, 32><<<dim3(nblk(nbox, 128), nblk(hout, 32), nm), 256, MapParShape<R, C, 32>::smem, s>>>(
+            (int)nbox, Lc, nin, nout, ME, MD, in, out);
     } else {
-        k_theta_map<R, C, 64><<<dim3(nblk(nbox, 64), nblk(nout, 64), nm), 256, MapShape<R, C, 64>::smem, s>>>(
-            (int)nbox, Lc, nin, nout, M, in, out);
+        k_theta_map_par<R, C, 64><<<dim3(nblk(nbox, 64), nblk(hout, 64), nm), 256, MapParShape<R, C, 64>::smem, s>>>(
+            (int)nbox, Lc, nin, nout, ME, MD, in, out);
     }
     MLFMA_LAUNCH_CHECK();
 }
@@ -1769,7 +1675,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v,
             if (CPB) {
                 // A+B: forward FFT of the children's rows and theta maps, on chip
                 launch_m2m_in<C, R>(CPB, (int)TC.nbox, Fc, Lc, Ch.nth, F.nth, Ch.fft, (const C*)Ch.tw,
-                                    (R)(1.0 / Ch.nph), (const R*)F.At, (C*)F.Y, s);
+                                    (R)(1.0 / Ch.nph), (const R*)F.AtE, (const R*)F.AtD, (C*)F.Y, s);
             } else {
                 // A: forward FFT of the children's rows, modes |m| <= Lc
                 int RB = tile_rows((int)std::min<int64_t>(rows_c, 1 << 20), budget - Ch.nph, 2 * (Ch.nph + 1));
@@ -1854,7 +1760,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v,
                 if (CPB) {
                     // theta maps and inverse FFT of the children's rows, on chip; added to G
                     launch_l2l_out<C, R>(CPB, (int)T.nbox, (const C*)Pf.Y, Lc, F.nth, Pf.nth, F.fft, (const C*)F.tw,
-                                         (const R*)Pf.Bt, Gc, s);
+                                         (const R*)Pf.BtE, (const R*)Pf.BtD, Gc, s);
                 } else {
                     launch_theta_map<R, C>(p, T.nbox, Lc, Pf.nth, F.nth, (const R*)Pf.Bt, Pf.BtTc, (const R*)Pf.BtE,
                                            (const R*)Pf.BtD, (const C*)Pf.Y, (C*)Pf.X, s);
@@ -1930,9 +1836,6 @@ static void prepare_fft_kernels() {
     allow_max_smem(k_l2l_out<C, R, 8>);
     allow_max_smem(k_l2l_out<C, R, 16>);
     allow_max_smem(k_l2l_fft_out<C>);
-    allow_max_smem(k_theta_map<R, C, 16>);
-    allow_max_smem(k_theta_map<R, C, 32>);
-    allow_max_smem(k_theta_map<R, C, 64>);
     allow_max_smem(k_theta_map_par<R, C, 32>);
     allow_max_smem(k_theta_map_par<R, C, 64>);
 }
