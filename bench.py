@@ -424,7 +424,9 @@ def config_dict(args, n, prm):
     if args.digits:
         wl += " (digits set on the command line; leaf edge and level count as in the plan object)"
     return {"workload": wl + f", {args.precision.upper()} complex, nrhs={args.nrhs}"
-                        + (", forward+backward (charges and positions)" if args.mode == "grad" else ""),
+                        + (", forward+backward (charges and positions)" if args.mode == "grad" else "")
+                        + (f", sampled operators (oversampling {args.sampled_operators})"
+                           if getattr(args, "sampled_operators", 0) else ""),
             "n": n, "digits": prm["digits"], "nrhs": args.nrhs, "mode": args.mode,
             "parallelism": f"replicas x{_dist()[0]}",
             "l2": "flushed between steps (256 MiB write outside the timed events)"}
@@ -456,6 +458,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "tf32x3", "bf16x3"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--digits", type=int, default=0, help="override the workload's digits (0: keep)")
+    ap.add_argument("--sampled-operators", type=int, default=0,
+                    help="oversampling of sampled translation operators at the wavelength-sized levels (0: full tables)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the default interpolation tile budgets instead of the plan-time autotuner "
                          "(--ncu always does: kernels outside the capture run slower under the profiler)")
@@ -490,7 +494,7 @@ def main():
     qd = torch.as_tensor(Q.astype(cdt), device=dev)
     out = torch.empty_like(qd)
     plan = mf.Plan(ptd, prm["k"], prm["digits"], leaf_max=prm.get("leaf_max", 0), precision=args.precision,
-                   offsets=offsets, autotune=not (args.no_autotune or args.ncu))
+                   offsets=offsets, autotune=not (args.no_autotune or args.ncu), sampled_operators=args.sampled_operators)
     info = plan.info()
     stream = plan.stream
 
@@ -629,7 +633,7 @@ def main():
         roof.update({"achieved": ach, "frac": ach / fp32_peak, "launches_per_step": int(m2l_launches),
                      "work": "8 flops per complex MAC x sum over levels of nv_l K_l (per step, all launches of "
                              "k_m2l and k_m2l_tail)"})
-        tr = measured_traffic(args.workload, args.precision, nrhs, args.mode)
+        tr = None if args.sampled_operators else measured_traffic(args.workload, args.precision, nrhs, args.mode)
         if tr is not None:
             roof["traffic"] = tr["bytes_per_step"]
             roof["traffic_source"] = tr["source"]
