@@ -400,6 +400,9 @@ static void init_streams(Plan& P, int nsub) {
     MLFMA_CUDA(cudaStreamCreateWithFlags(&P.nstream, cudaStreamNonBlocking));
     MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_nfork, cudaEventDisableTiming));
     MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_near, cudaEventDisableTiming));
+    MLFMA_CUDA(cudaStreamCreateWithFlags(&P.mstream, cudaStreamNonBlocking));
+    MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_mfork, cudaEventDisableTiming));
+    MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_mdone, cudaEventDisableTiming));
     for (int w = 0; w < nsub; ++w) {
         cudaStream_t st;
         cudaEvent_t ev;
@@ -414,6 +417,7 @@ static void release_plan(Plan& P) {
     if (P.stream) cudaStreamSynchronize(P.stream);
     if (P.gstream) cudaStreamSynchronize(P.gstream);
     if (P.nstream) cudaStreamSynchronize(P.nstream);
+    if (P.mstream) cudaStreamSynchronize(P.mstream);
     for (auto s : P.sub_streams) cudaStreamSynchronize(s);
     drop_graphs(P);
     for (auto* sp : P.subs) {
@@ -435,8 +439,11 @@ static void release_plan(Plan& P) {
     if (P.ev_nfork) cudaEventDestroy(P.ev_nfork);
     if (P.ev_near) cudaEventDestroy(P.ev_near);
     if (P.nstream) cudaStreamDestroy(P.nstream);
-    P.ev_fork = P.ev_join = P.ev_nfork = P.ev_near = nullptr;
-    P.gstream = P.nstream = nullptr;
+    if (P.ev_mfork) cudaEventDestroy(P.ev_mfork);
+    if (P.ev_mdone) cudaEventDestroy(P.ev_mdone);
+    if (P.mstream) cudaStreamDestroy(P.mstream);
+    P.ev_fork = P.ev_join = P.ev_nfork = P.ev_near = P.ev_mfork = P.ev_mdone = nullptr;
+    P.gstream = P.nstream = P.mstream = nullptr;
     P.mem.release_all();
 }
 

@@ -298,6 +298,11 @@ struct Plan {
     // (single and forest plans; null: one stream)
     cudaStream_t nstream = nullptr;
     cudaEvent_t ev_nfork = nullptr, ev_near = nullptr;
+    // M2L beside the upward pass: a level's M2L runs on mstream once its F is complete (ev_mfork,
+    // recorded after the level's C2M and M2M), while the plan stream goes on up the tree; the
+    // downward pass waits for ev_mdone, recorded after the last (top) level's M2L
+    cudaStream_t mstream = nullptr;
+    cudaEvent_t ev_mfork = nullptr, ev_mdone = nullptr;
     std::map<int64_t, cudaGraphExec_t> graphs;
     // batched plans: independent geometries; level-uniform ones are merged into this plan as a
     // forest (the sub-plans then only hold the shared operators), others run concurrently on

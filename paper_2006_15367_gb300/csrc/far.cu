@@ -1622,9 +1622,10 @@ static void launch_theta_map(const Plan& p, int64_t nbox, int Lc, int nin, int n
 // One pass of the far field for NR right-hand sides (charges qs[r n + j], potentials
 // phis[r n + j]; signatures of level l r nbox_l K_l apart).  C2M, M2L and L2O take all NR
 // at once; the interpolation steps run per right-hand side on the shared spectral scratch.
-// Upward pass, then M2L and L2L down the levels, then L2O at every level with leaves (after
-// near_done, when the near field runs on another stream: L2O adds to what it wrote; each
-// level's local signatures stay in place after its L2L, so L2O can come last).
+// Upward pass (with each level's M2L beside it once the level's F is complete), then L2L down
+// the levels, then L2O at every level with leaves (after near_done, when the near field runs
+// on another stream: L2O adds to what it wrote; each level's local signatures stay in place
+// after its L2L, so L2O can come last).
 template <typename R, int NR>
 static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v, cudaEvent_t near_done) {
     using C = typename Cx<R>::T;
@@ -1634,8 +1635,13 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v,
     const R k = (R)p.k;
     const int64_t sn = p.n;
     auto sF = [&](int l) { return p.lev[l].nbox * p.far[l].K; };
+    // M2L of a level needs only that level's F: unless stage timings are being taken, it runs
+    // on its own stream as soon as the upward pass has completed F (the fork and join are
+    // events, kept as graph edges in a captured apply); the downward pass starts after the
+    // last of them
+    const bool mfork = p.mstream && !p.profiling;
     // ---- upward pass: C2M at every far level's leaves, M2M from the deepest level up
-    for (int l = p.nlev; l >= p.top; --l) {
+    auto upward = [&](int l) {
         FarLevel& F = p.far[l];
         TreeLevel& T = p.lev[l];
         if (T.nleaf > 0) {
@@ -1652,7 +1658,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v,
                 MLFMA_LAUNCH_CHECK();
             }
         }
-        if (l == p.nlev) continue;
+        if (l == p.nlev) return;
         FarLevel& Ch = p.far[l + 1];
         TreeLevel& TC = p.lev[l + 1];
         if (F.dense) {
@@ -1661,7 +1667,7 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v,
             for (int r = 0; r < NR; ++r)
                 launch_dense_m2m_tc(p, TC.nbox, (int)Ch.K, (int)F.K, F.DmTc, TC.parent, TC.key, (const float2*)F.Soct,
                                     (const float2*)Ch.F + r * sF(l + 1), (float2*)F.F + r * sF(l), s);
-            continue;
+            return;
         }
         const int Lc = Ch.L;
         const int64_t rows_c = TC.nbox * (int64_t)Ch.nth;
@@ -1706,13 +1712,25 @@ static void far_pipeline(Plan& p, const void* qs_v, void* phis_v, void* grads_v,
             }
             MLFMA_LAUNCH_CHECK();
         }
+    };
+    for (int l = p.nlev; l >= p.top; --l) {
+        upward(l);
+        if (mfork) {
+            MLFMA_CUDA(cudaEventRecord(p.ev_mfork, s));
+            MLFMA_CUDA(cudaStreamWaitEvent(p.mstream, p.ev_mfork, 0));
+            launch_m2l<R, C, NR>(p, l, p.mstream);
+        }
     }
-    // ---- downward pass: M2L, L2L, L2O
+    if (mfork) {
+        MLFMA_CUDA(cudaEventRecord(p.ev_mdone, p.mstream));
+        MLFMA_CUDA(cudaStreamWaitEvent(s, p.ev_mdone, 0));
+    }
+    // ---- downward pass: M2L (unless it ran beside the upward pass), L2L, L2O
     for (int l = p.top; l <= p.nlev; ++l) {
         FarLevel& F = p.far[l];
         TreeLevel& T = p.lev[l];
         TreeLevel& TP = p.lev[l - 1];
-        {
+        if (!mfork) {
             StageTimer st(p, MLFMA_STAGE_M2L, l, m2l_launches<C, NR>(F.K, TP.nbox, F.T1 != nullptr));
             launch_m2l<R, C, NR>(p, l, s);
         }
