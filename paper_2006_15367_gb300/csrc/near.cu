@@ -12,21 +12,31 @@
 // k R / pi to [-1, 1] (absolute error about 4e-7).
 #include <cstdio>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace mlfma {
 
 static inline int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+// 1/R from R^2, 0 for coincident points (the excluded self term).  FP32: the SFU's reciprocal
+// square root with subnormals flushed (rsqrt.approx.ftz.f32: no subnormal handling around it),
+// so a squared distance below the smallest normal float (R < 1.1e-19) counts as coincident.
+__device__ __forceinline__ float inv_dist(float r2) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+    return r2 >= 1.17549435e-38f ? y : 0.f;
+}
+__device__ __forceinline__ double inv_dist(double r2) { return r2 > 0.0 ? rsqrt(r2) : 0.0; }
 
-// sin and cos of pi * x.  FP32: reduce x to [-1, 1] (x - 2 rint(x / 2)), then the SFU
-// __sincosf on [-pi, pi] (absolute error ~4e-7, below the FP32 path's tolerance);
-// FP64: sincospi.
+// sin and cos of pi * x.  FP32: reduce x to [-1, 1] (x - 2 rint(x / 2)), then the SFU's sine
+// and cosine on [-pi, pi] (sin.approx / cos.approx with subnormals flushed: absolute error
+// ~4e-7, below the FP32 path's tolerance); FP64: sincospi.
 __device__ __forceinline__ void scpi_fast(float x, float& s, float& c) {
-    const float r = x - 2.0f * rintf(0.5f * x);
-    __sincosf(3.14159265358979f * r, &s, &c);
+    const float a = 3.14159265358979f * (x - 2.0f * rintf(0.5f * x));
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(a));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(a));
 }
 __device__ __forceinline__ void scpi_fast(double x, double& s, double& c) { sincospi(x, &s, &c); }
 
@@ -104,7 +114,7 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t nleaf, const int* __restric
     auto term = [&](R tx, R ty, R tz, int jj, C (&ac)[NR], C (&gg)[3]) {
         const R dx = tx - sx[wl][jj], dy = ty - sy[wl][jj], dz = tz - sz[wl][jj];
         const R r2 = dx * dx + dy * dy + dz * dz;
-        const R inv = r2 > (R)0 ? rsq(r2) : (R)0;
+        const R inv = inv_dist(r2);
         const R r = r2 * inv;
         R s, c;
         scpi_fast(kpi * r, s, c);
@@ -268,14 +278,14 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_tile(const int2* __restrict__ 
                     const R r2 = dx * dx + dy * dy + dz * dz;
                     if (!GRAD) {
                         // branch-free: R = 0 (self / coincident) gives inv = 0 and no contribution
-                        const R inv = r2 > (R)0 ? rsq(r2) : (R)0;
+                        const R inv = inv_dist(r2);
                         R s, c;
                         scpi_fast(kpi * (r2 * inv), s, c);
                         const C g = cmake<C>(c * inv, s * inv);
 #pragma unroll
                         for (int r = 0; r < NR; ++r) cfma(acc[r], sq[r][m], g);
                     } else {
-                        const R inv = r2 > (R)0 ? rsq(r2) : (R)0;
+                        const R inv = inv_dist(r2);
                         const R r = r2 * inv;
                         R s, c;
                         scpi_fast(kpi * r, s, c);
@@ -367,24 +377,29 @@ __global__ void __launch_bounds__(kP2PTile) k_p2p_sym(const int4* __restrict__ i
         C rev = cmake<C>(0, 0);
         const SrcPos<R>* pl = sp + lane;
         const R* ql = sqi + lane;
-        // B = A: the chunks that overlap the tile keep only j > i (the chunks above it need no mask)
-        const bool mask = self && k0 < it.y + kP2PTile;
+        // B = A: the chunks that overlap the tile keep only j > i (the chunks above it need no mask,
+        // and run a loop without the test)
+        auto steps = [&](auto masked) {
 #pragma unroll 4
-        for (int st = 0; st < 32; ++st) {
-            const SrcPos<R> ps = pl[st];
-            const R qjy = ql[st];
-            const R dx = x - ps.x, dy = y - ps.y, dz = z - ps.z;
-            const R r2 = dx * dx + dy * dy + dz * dz;
-            R inv = r2 > (R)0 ? rsq(r2) : (R)0;
-            if (mask && k0 + ((lane + st) & 31) <= iu) inv = (R)0;
-            R sn, cs;
-            scpi_fast(kpi * (r2 * inv), sn, cs);
-            const C g = cmake<C>(cs * inv, sn * inv);
-            cfma(fwd, cmake<C>(ps.w, qjy), g);
-            cfma(rev, qi, g);
-            rev.x = __shfl_sync(FULL, rev.x, (lane + 1) & 31);
-            rev.y = __shfl_sync(FULL, rev.y, (lane + 1) & 31);
-        }
+            for (int st = 0; st < 32; ++st) {
+                const SrcPos<R> ps = pl[st];
+                const R qjy = ql[st];
+                const R dx = x - ps.x, dy = y - ps.y, dz = z - ps.z;
+                const R r2 = dx * dx + dy * dy + dz * dz;
+                R inv = inv_dist(r2);
+                if constexpr (decltype(masked)::value)
+                    if (k0 + ((lane + st) & 31) <= iu) inv = (R)0;
+                R sn, cs;
+                scpi_fast(kpi * (r2 * inv), sn, cs);
+                const C g = cmake<C>(cs * inv, sn * inv);
+                cfma(fwd, cmake<C>(ps.w, qjy), g);
+                cfma(rev, qi, g);
+                rev.x = __shfl_sync(FULL, rev.x, (lane + 1) & 31);
+                rev.y = __shfl_sync(FULL, rev.y, (lane + 1) & 31);
+            }
+        };
+        if (self && k0 < it.y + kP2PTile) steps(std::true_type{});
+        else steps(std::false_type{});
         red[wl][lane] = rev;
         __syncthreads();
         if (threadIdx.x < 32 && k0 + (int)threadIdx.x < nb) {
