@@ -417,3 +417,15 @@ def test_mlfma_with_sampled_operators_vs_direct(sphere4k):
     ref = direct.direct(pts, q[0], prm["k"])
     assert np.linalg.norm(phi_s - ref) / np.linalg.norm(ref) < 1e-3
     assert 0 < np.linalg.norm(phi_s - phi) / np.linalg.norm(phi) < 1e-4
+
+
+@pytest.mark.parametrize("Lc,Lp", [(10, 19), (11, 20), (33, 57)])
+def test_theta_maps_are_centrosymmetric(Lc, Lp):
+    """Gauss-Legendre nodes come in pairs (x, -x) with equal weights and Pbar_n^m(-x) =
+    (-1)^(n+m) Pbar_n^m(x), so every per-mode map satisfies A[n'-1-i', n-1-i] = A[i', i]: the
+    property that lets the GPU path apply each map as an even and an odd half of a quarter of
+    its size (odd and even grid lengths both covered)."""
+    gc, gp = mlfma.Grid(Lc), mlfma.Grid(Lp)
+    assert np.allclose(gc.x, -gc.x[::-1], atol=1e-15) and np.allclose(gc.wgl, gc.wgl[::-1], rtol=1e-13)
+    for m, A in enumerate(mlfma.theta_maps(gc, gp)):
+        assert np.max(np.abs(A[::-1, ::-1] - A)) <= 1e-13 * np.max(np.abs(A)), m
