@@ -403,6 +403,9 @@ static void init_streams(Plan& P, int nsub) {
     MLFMA_CUDA(cudaStreamCreateWithFlags(&P.mstream, cudaStreamNonBlocking));
     MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_mfork, cudaEventDisableTiming));
     MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_mdone, cudaEventDisableTiming));
+    MLFMA_CUDA(cudaStreamCreateWithFlags(&P.sstream, cudaStreamNonBlocking));
+    MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_sfork, cudaEventDisableTiming));
+    MLFMA_CUDA(cudaEventCreateWithFlags(&P.ev_sdone, cudaEventDisableTiming));
     for (int w = 0; w < nsub; ++w) {
         cudaStream_t st;
         cudaEvent_t ev;
@@ -418,6 +421,7 @@ static void release_plan(Plan& P) {
     if (P.gstream) cudaStreamSynchronize(P.gstream);
     if (P.nstream) cudaStreamSynchronize(P.nstream);
     if (P.mstream) cudaStreamSynchronize(P.mstream);
+    if (P.sstream) cudaStreamSynchronize(P.sstream);
     for (auto s : P.sub_streams) cudaStreamSynchronize(s);
     drop_graphs(P);
     for (auto* sp : P.subs) {
@@ -442,8 +446,11 @@ static void release_plan(Plan& P) {
     if (P.ev_mfork) cudaEventDestroy(P.ev_mfork);
     if (P.ev_mdone) cudaEventDestroy(P.ev_mdone);
     if (P.mstream) cudaStreamDestroy(P.mstream);
-    P.ev_fork = P.ev_join = P.ev_nfork = P.ev_near = P.ev_mfork = P.ev_mdone = nullptr;
-    P.gstream = P.nstream = P.mstream = nullptr;
+    if (P.ev_sfork) cudaEventDestroy(P.ev_sfork);
+    if (P.ev_sdone) cudaEventDestroy(P.ev_sdone);
+    if (P.sstream) cudaStreamDestroy(P.sstream);
+    P.ev_fork = P.ev_join = P.ev_nfork = P.ev_near = P.ev_mfork = P.ev_mdone = P.ev_sfork = P.ev_sdone = nullptr;
+    P.gstream = P.nstream = P.mstream = P.sstream = nullptr;
     P.mem.release_all();
 }
 

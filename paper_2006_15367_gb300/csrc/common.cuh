@@ -303,6 +303,10 @@ struct Plan {
     // downward pass waits for ev_mdone, recorded after the last (top) level's M2L
     cudaStream_t mstream = nullptr;
     cudaEvent_t ev_mfork = nullptr, ev_mdone = nullptr;
+    // inside the near field of plans with large leaves: the small leaves' kernels run on sstream
+    // beside the large leaves' tiled and symmetric kernels (disjoint targets), joined by ev_sdone
+    cudaStream_t sstream = nullptr;
+    cudaEvent_t ev_sfork = nullptr, ev_sdone = nullptr;
     std::map<int64_t, cudaGraphExec_t> graphs;
     // batched plans: independent geometries; level-uniform ones are merged into this plan as a
     // forest (the sub-plans then only hold the shared operators), others run concurrently on

@@ -493,13 +493,23 @@ static void near_apply(Plan& p, const void* qs, void* phis, void* grads, bool ti
     const R kpi = (R)(p.k / M_PI);
     const bool sym_pass = NR == 1 && !grads && p.n_tiles > 0 && p.n_sym_items > 0;
     StageTimer st(p, MLFMA_STAGE_P2P, 0, (n32 > 0) + (nmid > 0) + (p.n_tiles > 0) + 2 * sym_pass, timed);
+    // with large leaves, the small leaves' kernels (whose single wave of warps ends on the
+    // heaviest leaves) run on their own stream beside the large leaves' kernels, which write
+    // other targets; sequential while stage timings are taken
+    const cudaStream_t ns = p.stream;
+    const bool sfork = p.sstream && !p.profiling && p.n_tiles > 0 && (n32 > 0 || nmid > 0);
+    if (sfork) {
+        MLFMA_CUDA(cudaEventRecord(p.ev_sfork, ns));
+        MLFMA_CUDA(cudaStreamWaitEvent(p.sstream, p.ev_sfork, 0));
+    }
+    const cudaStream_t ss = sfork ? p.sstream : ns;
     if (n32 > 0) {
         if (grads)
-            k_p2p<R, C, true, 1, false><<<nblk(n32, 4), 128, 0, p.stream>>>(
+            k_p2p<R, C, true, 1, false><<<nblk(n32, 4), 128, 0, ss>>>(
                 n32, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos,
                 (const C*)qs, sn, kpi, (C*)phis, (C*)grads);
         else
-            k_p2p<R, C, false, NR, false><<<nblk(n32, 4), 128, 0, p.stream>>>(
+            k_p2p<R, C, false, NR, false><<<nblk(n32, 4), 128, 0, ss>>>(
                 n32, p.p2p_small, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos,
                 (const C*)qs, sn, kpi, (C*)phis, nullptr);
         MLFMA_LAUNCH_CHECK();
@@ -507,11 +517,11 @@ static void near_apply(Plan& p, const void* qs, void* phis, void* grads, bool ti
     if (nmid > 0) {
         const int* mid = p.p2p_small + n32;
         if (grads)
-            k_p2p<R, C, true, 1, true><<<nblk(nmid, 4), 128, 0, p.stream>>>(
+            k_p2p<R, C, true, 1, true><<<nblk(nmid, 4), 128, 0, ss>>>(
                 nmid, mid, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, sn,
                 kpi, (C*)phis, (C*)grads);
         else
-            k_p2p<R, C, false, NR, true><<<nblk(nmid, 4), 128, 0, p.stream>>>(
+            k_p2p<R, C, false, NR, true><<<nblk(nmid, 4), 128, 0, ss>>>(
                 nmid, mid, p.leaf_level, p.leaf_box, p.near_off, p.near_lev, p.near_box, LR, p.pos, (const C*)qs, sn,
                 kpi, (C*)phis, nullptr);
         MLFMA_LAUNCH_CHECK();
@@ -539,6 +549,10 @@ static void near_apply(Plan& p, const void* qs, void* phis, void* grads, bool ti
                 p.p2p_tiles, p.leaf_level, p.leaf_box, LR, p.sym_red_off, p.sym_red, (const C*)p.sym_buf, (C*)phis);
             MLFMA_LAUNCH_CHECK();
         }
+    }
+    if (sfork) {
+        MLFMA_CUDA(cudaEventRecord(p.ev_sdone, p.sstream));
+        MLFMA_CUDA(cudaStreamWaitEvent(ns, p.ev_sdone, 0));
     }
 }
 
