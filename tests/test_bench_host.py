@@ -35,3 +35,13 @@ def test_oracle_mlfma_cpu_reference_runs():
     r = bench.oracle_mlfma_rate("sphere4k")
     assert "error" not in r, r
     assert r["value"] > 0 and r["unit"] == "points/s" and r["apply_s"] > 0
+
+
+def test_config_names_the_sampled_operator_form():
+    import argparse
+    prm = {"digits": 3}
+    base = dict(workload=bench.WORKLOAD, digits=0, precision="fp32", nrhs=1, mode="apply")
+    plain = bench.config_dict(argparse.Namespace(**base, sampled_operators=0), 1 << 20, prm)
+    smp = bench.config_dict(argparse.Namespace(**base, sampled_operators=6), 1 << 20, prm)
+    assert "sampled operators" not in plain["workload"]
+    assert smp["workload"].endswith("sampled operators (oversampling 6)")
